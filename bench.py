@@ -1,0 +1,341 @@
+#!/usr/bin/env python3
+"""Benchmark: B_{p-3} and E_{p-3} mod p for every prime of the 1e5-wide window
+[1062200000, 1062300000) near 1e9 (4907 primes, all < 2^30).
+
+One step = the whole path over the window: segmented sieve on the device,
+planning, the persistent accumulation of BB30 (eqn 3.7) and EE33 (eqn 5.6),
+per-prime finalisation, and flag/compaction of the zero residues
+(wv_search_ex).  The headline value is primes/s (each prime gets both
+residues); modmul/s counts two modular multiplications per summed term
+(eqn 3.12).
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+For N > 1 launch with torch.distributed.run; each rank takes its own
+1e5-wide window (weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("primes/sec and modmul/sec at p≈1e9 (B_{p-3},E_{p-3} mod p), "
+          "% IMAD peak; p99 latency")
+LO, HI = 1_062_200_000, 1_062_300_000
+WIDTH = HI - LO
+IMAD_PER_SM_CLK = 64          # 32-bit integer multiply-add results per SM per clock
+IMAD_PER_MODMUL = 3.5         # see the design doc: 7 IMAD-pipe ops per term, 2 modmuls per term
+SM_MAX_MHZ_FALLBACK = 2070.0
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        rows = []
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 10:
+                continue
+            if self.uuid and self.uuid not in parts[1]:
+                continue
+            rows.append(parts)
+        if not rows:
+            return None
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def gpu_uuid(torch):
+    try:
+        u = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+        return u.replace("GPU-", "")
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_sample(k: int, seed: int = 7):
+    from paper_2101_11157_gb300 import workloads as W
+    ps = W.primes_in(LO, LO + 20000)  # a seeded draw from the window's first 2e4
+    return W.seeded_subset(ps, k, seed)
+
+
+def run_oracle_step(primes, threads: int):
+    """Both residues for `primes` with the oracle on host threads; B and E of a
+    prime run in parallel threads so a one-prime step uses two cores."""
+    from oracle import oracle as O
+    res = {}
+
+    def job(kind):
+        if kind == "b":
+            res["b"] = O.residues(primes, method_b="default", method_e=None, threads=max(1, threads // 2))[0]
+        else:
+            res["e"] = O.residues(primes, method_b=None, method_e="default", threads=max(1, threads // 2))[1]
+    ts = [threading.Thread(target=job, args=(k,)) for k in ("b", "e")]
+    t0 = time.perf_counter()
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    return time.perf_counter() - t0, res
+
+
+def reference_arm(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    sample = oracle_sample(1, seed=11)
+    threads = 2
+    for _ in range(args.warmup):
+        run_oracle_step(sample, threads)
+    times = []
+    for _ in range(args.steps):
+        dt, _ = run_oracle_step(sample, threads)
+        times.append(dt)
+    ms = 1000.0 * sum(times) / len(times)
+    val = len(sample) / (ms / 1000.0)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "primes/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int128",
+        "data": "synthetic: primes of the window near 1.06e9 (no dataset)",
+        "config": {"workload": f"B_{{p-3}}, E_{{p-3}} mod p for primes in [{LO}, {HI}); "
+                               "reference = plain CPU oracle (Stafford-Vandiver eqn 2.4 for B, "
+                               "Glaisher eqn 4.1 for E), one seeded prime per step",
+                   "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": val, "unit": "primes/s", "cores": threads, "kind": "oracle",
+                         "sample": f"1 prime per step ({int(sample[0])}), B and E on 2 threads"},
+        "e2e": {"value": val, "unit": "primes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def gpu_arm(args):
+    import numpy as np
+    import torch
+
+    from paper_2101_11157_gb300 import api, wv
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    width = args.width
+    lo = LO + rank * WIDTH
+    hi = lo + width
+    stream = torch.cuda.current_stream()
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+
+    # inputs: the window's primes (for counting terms and for the e2e leg)
+    d_pr_all = api.sieve(lo, hi)
+    primes = api.to_u64(d_pr_all)
+    n_primes = primes.size
+    tb, te = wv.wv_count_terms(primes)
+    modmuls_per_step = 2 * (tb + te)
+    cap_h = 64
+    hits = torch.empty((cap_h, 2), dtype=torch.int64, device="cuda")
+    d_pr = torch.empty(n_primes, dtype=torch.int64, device="cuda")
+    d_rb, d_re = torch.empty_like(d_pr), torch.empty_like(d_pr)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")  # > L2 (129 MB)
+
+    def step():
+        return wv.wv_search_ex(lo, hi, 0, hits, d_pr, d_rb, d_re, None, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # timed region: K steps, CUDA events per step, L2 flushed between steps
+    uuid = gpu_uuid(torch)
+    sampler = ClockSampler(uuid)
+    sampler.start()
+    time.sleep(0.3)
+    wv.wv_profile_reset()
+    wv.wv_profile_enable(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    t_wall = time.perf_counter()
+    nh = 0
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        nh, npr = step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    wv.wv_profile_enable(False)
+    prof = wv.wv_profile_collect()
+    launches = wv.wv_profile_launches()
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(step_ms) / len(step_ms)
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # e2e: host prime list in pinned memory -> device -> residues -> host
+    h_in = torch.from_numpy(primes.view(np.int64)).pin_memory()
+    h_b = torch.empty(n_primes, dtype=torch.int64, pin_memory=True)
+    h_e = torch.empty(n_primes, dtype=torch.int64, pin_memory=True)
+    d_in = torch.empty_like(d_pr)
+    e2e_ms = []
+    for i in range(max(1, args.steps)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d_in.copy_(h_in, non_blocking=True)
+        wv.wv_residues_pm3(d_in, d_rb, d_re, stream)
+        h_b.copy_(d_rb, non_blocking=True)
+        h_e.copy_(d_re, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append(1000 * (time.perf_counter() - t0))
+    e2e_step = statistics.median(e2e_ms)
+    if dist:
+        t = torch.tensor([e2e_step], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_step = float(t.item())
+
+    # CPU oracle baseline (rank 0, N = 1 only)
+    cpu = None
+    if ws == 1 and rank == 0 and not args.no_cpu:
+        sample = oracle_sample(2, seed=7)
+        dt, res = run_oracle_step(sample, threads=4)
+        cpu = {"value": len(sample) / dt, "unit": "primes/s", "cores": 4, "kind": "oracle",
+               "sample": f"{len(sample)} seeded primes of the window ({', '.join(str(int(x)) for x in sample)}): "
+                         "B by Stafford-Vandiver (eqn 2.4), E by Glaisher (eqn 4.1), 2 threads per kind"}
+        # the oracle and the GPU agree on the sample
+        idx = np.searchsorted(primes, sample)
+        gb, ge = api.to_u64(d_rb)[idx], api.to_u64(d_re)[idx]
+        cpu["agrees_with_gpu"] = bool(np.array_equal(gb, res["b"]) and np.array_equal(ge, res["e"]))
+
+    # roofline of the dominant kernel (the p < 2^30 accumulation)
+    acc_launches, acc_ms = prof.get("accumulate_m31", (0, 0.0))
+    acc_avg_ms = acc_ms / max(1, acc_launches)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz") or SM_MAX_MHZ_FALLBACK)
+    imad_peak = sms * IMAD_PER_SM_CLK * sm_max * 1e6            # IMAD results / s
+    peak_gmodmul = imad_peak / IMAD_PER_MODMUL / 1e9
+    achieved_gmodmul = (modmuls_per_step / (acc_avg_ms / 1000.0)) / 1e9 if acc_avg_ms else 0.0
+    total_primes = n_primes * ws
+    value = total_primes / (ms / 1000.0)
+    line = {
+        "metric": METRIC, "value": value, "unit": "primes/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic: every prime of the window, sieved on the device (no dataset)",
+        "config": {"workload": f"sieve + B_{{p-3}} (BB30, eqn 3.7) + E_{{p-3}} (EE33, eqn 5.6) mod p "
+                               f"+ zero/near flags for all primes in [{lo}, {hi}) per GPU",
+                   "primes_per_gpu": int(n_primes), "congruences": "BB30+EE33",
+                   "terms_per_step": int(tb + te), "parallelism": f"range-sharded x{ws}",
+                   "l2": "flushed between steps (256 MB write)"},
+        "modmul_per_s": modmuls_per_step * ws / (ms / 1000.0),
+        "roofline": {"bound": "alu", "achieved": achieved_gmodmul, "peak": peak_gmodmul,
+                     "unit": "Gmodmul/s", "frac": achieved_gmodmul / peak_gmodmul if peak_gmodmul else None,
+                     "traffic": None,
+                     "peak_basis": f"{sms} SMs x {IMAD_PER_SM_CLK} IMAD/clk x {sm_max:.0f} MHz / "
+                                   f"{IMAD_PER_MODMUL} IMAD per modmul (derived, not measured)",
+                     "kernel": "accumulate_m31", "kernel_ms": acc_avg_ms},
+        "e2e": {"value": total_primes / (e2e_step / 1000.0), "unit": "primes/s",
+                "h2d_bytes_per_step": int(n_primes * 8), "d2h_bytes_per_step": int(n_primes * 16),
+                "path": "host prime list (pinned) -> wv_residues_pm3 -> host residues"},
+        "gpu_launches": int(launches),
+        "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()},
+        "wall_s": wall, "hits": int(nh),
+        "clocks": clocks,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="wv", choices=["wv", "reference"])
+    ap.add_argument("--width", type=int, default=WIDTH, help="window width (smaller for profiling)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return gpu_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

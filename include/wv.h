@@ -1,0 +1,213 @@
+/*
+ * wv.h -- C ABI of the GB300 Wolstenholme / Vandiver residue library.
+ *
+ * For primes p the library computes B_{p-3} mod p and E_{p-3} mod p
+ * (Bernoulli numbers from z/(e^z-1), Euler numbers from sec z; Sec. 1) with
+ * the computation-friendly congruences of Sec. 3 (eqns 3.1-3.7) and Sec. 5
+ * (eqns 5.1-5.6), and flags the primes where a residue is 0: p is a
+ * Wolstenholme prime iff p | B_{p-3} (Sec. 1, eqn 1.2 and the remark after
+ * it) and a Vandiver prime iff p | E_{p-3} (Sec. 1).
+ *
+ * Conventions for every entry point:
+ *  - Pointers named d_* are DEVICE pointers (global memory of the current
+ *    CUDA device), owned and allocated by the caller.  Pointers named h_* or
+ *    plain out-parameters (n_out, count, ...) are HOST pointers.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are asynchronous on `stream` unless stated otherwise;
+ *    library-internal scratch is allocated stream-ordered on `stream`.
+ *  - Every call returns a wv_status.  Nothing aborts, throws or traps; on
+ *    failure wv_last_error() returns a message for the calling thread.
+ *  - Residues are the canonical representatives in [0, p), as uint64.
+ *  - Supported primes: 5 <= p < 2^37 (WV_P_MAX).  Primality is the caller's
+ *    contract for d_primes; an odd p outside the range, or an even p, gives
+ *    WV_RESIDUE_INVALID in its output slot (the call itself still succeeds).
+ *  - The Euler numbers use the sec convention (E_2 = +1), as the paper does.
+ */
+#ifndef WV_H
+#define WV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int wv_status;
+#define WV_OK 0
+#define WV_EINVAL 1      /* bad argument */
+#define WV_ENOMEM 2      /* device or host allocation failed */
+#define WV_ERANGE 3      /* output capacity too small; the full count is still reported */
+#define WV_ECUDA 4       /* a CUDA runtime call failed */
+#define WV_ETIMEOUT 5    /* a bounded wait expired */
+#define WV_ECANCELLED 6  /* the work was cancelled */
+#define WV_EBUSY 7       /* the object is busy (e.g. a server queue is full) */
+
+#define WV_P_MAX (1ull << 37)
+#define WV_RESIDUE_INVALID UINT64_MAX
+
+/* hit kinds (wv_hit.kind bit mask) */
+#define WV_KIND_BERNOULLI 1u /* B_{p-3} = 0 mod p: Wolstenholme prime */
+#define WV_KIND_EULER 2u     /* E_{p-3} = 0 mod p: Vandiver prime     */
+
+typedef void *wv_stream; /* a cudaStream_t */
+
+/* Library version string (static storage). */
+const char *wv_version(void);
+
+/* Message for the last failing call made on this host thread ("" if none). */
+const char *wv_last_error(void);
+
+/* ---------------------------------------------------------------------- */
+/* a1: prime enumeration (the paper enumerates primes over intervals with */
+/* a CPU sieve, Sec. 3 "Results" and Sec. 5; here a segmented GPU sieve)  */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * All primes in [lo, hi), ascending, written to d_out[0 .. min(count,cap)).
+ *  lo, hi : 0 <= lo <= hi <= WV_P_MAX.
+ *  d_out  : device array of `cap` uint64 (may be NULL if cap == 0).
+ *  n_out  : host; receives the number of primes in [lo, hi).
+ * SYNCHRONOUS: returns after the count is known (stream synchronised).
+ * Returns WV_ERANGE if count > cap (the first cap primes are written and
+ * *n_out holds the full count), WV_EINVAL on a bad range.
+ */
+wv_status wv_sieve(uint64_t lo, uint64_t hi, uint64_t *d_out, size_t cap,
+                   size_t *n_out, wv_stream stream);
+
+/* Number of primes in [lo, hi) without materialising them.  SYNCHRONOUS. */
+wv_status wv_sieve_count(uint64_t lo, uint64_t hi, uint64_t *count, wv_stream stream);
+
+/* ---------------------------------------------------------------------- */
+/* a2-a6: residues                                                         */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * d_out[i] = B_{p_i - 3} mod p_i for the n primes d_primes[0..n).
+ * Follows Sec. 3: B_{p-3} from eqn 3.7 (BB30) for p >= 11, each sum
+ * S_{p-4}(x,y) = sum_{xp<s<yp} s^-3 evaluated as c1/c0 of
+ * prod (z + s^3) (the polynomial trick and eqn 3.12), partial products
+ * combined with eqn 3.14, one modular inverse per prime; p = 5, 7 from the
+ * definition.  d_primes and d_out: device arrays of n uint64 (may alias
+ * only if d_out == d_primes).  Asynchronous.
+ */
+wv_status wv_bernoulli_pm3(const uint64_t *d_primes, size_t n, uint64_t *d_out,
+                           wv_stream stream);
+
+/*
+ * d_out[i] = E_{p_i - 3} mod p_i (sec convention).  Follows Sec. 5: eqn 5.6
+ * (EE33) for p >= 11 with S_{p-3}(x,y) = sum s^-2 evaluated through
+ * prod (z + s^2) (the remark after eqn 5.6).  Same layout and behaviour as
+ * wv_bernoulli_pm3.  Asynchronous.
+ */
+wv_status wv_euler_pm3(const uint64_t *d_primes, size_t n, uint64_t *d_out,
+                       wv_stream stream);
+
+/*
+ * Both residues in one launch sequence (one persistent accumulation launch
+ * covers the sums of both congruences).  Either output may be NULL.
+ * Asynchronous.
+ */
+wv_status wv_residues_pm3(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,
+                          uint64_t *d_out_e, wv_stream stream);
+
+/* Options for the *_ex entry points.  Zero-initialise, then set fields;
+ * a zero / negative field means "library default". */
+typedef struct {
+  int cong_b;       /* congruence id (wv_congruence_info) for B; <0: default BB30 */
+  int cong_e;       /* congruence id for E; <0: default EE33 */
+  int block;        /* accumulation block size (threads), multiple of 32 */
+  int ilp;          /* independent accumulator chains per thread: 1, 2 or 4 */
+  int tile_terms;   /* target terms per warp tile */
+  int max_tiles;    /* maximum tiles per (prime, sum) */
+  int blocks_per_sm;/* persistent grid = SMs x this */
+  int reserved[9];
+} wv_options;
+
+/* wv_residues_pm3 with explicit congruence choice and launch shape.
+ * Any valid congruence gives the identical residue (the choice only changes
+ * the cost, Sec. 3 and Sec. 5).  Asynchronous. */
+wv_status wv_residues_ex(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,
+                         uint64_t *d_out_e, const wv_options *opt, wv_stream stream);
+
+/* ---------------------------------------------------------------------- */
+/* a7: search (sieve + both residues + flag/compact)                      */
+/* ---------------------------------------------------------------------- */
+
+typedef struct {
+  uint64_t p;
+  uint32_t kind; /* WV_KIND_BERNOULLI | WV_KIND_EULER */
+  uint32_t pad;
+} wv_hit;
+
+/*
+ * All primes p in [lo, hi) (5 <= p) with B_{p-3} = 0 or E_{p-3} = 0 mod p
+ * (Sec. 3 and Sec. 5 searches), ascending by p, written to
+ * d_hits[0 .. min(count, cap)).  n_hits (host) receives the count.
+ * SYNCHRONOUS.  WV_ERANGE if count > cap.
+ */
+wv_status wv_search(uint64_t lo, uint64_t hi, wv_hit *d_hits, size_t cap,
+                    size_t *n_hits, wv_stream stream);
+
+/*
+ * Search with residues: like wv_search, and also writes, for every prime of
+ * [lo, hi) in ascending order, p to d_primes[i], B_{p-3} mod p to d_res_b[i]
+ * and E_{p-3} mod p to d_res_e[i] (any of the three may be NULL).  Those
+ * arrays hold `cap_primes` entries; *n_primes receives the prime count.
+ * `near` > 0 also reports primes whose symmetric residue <r>_p in
+ * (-p/2, p/2] satisfies |<r>_p| < near (the near-miss tables of Sec. 3 and
+ * Sec. 5); near-miss entries carry kind bit 2 (B) / bit 3 (E).
+ * SYNCHRONOUS.
+ */
+#define WV_KIND_NEAR_B 4u
+#define WV_KIND_NEAR_E 8u
+wv_status wv_search_ex(uint64_t lo, uint64_t hi, uint64_t near, wv_hit *d_hits,
+                       size_t cap, size_t *n_hits, uint64_t *d_primes,
+                       uint64_t *d_res_b, uint64_t *d_res_e, size_t cap_primes,
+                       size_t *n_primes, const wv_options *opt, wv_stream stream);
+
+/* ---------------------------------------------------------------------- */
+/* host-side inspection of the congruence tables (no GPU needed)           */
+/* ---------------------------------------------------------------------- */
+
+/* Number of congruences in the library (BB1..BB30, EE3..EE33). */
+int wv_congruence_count(void);
+
+/* Congruence `id`: kind 0 = B_{p-3}, 1 = E_{p-3}; n_rows sums; lhs = the
+ * constant on the left; name (static string).  Any out-pointer may be NULL. */
+wv_status wv_congruence_info(int id, int *kind, int *n_rows, int64_t *lhs,
+                             const char **name);
+
+/* Row `row` of congruence `id`: coef * S(xn/xd, yn/yd). */
+wv_status wv_congruence_row(int id, int row, int64_t *coef, uint32_t *xn,
+                            uint32_t *xd, uint32_t *yn, uint32_t *yd);
+
+/* ---------------------------------------------------------------------- */
+/* profiling: per-kernel CUDA-event timing on the launching stream         */
+/* ---------------------------------------------------------------------- */
+
+/* Enable (1) / disable (0) event timing of every library kernel launch. */
+void wv_profile_enable(int on);
+/* Clear accumulated timings and launch counts. */
+void wv_profile_reset(void);
+/* Synchronise pending events and fold them into the totals. */
+wv_status wv_profile_collect(void);
+/* Number of distinct kernels seen; then per index its name, launch count
+ * and total milliseconds (totals are those folded in by wv_profile_collect;
+ * launch counts are kept even when timing is disabled). */
+int wv_profile_kernels(void);
+wv_status wv_profile_get(int idx, const char **name, uint64_t *launches, double *total_ms);
+/* Total kernel launches issued by the library since the last reset. */
+uint64_t wv_profile_launches(void);
+
+/* Algorithmic work of one residue call: the number of terms s summed for the
+ * given primes (host array h_primes) under congruences cong_b / cong_e
+ * (<0: defaults; pass -2 to skip that kind).  Each term costs two modular
+ * multiplications (eqn 3.12).  Host only.  */
+wv_status wv_count_terms(const uint64_t *h_primes, size_t n, int cong_b, int cong_e,
+                         uint64_t *terms_b, uint64_t *terms_e);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WV_H */

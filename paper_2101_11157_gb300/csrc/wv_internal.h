@@ -1,0 +1,111 @@
+// wv_internal.h -- host-side runtime shared by the library's translation units:
+// error reporting, per-device state, stream-ordered scratch, launch profiling,
+// and the device-wide scan used by the sieve and the planner.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include <string>
+
+#include "../../include/wv.h"
+
+namespace wv {
+
+// ------------------------------------------------------------ errors
+wv_status set_error(wv_status st, const char *fmt, ...);
+void clear_error();
+wv_status cuda_fail(cudaError_t e, const char *where);
+
+#define WV_CUDA(call)                                                   \
+  do {                                                                  \
+    cudaError_t _e = (call);                                            \
+    if (_e != cudaSuccess) return ::wv::cuda_fail(_e, #call);           \
+  } while (0)
+
+#define WV_CHECK(expr)                                                  \
+  do {                                                                  \
+    wv_status _s = (expr);                                              \
+    if (_s != WV_OK) return _s;                                         \
+  } while (0)
+
+// ------------------------------------------------------------ device state
+struct DeviceState {
+  int device = -1;
+  int sms = 0;
+  int cc_major = 0, cc_minor = 0;
+  cudaMemPool_t pool = nullptr;
+  uint32_t *base_primes = nullptr;  // odd primes 3 .. sqrt(WV_P_MAX), device
+  uint32_t n_base = 0;
+};
+// State of the current device, created on first use.
+wv_status device_state(DeviceState **out);
+
+// ------------------------------------------------------------ scratch
+// Stream-ordered allocation from the library's own memory pool.
+wv_status scratch_alloc(void **ptr, size_t bytes, cudaStream_t s);
+void scratch_free(void *ptr, cudaStream_t s);
+
+// RAII list of scratch blocks freed (stream-ordered) on scope exit.
+struct Scratch {
+  cudaStream_t s;
+  void *ptrs[32];
+  int n = 0;
+  explicit Scratch(cudaStream_t st) : s(st) {}
+  ~Scratch() {
+    for (int i = n - 1; i >= 0; --i) scratch_free(ptrs[i], s);
+  }
+  template <typename T>
+  wv_status get(T **p, size_t count) {
+    void *v = nullptr;
+    wv_status st = scratch_alloc(&v, count * sizeof(T) + 256, s);
+    if (st != WV_OK) return st;
+    ptrs[n++] = v;
+    *p = reinterpret_cast<T *>(v);
+    return WV_OK;
+  }
+};
+
+// ------------------------------------------------------------ profiling
+void prof_begin(const char *name, cudaStream_t s);
+void prof_end(const char *name, cudaStream_t s);
+
+#define WV_LAUNCH(name, kern, grid, block, smem, stream, ...)           \
+  do {                                                                  \
+    ::wv::prof_begin(name, stream);                                     \
+    kern<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);           \
+    ::wv::prof_end(name, stream);                                       \
+    cudaError_t _le = cudaGetLastError();                               \
+    if (_le != cudaSuccess) return ::wv::cuda_fail(_le, name);          \
+  } while (0)
+
+// ------------------------------------------------------------ scan
+// Exclusive prefix sum of n values; *d_total (device) receives the sum.
+// tmp must hold scan_tmp_elems(n) elements.
+size_t scan_tmp_elems(size_t n);
+wv_status scan_exclusive_u32(const uint32_t *d_in, uint32_t *d_out, size_t n,
+                             uint32_t *d_total, uint32_t *d_tmp, cudaStream_t s);
+wv_status scan_exclusive_u64(const uint64_t *d_in, uint64_t *d_out, size_t n,
+                             uint64_t *d_total, uint64_t *d_tmp, cudaStream_t s);
+
+// ------------------------------------------------------------ residues
+struct ResidueConfig {
+  int cong_b = 6;        // BB30; -2 = skip
+  int cong_e = 12;       // EE33; -2 = skip
+  int block = 256;
+  int ilp = 2;
+  int tile_terms = 65536;
+  int max_tiles = 32;
+  int blocks_per_sm = 0;  // 0 = occupancy
+};
+wv_status resolve_config(const wv_options *opt, bool want_b, bool want_e, ResidueConfig *cfg);
+
+// Residues for n primes (device array), asynchronous on s.
+wv_status residues_device(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,
+                          uint64_t *d_out_e, const ResidueConfig &cfg, cudaStream_t s);
+
+// Sieve primitives
+wv_status sieve_device(uint64_t lo, uint64_t hi, uint64_t *d_out, size_t cap,
+                       uint64_t *count_host, cudaStream_t s);
+
+}  // namespace wv

@@ -1,0 +1,502 @@
+// wv_residue.cu -- steps a2-a6: plan, term generation, accumulation, reduction
+// and finalisation of B_{p-3} mod p and E_{p-3} mod p.
+//
+// Method (Sec. 3, "It remains to describe how to calculate these sums"; Sec. 5
+// after eqn 5.6): every congruence row contributes coef * S(x, y) with
+// S = sum_{xp<s<yp} s^-e (e = 3 for B_{p-3}, e = 2 for E_{p-3}).  S is the
+// ratio c1/c0 of the two lowest coefficients of prod (z + s^e), built one
+// term at a time by eqn 3.12 (c1 <- c1 t + c0, c0 <- c0 t, t = s^e); pieces
+// of a product are merged with eqn 3.14.  One modular inverse per prime
+// finishes the sum (Sec. 3, the CPU's last step in the paper's GPU method).
+//
+// GB300 design:
+//  * Work unit = a warp tile: a contiguous range of s inside one (prime, row)
+//    sum.  The planner splits every sum into at most `max_tiles` tiles of about
+//    `tile_terms` terms.  A persistent kernel (grid = SMs x occupancy) lets
+//    warps take tiles from an atomic counter, largest primes first.
+//  * Inside a tile, 32 lanes x ILP chains each own a contiguous run of s.  Term
+//    generation is by forward differences (Sec. 3, improvement 1): s^3 from
+//    (s-1)^3 with three modular additions, s^2 with one; no multiplication.
+//  * Accumulation: signed Montgomery arithmetic (see wv_arith.cuh).  For
+//    p < 2^30 a term costs 7 integer multiplies (hi(c0 t), hi(c1 t), t p^-1,
+//    c0 tq, c1 tq, hi(m0 p), hi(m1 p)); 64-bit words for 2^30 <= p < 2^37.
+//  * The chains of a tile are merged with eqn 3.14 in registers and by warp
+//    shuffles; one (c0, c1) pair per tile goes to global memory.  The finalise
+//    kernel (one warp per prime and kind) merges the tiles of each sum, forms
+//    sum_j coef_j c1_j / c0_j as one fraction, and inverts once (Fermat).
+//
+// Montgomery bookkeeping: the hot step multiplies by a plain t with REDC, so
+// c0 and c1 drift by powers of R, but the ratio c1/c0 always equals S * R
+// (true initially for (c0, c1) = (R, 0) and preserved by both eqn 3.12 steps
+// and by eqn 3.14 under REDC).  The finaliser therefore divides by R once.
+#include <stdio.h>
+
+#include "wv_arith.cuh"
+#include "wv_internal.h"
+#include "wv_tables.h"
+
+namespace wv {
+
+constexpr int kAccThreads = 256;
+constexpr int kMaxRowsPP = 66;  // B rows + E rows for one prime (30 + 33 for BB30 + EE33)
+constexpr uint32_t kChunkPrimes = 16384;  // primes per internal launch sequence
+
+struct Plan {
+  uint32_t n;                   // primes in this chunk
+  uint32_t rows_b, rows_e, rows_pp;
+  uint32_t tile_terms, max_tiles;
+  const uint64_t *primes;       // caller's primes (chunk base)
+  uint64_t *out_b, *out_e;      // caller's outputs (chunk base), may be null
+  PrimeCtx *ctx;                // per slot (M31 slots first, then M64)
+  uint32_t *flag, *pos, *n31;   // path partition
+  uint64_t *seg_lo, *seg_cnt;   // per segment (slot * rows_pp + row)
+  uint32_t *seg_tiles, *seg_first;
+  uint32_t *total_tiles, *split_tile;
+  uint32_t *counters;           // [0] M31 accumulation, [1] M64 accumulation
+  ulonglong2 *partials;         // per tile (c0, c1), canonical
+  // congruence rows: rows [0, rows_b) are B rows, [rows_b, rows_pp) E rows
+  uint32_t xn[kMaxRowsPP], xd[kMaxRowsPP], yn[kMaxRowsPP], yd[kMaxRowsPP];
+  int64_t coef[kMaxRowsPP];
+  int64_t lhs_b, lhs_e;
+};
+
+// ------------------------------------------------------------------ planner
+__global__ void k_plan_prime(Plan P) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P.n) return;
+  uint64_t p = P.primes[i];
+  P.flag[i] = (p < kM31Limit) ? 1u : 0u;  // invalid values also go with the M31 slots
+}
+
+__global__ void k_plan_scatter(Plan P) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P.n) return;
+  uint64_t p = P.primes[i];
+  uint32_t slot = P.flag[i] ? P.pos[i] : *P.n31 + (i - P.pos[i]);
+  PrimeCtx c;
+  bool valid = (p >= 5) && (p & 1) && (p < kPMax);
+  if (valid && p >= 11) {
+    c = make_ctx(p, i);
+  } else {
+    c.p = p; c.q = 0; c.one = 0; c.r2 = 0; c.orig = i;
+    c.flags = 2u | ((p >= kM31Limit) ? 1u : 0u);  // no sums: special or invalid
+  }
+  P.ctx[slot] = c;
+}
+
+__global__ void k_plan_segments(Plan P) {
+  uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= P.n * P.rows_pp) return;
+  uint32_t slot = idx / P.rows_pp, j = idx - slot * P.rows_pp;
+  const PrimeCtx c = P.ctx[slot];
+  uint64_t lo = 0, cnt = 0;
+  uint32_t tiles = 0;
+  if (!(c.flags & 2u)) {
+    const uint64_t p = c.p;
+    // open interval (x p, y p): s = floor(xn p / xd) + 1 .. floor(yn p / yd)
+    lo = (uint64_t)P.xn[j] * p / P.xd[j] + 1;
+    uint64_t hi = (uint64_t)P.yn[j] * p / P.yd[j] + 1;
+    cnt = hi > lo ? hi - lo : 0;
+    if (cnt) {
+      uint64_t t = (cnt + P.tile_terms - 1) / P.tile_terms;
+      tiles = (uint32_t)(t < 1 ? 1 : (t > P.max_tiles ? P.max_tiles : t));
+    }
+  }
+  P.seg_lo[idx] = lo;
+  P.seg_cnt[idx] = cnt;
+  P.seg_tiles[idx] = tiles;
+}
+
+__global__ void k_plan_split(Plan P) {
+  uint32_t n31 = *P.n31;
+  *P.split_tile = (n31 < P.n) ? P.seg_first[n31 * P.rows_pp] : *P.total_tiles;
+  P.counters[0] = 0;
+  P.counters[1] = 0;
+}
+
+// ------------------------------------------------------------------ tiles
+// Warp-level merge of the per-lane pairs (eqn 3.14) through shuffles.
+__device__ __forceinline__ void warp_merge(const Mont &M, int64_t &a0, int64_t &a1) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    int64_t b0 = __shfl_xor_sync(0xffffffffu, a0, o);
+    int64_t b1 = __shfl_xor_sync(0xffffffffu, a1, o);
+    M.combine(a0, a1, b0, b1);
+  }
+}
+
+// p < 2^30: signed 32-bit Montgomery, R = 2^32.
+template <int ILP, bool CUBES>
+__device__ __forceinline__ void tile_m31(const PrimeCtx &ctx, uint64_t start, uint64_t n,
+                                         int64_t &r0, int64_t &r1) {
+  const int lane = threadIdx.x & 31;
+  const int32_t p = (int32_t)ctx.p;
+  const uint32_t up = (uint32_t)ctx.p;
+  const uint32_t q = (uint32_t)ctx.q;
+  const uint64_t nch = 32 * ILP;
+  const uint64_t len = n / nch;
+  const uint32_t rem = (uint32_t)(n - len * nch);
+  int32_t c0[ILP], c1[ILP], t[ILP], d1[ILP], d2[ILP];
+#pragma unroll
+  for (int k = 0; k < ILP; ++k) {
+    const uint32_t ch = k * 32 + lane;
+    const uint64_t s = start + ch * len + (ch < rem ? ch : rem);
+    const uint64_t s2 = (s * s) % ctx.p;  // s < 2^30: exact in 64 bits
+    if (CUBES) {
+      t[k] = (int32_t)((s2 * s) % ctx.p);              // s^3
+      d1[k] = (int32_t)((3 * s2 + 3 * s + 1) % ctx.p); // (s+1)^3 - s^3
+      d2[k] = (int32_t)((6 * s + 6) % ctx.p);          // second difference
+    } else {
+      t[k] = (int32_t)s2;                              // s^2
+      d1[k] = (int32_t)(2 * s + 1);                    // (s+1)^2 - s^2 <= p (s < p/2)
+      d2[k] = 0;
+    }
+    c0[k] = (int32_t)ctx.one;
+    c1[k] = 0;
+  }
+  auto step = [&](int k) {
+    // eqn 3.12 with REDC against the plain term t
+    const uint32_t tq = (uint32_t)t[k] * q;
+    const int32_t m0 = (int32_t)((uint32_t)c0[k] * tq);
+    const int32_t m1 = (int32_t)((uint32_t)c1[k] * tq);
+    const int32_t h0 = __mulhi(c0[k], t[k]);
+    const int32_t h1 = __mulhi(c1[k], t[k]);
+    const int32_t n1 = h1 - __mulhi(m1, p) + c0[k];
+    c0[k] = h0 - __mulhi(m0, p);
+    c1[k] = n1;
+    // forward differences, each a modular add as min(x, x - p) on unsigned words
+    uint32_t x = (uint32_t)t[k] + (uint32_t)d1[k];
+    t[k] = (int32_t)min(x, x - up);
+    if (CUBES) {
+      x = (uint32_t)d1[k] + (uint32_t)d2[k];
+      d1[k] = (int32_t)min(x, x - up);
+      x = (uint32_t)d2[k] + 6u;
+      d2[k] = (int32_t)min(x, x - up);
+    } else {
+      d1[k] += 2;
+    }
+  };
+#pragma unroll 2
+  for (uint64_t it = 0; it < len; ++it) {
+#pragma unroll
+    for (int k = 0; k < ILP; ++k) step(k);
+  }
+#pragma unroll
+  for (int k = 0; k < ILP; ++k)
+    if ((uint32_t)(k * 32 + lane) < rem) step(k);
+
+  const Mont M(ctx);
+  int64_t a0 = m31_canon(c0[0], p), a1 = m31_canon(c1[0], p);
+#pragma unroll
+  for (int k = 1; k < ILP; ++k) M.combine(a0, a1, m31_canon(c0[k], p), m31_canon(c1[k], p));
+  warp_merge(M, a0, a1);
+  r0 = a0;
+  r1 = a1;
+}
+
+// 2^30 <= p < 2^37: signed 64-bit Montgomery, R = 2^64.
+template <int ILP, bool CUBES>
+__device__ __forceinline__ void tile_m64(const PrimeCtx &ctx, uint64_t start, uint64_t n,
+                                         int64_t &r0, int64_t &r1) {
+  const int lane = threadIdx.x & 31;
+  const Mont M(ctx);
+  const int64_t p = (int64_t)ctx.p;
+  const uint64_t up = ctx.p;
+  const uint64_t q = ctx.q;
+  const uint64_t nch = 32 * ILP;
+  const uint64_t len = n / nch;
+  const uint32_t rem = (uint32_t)(n - len * nch);
+  int64_t c0[ILP], c1[ILP], t[ILP], d1[ILP], d2[ILP];
+#pragma unroll
+  for (int k = 0; k < ILP; ++k) {
+    const uint32_t ch = k * 32 + lane;
+    const uint64_t s = start + ch * len + (ch < rem ? ch : rem);
+    const int64_t s2 = M.mulmod((int64_t)s, (int64_t)s);
+    if (CUBES) {
+      t[k] = M.mulmod(s2, (int64_t)s);
+      d1[k] = (int64_t)((3 * (uint64_t)s2 + 3 * s + 1) % up);
+      d2[k] = (int64_t)((6 * s + 6) % up);
+    } else {
+      t[k] = s2;
+      d1[k] = (int64_t)(2 * s + 1);
+      d2[k] = 0;
+    }
+    c0[k] = (int64_t)ctx.one;
+    c1[k] = 0;
+  }
+  auto step = [&](int k) {
+    const uint64_t tq = (uint64_t)t[k] * q;
+    const int64_t m0 = (int64_t)((uint64_t)c0[k] * tq);
+    const int64_t m1 = (int64_t)((uint64_t)c1[k] * tq);
+    const int64_t h0 = __mul64hi(c0[k], t[k]);
+    const int64_t h1 = __mul64hi(c1[k], t[k]);
+    const int64_t n1 = h1 - __mul64hi(m1, p) + c0[k];
+    c0[k] = h0 - __mul64hi(m0, p);
+    c1[k] = n1;
+    uint64_t x = (uint64_t)t[k] + (uint64_t)d1[k];
+    t[k] = (int64_t)min(x, x - up);
+    if (CUBES) {
+      x = (uint64_t)d1[k] + (uint64_t)d2[k];
+      d1[k] = (int64_t)min(x, x - up);
+      x = (uint64_t)d2[k] + 6u;
+      d2[k] = (int64_t)min(x, x - up);
+    } else {
+      d1[k] += 2;
+    }
+  };
+#pragma unroll 1
+  for (uint64_t it = 0; it < len; ++it) {
+#pragma unroll
+    for (int k = 0; k < ILP; ++k) step(k);
+  }
+#pragma unroll
+  for (int k = 0; k < ILP; ++k)
+    if ((uint32_t)(k * 32 + lane) < rem) step(k);
+
+  int64_t a0 = m64_canon(c0[0], p), a1 = m64_canon(c1[0], p);
+#pragma unroll
+  for (int k = 1; k < ILP; ++k) M.combine(a0, a1, m64_canon(c0[k], p), m64_canon(c1[k], p));
+  warp_merge(M, a0, a1);
+  r0 = a0;
+  r1 = a1;
+}
+
+// ------------------------------------------------------------------ accumulate
+template <bool WIDE, int ILP>
+__global__ void __launch_bounds__(kAccThreads) k_accumulate(Plan P) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t total = *P.total_tiles, split = *P.split_tile;
+  const uint32_t t_begin = WIDE ? split : 0u, t_end = WIDE ? total : split;
+  const uint32_t ntiles = t_end - t_begin;
+  uint32_t *counter = P.counters + (WIDE ? 1 : 0);
+  const uint32_t nsegs = P.n * P.rows_pp;
+  for (;;) {
+    uint32_t g = 0;
+    if (lane == 0) g = atomicAdd(counter, 1u);
+    g = __shfl_sync(0xffffffffu, g, 0);
+    if (g >= ntiles) break;
+    g = t_end - 1 - g;  // largest slots (largest primes of an ascending list) first
+    // segment owning tile g: the last s with seg_first[s] <= g
+    uint32_t lo = 0, hi = nsegs;
+    while (hi - lo > 1) {
+      uint32_t mid = (lo + hi) >> 1;
+      if (__ldg(&P.seg_first[mid]) <= g) lo = mid; else hi = mid;
+    }
+    const uint32_t s = lo;
+    const uint32_t slot = s / P.rows_pp, j = s - slot * P.rows_pp;
+    const PrimeCtx ctx = P.ctx[slot];
+    const uint32_t k = g - P.seg_first[s], T = P.seg_tiles[s];
+    const uint64_t cnt = P.seg_cnt[s];
+    const uint64_t b0 = cnt * k / T, b1 = cnt * (k + 1) / T;
+    const uint64_t start = P.seg_lo[s] + b0, n = b1 - b0;
+    int64_t r0, r1;
+    if (!WIDE) {
+      if (j < P.rows_b) tile_m31<ILP, true>(ctx, start, n, r0, r1);
+      else tile_m31<ILP, false>(ctx, start, n, r0, r1);
+    } else {
+      if (j < P.rows_b) tile_m64<ILP, true>(ctx, start, n, r0, r1);
+      else tile_m64<ILP, false>(ctx, start, n, r0, r1);
+    }
+    if (lane == 0) P.partials[g] = make_ulonglong2((unsigned long long)r0, (unsigned long long)r1);
+  }
+}
+
+// ------------------------------------------------------------------ finalize
+__device__ __forceinline__ int64_t smod64(int64_t c, int64_t p) {
+  int64_t r = c % p;
+  return r < 0 ? r + p : r;
+}
+
+// B_{p-3}, E_{p-3} mod p for p = 5, 7 (where some LHS constants vanish):
+// B_2 = 1/6 = 1 mod 5, E_2 = 1;  B_4 = -1/30 = 3 mod 7, E_4 = 5.
+__device__ __forceinline__ uint64_t special_value(uint64_t p, bool isB) {
+  if (p == 5) return 1;
+  if (p == 7) return isB ? 3 : 5;
+  return WV_RESIDUE_INVALID;
+}
+
+__global__ void k_finalize(Plan P) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nk = (P.rows_b ? 1u : 0u) + (P.rows_e ? 1u : 0u);
+  if (gw >= P.n * nk) return;
+  const uint32_t slot = gw / nk, kk = gw - slot * nk;
+  const bool isB = (P.rows_b != 0) && kk == 0;
+  uint64_t *out = isB ? P.out_b : P.out_e;
+  if (!out) return;
+  const PrimeCtx ctx = P.ctx[slot];
+  if (ctx.flags & 2u) {
+    if (lane == 0) out[ctx.orig] = special_value(ctx.p, isB);
+    return;
+  }
+  const Mont M(ctx);
+  const int64_t p = (int64_t)ctx.p;
+  const uint32_t nrows = isB ? P.rows_b : P.rows_e;
+  const uint32_t r0 = isB ? 0u : P.rows_b;
+  const uint32_t seg0 = slot * P.rows_pp + r0;
+  int64_t N = 0, D = M.one;  // running fraction N / D = sum coef_j c1_j / c0_j
+  for (uint32_t j = lane; j < nrows; j += 32) {
+    const uint32_t s = seg0 + j;
+    int64_t C0 = M.one, C1 = 0;
+    const uint32_t f = P.seg_first[s], T = P.seg_tiles[s];
+    for (uint32_t g = f; g < f + T; ++g) {
+      const ulonglong2 v = P.partials[g];
+      M.combine(C0, C1, (int64_t)v.x, (int64_t)v.y);
+    }
+    const int64_t aM = M.to_mont(smod64(P.coef[r0 + j], p));
+    const int64_t X = M.mul(aM, C1);  // coef * C1 at C1's scale
+    N = M.add(M.mul(N, C0), M.mul(X, D));
+    D = M.mul(D, C0);
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const int64_t N2 = __shfl_xor_sync(0xffffffffu, N, o);
+    const int64_t D2 = __shfl_xor_sync(0xffffffffu, D, o);
+    N = M.add(M.mul(N, D2), M.mul(N2, D));
+    D = M.mul(D, D2);
+  }
+  if (lane == 0) {
+    const int64_t L = smod64(isB ? P.lhs_b : P.lhs_e, p);
+    if (L == 0 || D == 0) {
+      out[ctx.orig] = WV_RESIDUE_INVALID;
+      return;
+    }
+    // residue = (N/D) R^-1 / L = N / (D L R)
+    const int64_t DLR = M.mul(D, M.to_mont(M.to_mont(L)));  // D * L R^2 * R^-1
+    const int64_t inv = M.pow(M.to_mont(DLR), (uint64_t)(p - 2));  // (DLR)^-1 R
+    out[ctx.orig] = (uint64_t)M.mul(N, inv);                 // N (DLR)^-1
+  }
+}
+
+// ------------------------------------------------------------------ host
+template <bool WIDE>
+static wv_status launch_accumulate(const Plan &P, const ResidueConfig &cfg, int sms, cudaStream_t s) {
+  const char *name = WIDE ? "accumulate_m64" : "accumulate_m31";
+  void (*kern)(Plan) = nullptr;
+  switch (cfg.ilp) {
+    case 1: kern = k_accumulate<WIDE, 1>; break;
+    case 2: kern = k_accumulate<WIDE, 2>; break;
+    default: kern = k_accumulate<WIDE, 4>; break;
+  }
+  int occ = cfg.blocks_per_sm;
+  if (occ <= 0) {
+    WV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kAccThreads, 0));
+    if (occ < 1) occ = 1;
+  }
+  WV_LAUNCH(name, kern, (unsigned)(sms * occ), kAccThreads, 0, s, P);
+  return WV_OK;
+}
+
+wv_status residues_device(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,
+                          uint64_t *d_out_e, const ResidueConfig &cfg, cudaStream_t s) {
+  if (n == 0) return WV_OK;
+  if (!d_primes) return set_error(WV_EINVAL, "d_primes is NULL");
+  DeviceState *dev = nullptr;
+  WV_CHECK(device_state(&dev));
+  Plan P;
+  memset(&P, 0, sizeof P);
+  const bool do_b = cfg.cong_b >= 0 && d_out_b;
+  const bool do_e = cfg.cong_e >= 0 && d_out_e;
+  if (!do_b && !do_e) return WV_OK;
+  uint32_t r = 0;
+  if (do_b) {
+    const WvCongruence &c = kWvCongruences[cfg.cong_b];
+    for (int j = 0; j < c.nrows; ++j, ++r) {
+      const WvRow &w = kWvRows[c.row_offset + j];
+      P.xn[r] = w.xn; P.xd[r] = w.xd; P.yn[r] = w.yn; P.yd[r] = w.yd; P.coef[r] = w.coef;
+    }
+    P.rows_b = c.nrows;
+    P.lhs_b = c.lhs;
+  }
+  if (do_e) {
+    const WvCongruence &c = kWvCongruences[cfg.cong_e];
+    for (int j = 0; j < c.nrows; ++j, ++r) {
+      const WvRow &w = kWvRows[c.row_offset + j];
+      P.xn[r] = w.xn; P.xd[r] = w.xd; P.yn[r] = w.yn; P.yd[r] = w.yd; P.coef[r] = w.coef;
+    }
+    P.rows_e = c.nrows;
+    P.lhs_e = c.lhs;
+  }
+  P.rows_pp = r;
+  P.tile_terms = (uint32_t)(cfg.tile_terms > 0 ? cfg.tile_terms : 65536);
+  P.max_tiles = (uint32_t)(cfg.max_tiles > 0 ? cfg.max_tiles : 32);
+
+  const uint32_t chunk = (uint32_t)(n < kChunkPrimes ? n : kChunkPrimes);
+  const size_t nseg = (size_t)chunk * P.rows_pp;
+  Scratch sc(s);
+  uint32_t *u32tmp = nullptr, *scal = nullptr;
+  WV_CHECK(sc.get(&P.ctx, chunk));
+  WV_CHECK(sc.get(&P.flag, chunk));
+  WV_CHECK(sc.get(&P.pos, chunk));
+  WV_CHECK(sc.get(&P.seg_lo, nseg));
+  WV_CHECK(sc.get(&P.seg_cnt, nseg));
+  WV_CHECK(sc.get(&P.seg_tiles, nseg));
+  WV_CHECK(sc.get(&P.seg_first, nseg));
+  WV_CHECK(sc.get(&P.partials, nseg * P.max_tiles));
+  WV_CHECK(sc.get(&u32tmp, scan_tmp_elems(nseg)));
+  WV_CHECK(sc.get(&scal, 8));
+  P.n31 = scal + 0;
+  P.total_tiles = scal + 1;
+  P.split_tile = scal + 2;
+  P.counters = scal + 4;
+
+  for (size_t base = 0; base < n; base += chunk) {
+    P.n = (uint32_t)((n - base) < chunk ? (n - base) : chunk);
+    P.primes = d_primes + base;
+    P.out_b = do_b ? d_out_b + base : nullptr;
+    P.out_e = do_e ? d_out_e + base : nullptr;
+    const unsigned gp = (P.n + 255) / 256;
+    WV_LAUNCH("plan_prime", k_plan_prime, gp, 256, 0, s, P);
+    WV_CHECK(scan_exclusive_u32(P.flag, P.pos, P.n, P.n31, u32tmp, s));
+    WV_LAUNCH("plan_scatter", k_plan_scatter, gp, 256, 0, s, P);
+    const size_t ns = (size_t)P.n * P.rows_pp;
+    WV_LAUNCH("plan_segments", k_plan_segments, (unsigned)((ns + 255) / 256), 256, 0, s, P);
+    WV_CHECK(scan_exclusive_u32(P.seg_tiles, P.seg_first, ns, P.total_tiles, u32tmp, s));
+    WV_LAUNCH("plan_split", k_plan_split, 1, 1, 0, s, P);
+    WV_CHECK(launch_accumulate<false>(P, cfg, dev->sms, s));
+    WV_CHECK(launch_accumulate<true>(P, cfg, dev->sms, s));
+    const uint32_t nk = (do_b ? 1 : 0) + (do_e ? 1 : 0);
+    const size_t warps = (size_t)P.n * nk;
+    WV_LAUNCH("finalize", k_finalize, (unsigned)((warps * 32 + 255) / 256), 256, 0, s, P);
+  }
+  return WV_OK;
+}
+
+}  // namespace wv
+
+using namespace wv;
+
+extern "C" {
+
+wv_status wv_residues_ex(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,
+                         uint64_t *d_out_e, const wv_options *opt, wv_stream stream) {
+  clear_error();
+  if (n > 0 && !d_primes) return set_error(WV_EINVAL, "d_primes is NULL");
+  if (n > ((size_t)1 << 40)) return set_error(WV_EINVAL, "n too large");
+  ResidueConfig cfg;
+  WV_CHECK(resolve_config(opt, d_out_b != nullptr, d_out_e != nullptr, &cfg));
+  return residues_device(d_primes, n, d_out_b, d_out_e, cfg, (cudaStream_t)stream);
+}
+
+wv_status wv_residues_pm3(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,
+                          uint64_t *d_out_e, wv_stream stream) {
+  return wv_residues_ex(d_primes, n, d_out_b, d_out_e, nullptr, stream);
+}
+
+wv_status wv_bernoulli_pm3(const uint64_t *d_primes, size_t n, uint64_t *d_out, wv_stream stream) {
+  if (n > 0 && !d_out) {
+    clear_error();
+    return set_error(WV_EINVAL, "d_out is NULL");
+  }
+  return wv_residues_ex(d_primes, n, d_out, nullptr, nullptr, stream);
+}
+
+wv_status wv_euler_pm3(const uint64_t *d_primes, size_t n, uint64_t *d_out, wv_stream stream) {
+  if (n > 0 && !d_out) {
+    clear_error();
+    return set_error(WV_EINVAL, "d_out is NULL");
+  }
+  return wv_residues_ex(d_primes, n, nullptr, d_out, nullptr, stream);
+}
+
+}  // extern "C"

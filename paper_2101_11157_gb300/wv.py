@@ -1,0 +1,278 @@
+"""Thin Python binding of the C ABI in ``include/wv.h`` (ctypes).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Functions carry the C names; device buffers are torch tensors
+(int64 or uint64 storage, contiguous, on the current CUDA device) and the
+stream defaults to torch's current stream.  A non-OK status raises
+``WvError``.  There is no CPU fallback: if the library cannot be built or
+loaded, the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+WV_OK, WV_EINVAL, WV_ENOMEM, WV_ERANGE, WV_ECUDA, WV_ETIMEOUT, WV_ECANCELLED, WV_EBUSY = range(8)
+WV_P_MAX = 1 << 37
+WV_RESIDUE_INVALID = (1 << 64) - 1
+WV_KIND_BERNOULLI, WV_KIND_EULER, WV_KIND_NEAR_B, WV_KIND_NEAR_E = 1, 2, 4, 8
+
+_STATUS = {0: "WV_OK", 1: "WV_EINVAL", 2: "WV_ENOMEM", 3: "WV_ERANGE", 4: "WV_ECUDA",
+           5: "WV_ETIMEOUT", 6: "WV_ECANCELLED", 7: "WV_EBUSY"}
+
+
+class WvError(RuntimeError):
+    def __init__(self, status: int, msg: str, count: int | None = None):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+        self.count = count
+
+
+class wv_hit(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_uint64), ("kind", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
+
+
+class wv_options(ctypes.Structure):
+    _fields_ = [("cong_b", ctypes.c_int), ("cong_e", ctypes.c_int), ("block", ctypes.c_int),
+                ("ilp", ctypes.c_int), ("tile_terms", ctypes.c_int), ("max_tiles", ctypes.c_int),
+                ("blocks_per_sm", ctypes.c_int), ("reserved", ctypes.c_int * 9)]
+
+
+_lock = threading.Lock()
+_lib = None
+_u64, _sz, _vp, _i32 = ctypes.c_uint64, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_int
+_pu64, _psz = ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_size_t)
+
+_SIGS = {
+    "wv_version": ([], ctypes.c_char_p),
+    "wv_last_error": ([], ctypes.c_char_p),
+    "wv_sieve": ([_u64, _u64, _vp, _sz, _psz, _vp], _i32),
+    "wv_sieve_count": ([_u64, _u64, _pu64, _vp], _i32),
+    "wv_bernoulli_pm3": ([_vp, _sz, _vp, _vp], _i32),
+    "wv_euler_pm3": ([_vp, _sz, _vp, _vp], _i32),
+    "wv_residues_pm3": ([_vp, _sz, _vp, _vp, _vp], _i32),
+    "wv_residues_ex": ([_vp, _sz, _vp, _vp, ctypes.POINTER(wv_options), _vp], _i32),
+    "wv_search": ([_u64, _u64, _vp, _sz, _psz, _vp], _i32),
+    "wv_search_ex": ([_u64, _u64, _u64, _vp, _sz, _psz, _vp, _vp, _vp, _sz, _psz,
+                      ctypes.POINTER(wv_options), _vp], _i32),
+    "wv_congruence_count": ([], _i32),
+    "wv_congruence_info": ([_i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32),
+                            ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_char_p)], _i32),
+    "wv_congruence_row": ([_i32, _i32, ctypes.POINTER(ctypes.c_int64)] +
+                          [ctypes.POINTER(ctypes.c_uint32)] * 4, _i32),
+    "wv_profile_enable": ([_i32], None),
+    "wv_profile_reset": ([], None),
+    "wv_profile_collect": ([], _i32),
+    "wv_profile_kernels": ([], _i32),
+    "wv_profile_get": ([_i32, ctypes.POINTER(ctypes.c_char_p), _pu64,
+                        ctypes.POINTER(ctypes.c_double)], _i32),
+    "wv_profile_launches": ([], _u64),
+    "wv_count_terms": ([_pu64, _sz, _i32, _i32, _pu64, _pu64], _i32),
+    "wv_diag_throughput": ([_i32, _i32, ctypes.POINTER(ctypes.c_double)], _i32),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Build (if needed) and load libwv.so; raises if that is impossible."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def declared_symbols():
+    return sorted(_SIGS)
+
+
+def _check(st: int, count: int | None = None):
+    if st != WV_OK:
+        msg = load().wv_last_error().decode()
+        raise WvError(st, msg, count)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    import torch
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if t.dtype not in (torch.int64, torch.uint64):
+        raise TypeError("expected an int64/uint64 tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _options(opt: dict | None):
+    if not opt:
+        return None
+    o = wv_options()
+    o.cong_b = o.cong_e = -1
+    for k, v in opt.items():
+        setattr(o, k, int(v))
+    return ctypes.byref(o)
+
+
+# ------------------------------------------------------------------ entry points
+def wv_version() -> str:
+    return load().wv_version().decode()
+
+
+def wv_last_error() -> str:
+    return load().wv_last_error().decode()
+
+
+def wv_sieve(lo: int, hi: int, d_out, stream=None) -> int:
+    """Primes of [lo, hi) into d_out (device); returns the count."""
+    n = ctypes.c_size_t(0)
+    cap = 0 if d_out is None else d_out.numel()
+    st = load().wv_sieve(lo, hi, _ptr(d_out) if cap else None, cap, ctypes.byref(n), _stream(stream))
+    _check(st, n.value)
+    return n.value
+
+
+def wv_sieve_count(lo: int, hi: int, stream=None) -> int:
+    c = ctypes.c_uint64(0)
+    _check(load().wv_sieve_count(lo, hi, ctypes.byref(c), _stream(stream)))
+    return c.value
+
+
+def wv_bernoulli_pm3(d_primes, d_out, stream=None) -> None:
+    _check(load().wv_bernoulli_pm3(_ptr(d_primes), d_primes.numel(), _ptr(d_out), _stream(stream)))
+
+
+def wv_euler_pm3(d_primes, d_out, stream=None) -> None:
+    _check(load().wv_euler_pm3(_ptr(d_primes), d_primes.numel(), _ptr(d_out), _stream(stream)))
+
+
+def wv_residues_pm3(d_primes, d_out_b, d_out_e, stream=None) -> None:
+    _check(load().wv_residues_pm3(_ptr(d_primes), d_primes.numel(), _ptr(d_out_b), _ptr(d_out_e),
+                                  _stream(stream)))
+
+
+def wv_residues_ex(d_primes, d_out_b, d_out_e, options: dict | None = None, stream=None) -> None:
+    _check(load().wv_residues_ex(_ptr(d_primes), d_primes.numel(), _ptr(d_out_b), _ptr(d_out_e),
+                                 _options(options), _stream(stream)))
+
+
+def wv_search(lo: int, hi: int, d_hits, stream=None) -> int:
+    """Hits of [lo, hi) into d_hits (an int64 tensor of shape (cap, 2) holding
+    wv_hit records); returns the hit count."""
+    n = ctypes.c_size_t(0)
+    cap = 0 if d_hits is None else d_hits.shape[0]
+    st = load().wv_search(lo, hi, _ptr(d_hits) if cap else None, cap, ctypes.byref(n), _stream(stream))
+    _check(st, n.value)
+    return n.value
+
+
+def wv_search_ex(lo: int, hi: int, near: int, d_hits, d_primes=None, d_res_b=None, d_res_e=None,
+                 options: dict | None = None, stream=None):
+    """Returns (n_hits, n_primes)."""
+    nh, npr = ctypes.c_size_t(0), ctypes.c_size_t(0)
+    cap = 0 if d_hits is None else d_hits.shape[0]
+    caps = [t.numel() for t in (d_primes, d_res_b, d_res_e) if t is not None]
+    cap_p = min(caps) if caps else 0
+    st = load().wv_search_ex(lo, hi, near, _ptr(d_hits) if cap else None, cap, ctypes.byref(nh),
+                             _ptr(d_primes), _ptr(d_res_b), _ptr(d_res_e), cap_p,
+                             ctypes.byref(npr), _options(options), _stream(stream))
+    _check(st, nh.value)
+    return nh.value, npr.value
+
+
+def wv_congruence_count() -> int:
+    return load().wv_congruence_count()
+
+
+def wv_congruence_info(cid: int):
+    """(name, kind, n_rows, lhs) -- kind 0 = B_{p-3}, 1 = E_{p-3}."""
+    k, n, l, nm = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64(), ctypes.c_char_p()
+    _check(load().wv_congruence_info(cid, ctypes.byref(k), ctypes.byref(n), ctypes.byref(l),
+                                     ctypes.byref(nm)))
+    return nm.value.decode(), k.value, n.value, l.value
+
+
+def wv_congruence_row(cid: int, row: int):
+    """(coef, xn, xd, yn, yd)."""
+    c = ctypes.c_int64()
+    v = [ctypes.c_uint32() for _ in range(4)]
+    _check(load().wv_congruence_row(cid, row, ctypes.byref(c), *[ctypes.byref(x) for x in v]))
+    return (c.value,) + tuple(x.value for x in v)
+
+
+def wv_count_terms(primes, cong_b: int = -1, cong_e: int = -1):
+    """(terms_b, terms_e) for a host list of primes; -2 skips a kind."""
+    a = np.ascontiguousarray(np.asarray(primes, dtype=np.uint64))
+    tb, te = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load().wv_count_terms(a.ctypes.data_as(_pu64), a.size, cong_b, cong_e,
+                                 ctypes.byref(tb), ctypes.byref(te)))
+    return tb.value, te.value
+
+
+def wv_profile_enable(on: bool = True) -> None:
+    load().wv_profile_enable(1 if on else 0)
+
+
+def wv_profile_reset() -> None:
+    load().wv_profile_reset()
+
+
+def wv_profile_collect() -> dict:
+    """Fold pending events; returns {kernel: (launches, total_ms)}."""
+    lib = load()
+    _check(lib.wv_profile_collect())
+    out = {}
+    for i in range(lib.wv_profile_kernels()):
+        nm, la, ms = ctypes.c_char_p(), ctypes.c_uint64(), ctypes.c_double()
+        _check(lib.wv_profile_get(i, ctypes.byref(nm), ctypes.byref(la), ctypes.byref(ms)))
+        out[nm.value.decode()] = (la.value, ms.value)
+    return out
+
+
+def wv_profile_launches() -> int:
+    return int(load().wv_profile_launches())
+
+
+def wv_profile_kernels() -> int:
+    return int(load().wv_profile_kernels())
+
+
+def wv_profile_get(idx: int):
+    """(name, launches, total_ms) of profiled kernel `idx`."""
+    nm, la, ms = ctypes.c_char_p(), ctypes.c_uint64(), ctypes.c_double()
+    _check(load().wv_profile_get(idx, ctypes.byref(nm), ctypes.byref(la), ctypes.byref(ms)))
+    return nm.value.decode(), la.value, ms.value
+
+
+DIAG_OPS = {"imad": 0, "imad_hi": 1, "imad_wide": 2, "iadd": 3, "imnmx": 4, "term_b": 5, "term_e": 6}
+
+
+def wv_diag_throughput(op, iters: int = 4096) -> float:
+    """Measured lane-operations (or terms) per SM per clock for diagnostic `op`."""
+    v = ctypes.c_double()
+    _check(load().wv_diag_throughput(DIAG_OPS.get(op, op), iters, ctypes.byref(v)))
+    return v.value

@@ -1,0 +1,259 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle, element
+by element and bit-exact (residues are exact integers; any correct evaluation
+order gives the same value), plus the paper's printed values and properties
+that hold at any size."""
+import os
+
+import numpy as np
+import pytest
+
+from conftest import read_golden
+from paper_2101_11157_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2101_11157_gb300 import api, wv  # noqa: E402
+
+INVALID = (1 << 64) - 1
+
+
+def u64(t):
+    return api.to_u64(t)
+
+
+def gpu_residues(primes, options=None):
+    d = torch.from_numpy(np.asarray(primes, dtype=np.uint64).view(np.int64)).cuda()
+    rb, re = api.residues(d, options=options)
+    torch.cuda.synchronize()
+    return u64(rb), u64(re)
+
+
+def cong_id(name):
+    for cid in range(wv.wv_congruence_count()):
+        if wv.wv_congruence_info(cid)[0] == name:
+            return cid
+    raise KeyError(name)
+
+
+# ---------------------------------------------------------------- sieve (a1)
+@pytest.mark.parametrize("lo,hi", [(0, 50_000), (5, 50_000), W.P1E9_WINDOW, W.TOP_WINDOW,
+                                   (2**31 - 5000, 2**31 + 5000), (2**37 - 3000, 2**37),
+                                   (0, 3), (2, 3), (24, 29), (10, 10), (1, 2)])
+def test_sieve_matches_oracle(orc, lo, hi):
+    got = u64(api.sieve(lo, hi))
+    ref = orc.sieve(lo, hi)
+    assert np.array_equal(got, ref)
+
+
+def test_sieve_multi_segment(orc):
+    lo, hi = 10**9, 10**9 + 3 * (1 << 19) + 12345  # several segments and a ragged tail
+    assert np.array_equal(u64(api.sieve(lo, hi)), orc.sieve(lo, hi))
+    assert wv.wv_sieve_count(lo, hi) == orc.sieve(lo, hi).size
+
+
+def test_sieve_capacity_error():
+    out = torch.empty(10, dtype=torch.int64, device="cuda")
+    with pytest.raises(wv.WvError) as e:
+        wv.wv_sieve(0, 1000, out)
+    assert e.value.status == wv.WV_ERANGE and e.value.count == 168
+    assert list(u64(out)) == [2, 3, 5, 7, 11, 13, 17, 19, 23, 29]
+
+
+def test_prime_count_below_1e11():
+    # 4118054811 primes with 5 <= p < 1e11 (Sec. 3, "Results")
+    rows = read_golden("prime_counts.txt")
+    for lo, hi, cnt in rows:
+        assert wv.wv_sieve_count(int(lo), int(hi)) == int(cnt)
+
+
+# ---------------------------------------------------------------- residues
+def test_small_window_all_primes(orc):
+    """All primes 5 <= p < 50000 against the oracle."""
+    ps = orc.sieve(*W.SMALL_WINDOW)
+    assert ps.size == 5131
+    gb, ge = gpu_residues(ps)
+    ob, oe = orc.residues(ps)
+    assert np.array_equal(gb, ob)
+    assert np.array_equal(ge, oe)
+
+
+def test_definition_level_small(orc):
+    ps = [p for p in range(5, 1000) if W.is_prime(p)]
+    gb, ge = gpu_residues(ps)
+    ob, oe = orc.residues(ps, method_b="def", method_e="def")
+    assert np.array_equal(gb, ob) and np.array_equal(ge, oe)
+
+
+def test_p1e9_window_full_launch_sampled_against_oracle(orc):
+    """The 1e5-wide window at 1.06e9 in the benchmark's launch configuration:
+    every prime computed on the GPU, a seeded sample checked by the oracle."""
+    ps = u64(api.sieve(*W.P1E9_WINDOW))
+    assert ps.size == orc.sieve(*W.P1E9_WINDOW).size
+    gb, ge = gpu_residues(ps)
+    k = int(os.environ.get("WV_ORACLE_SAMPLE", "24"))
+    sample = W.seeded_subset(ps, k, seed=2021, must_include=[W.KNOWN_VANDIVER_IN_P1E9])
+    ob, oe = orc.residues(sample)
+    idx = np.searchsorted(ps, sample)
+    assert np.array_equal(gb[idx], ob)
+    assert np.array_equal(ge[idx], oe)
+    # the known Vandiver prime in the window
+    assert ge[np.searchsorted(ps, W.KNOWN_VANDIVER_IN_P1E9)] == 0
+
+
+def test_p1e9_window_cross_congruences():
+    """Every congruence family member gives the identical residue (Sec. 3, 5)."""
+    ps = u64(api.sieve(*W.P1E9_WINDOW))
+    ref_b, ref_e = gpu_residues(ps)
+    for nb, ne in (("BB1", "EE3"), ("BB2", "EE5"), ("BB6", "EE9"), ("BB9", "EE16"),
+                   ("BB16", "EE24"), ("BB22", "EE33")):
+        gb, ge = gpu_residues(ps, {"cong_b": cong_id(nb), "cong_e": cong_id(ne)})
+        assert np.array_equal(gb, ref_b), nb
+        assert np.array_equal(ge, ref_e), ne
+
+
+def test_near_miss_tables():
+    """Tables 1 and 2 of the paper, p up to 7.8e10: symmetric residues as printed."""
+    for fname, which in (("near_miss_bernoulli.txt", 0), ("near_miss_euler.txt", 1)):
+        rows = [(int(p), int(v)) for p, v in read_golden(fname)]
+        gb, ge = gpu_residues([p for p, _ in rows])
+        got = gb if which == 0 else ge
+        for (p, v), r in zip(rows, got):
+            assert api.symmetric(int(r), p) == v, (fname, p)
+
+
+def test_wide_path_boundary(orc):
+    """Primes on both sides of the 2^30 switch between 32- and 64-bit words."""
+    below = [p for p in range(2**30 - 200, 2**30) if W.is_prime(p)][-2:]
+    above = [p for p in range(2**30, 2**30 + 200) if W.is_prime(p)][:2]
+    ps = below + above
+    gb, ge = gpu_residues(ps)
+    ob, oe = orc.residues(ps)
+    assert np.array_equal(gb, ob) and np.array_equal(ge, oe)
+
+
+def test_top_window_cross_congruences():
+    """[1e11 - 1e4, 1e11): 64-bit path, two independent congruences per kind."""
+    ps = u64(api.sieve(*W.TOP_WINDOW))
+    assert ps.size == 391
+    sub = W.top_window_subset(seed=5, k=8)
+    assert np.all(np.isin(sub, ps))
+    gb, ge = gpu_residues(ps)
+    ab, ae = gpu_residues(ps, {"cong_b": cong_id("BB22"), "cong_e": cong_id("EE24")})
+    assert np.array_equal(gb, ab) and np.array_equal(ge, ae)
+    assert np.all(gb < ps) and np.all(ge < ps)
+    assert not np.any(gb == 0) and not np.any(ge == 0)  # Theorem 1.1
+
+
+@pytest.mark.skipif(not os.environ.get("WV_SLOW_ORACLE"), reason="oracle needs ~20 core-minutes per prime at 1e11")
+def test_top_window_oracle_spot_check(orc):
+    sub = W.top_window_subset(seed=5, k=int(os.environ.get("WV_SLOW_ORACLE_K", "2")))
+    gb, ge = gpu_residues(sub)
+    ob, oe = orc.residues(sub)
+    assert np.array_equal(gb, ob) and np.array_equal(ge, oe)
+
+
+def test_edge_cases(orc):
+    ps = [5, 7, 11, 13, 17, 19, 23]
+    gb, ge = gpu_residues(ps)
+    ob, oe = orc.residues(ps, method_b="def", method_e="def")
+    assert np.array_equal(gb, ob) and np.array_equal(ge, oe)
+    # invalid inputs give the sentinel, valid neighbours are unaffected
+    bad = [0, 1, 2, 3, 4, 10, 2**37 + 1, 2**37 - 1 + 2**37, 29]
+    gb, ge = gpu_residues(bad)
+    assert list(gb[:8]) == [INVALID] * 8 and list(ge[:8]) == [INVALID] * 8
+    assert gb[8] == orc.bernoulli_pm3(29) and ge[8] == orc.euler_pm3(29)
+    # empty input
+    e = torch.empty(0, dtype=torch.int64, device="cuda")
+    wv.wv_residues_pm3(e, e, e)
+
+
+def test_launch_shapes_agree():
+    """Ragged tiles, many tiles per sum, ILP 1/2/4 and the single-kind entry
+    points all give the identical residues."""
+    ps = np.concatenate([u64(api.sieve(10**6, 10**6 + 3000)), u64(api.sieve(2**31, 2**31 + 400))])
+    ref_b, ref_e = gpu_residues(ps)
+    for opt in ({"ilp": 1}, {"ilp": 4}, {"tile_terms": 97, "max_tiles": 4096},
+                {"tile_terms": 1 << 20, "max_tiles": 1}, {"blocks_per_sm": 1}):
+        gb, ge = gpu_residues(ps, opt)
+        assert np.array_equal(gb, ref_b), opt
+        assert np.array_equal(ge, ref_e), opt
+    d = torch.from_numpy(ps.view(np.int64)).cuda()
+    ob, oe = torch.empty_like(d), torch.empty_like(d)
+    wv.wv_bernoulli_pm3(d, ob)
+    wv.wv_euler_pm3(d, oe)
+    torch.cuda.synchronize()
+    assert np.array_equal(u64(ob), ref_b) and np.array_equal(u64(oe), ref_e)
+
+
+def test_chunked_call_many_primes(orc):
+    """More primes than one internal launch sequence holds (16384)."""
+    ps = u64(api.sieve(10**5, 10**5 + 500_000))
+    assert ps.size > 16384
+    gb, ge = gpu_residues(ps)
+    sample = W.seeded_subset(ps, 64, seed=9)
+    ob, oe = orc.residues(sample)
+    idx = np.searchsorted(ps, sample)
+    assert np.array_equal(gb[idx], ob) and np.array_equal(ge[idx], oe)
+    # order of the input does not matter
+    perm = np.random.default_rng(1).permutation(ps.size)
+    pb, pe = gpu_residues(ps[perm])
+    assert np.array_equal(pb, gb[perm]) and np.array_equal(pe, ge[perm])
+
+
+def test_host_buffer_path(orc):
+    ps = orc.sieve(10**7, 10**7 + 5000)
+    hb, he = api.residues_host(ps)
+    ob, oe = orc.residues(ps)
+    assert np.array_equal(hb, ob) and np.array_equal(he, oe)
+
+
+# ---------------------------------------------------------------- search (a7)
+def _known():
+    return [(k, int(p)) for k, p in read_golden("known_primes.txt")]
+
+
+def test_search_known_primes_below_2e7():
+    hits = api.search(5, 2 * 10**7)
+    w = sorted(p for p, k in hits if k & wv.WV_KIND_BERNOULLI)
+    v = sorted(p for p, k in hits if k & wv.WV_KIND_EULER)
+    assert w == sorted(p for k, p in _known() if k == "W" and p < 2e7)
+    assert v == sorted(p for k, p in _known() if k == "V" and p < 2e7)
+    assert 2124679 not in v
+
+
+def test_search_windows_around_large_known_primes():
+    for kind, p in _known():
+        if p < 2e7 or kind == "notV":
+            continue
+        hits = api.search(p - 5000, p + 5000)
+        bit = wv.WV_KIND_BERNOULLI if kind == "W" else wv.WV_KIND_EULER
+        assert (p, bit) in [(q, k & bit) for q, k in hits]
+
+
+def test_search_p1e9_window_hits_and_near_misses(orc):
+    hits = api.search(*W.P1E9_WINDOW)
+    assert hits == [(W.KNOWN_VANDIVER_IN_P1E9, wv.WV_KIND_EULER)]
+    near = api.search(*W.P1E9_WINDOW, near=50)
+    # Tables 1-2 are complete over (1e9, 1e11): only 1062232319 lies in this window
+    assert [p for p, _ in near] == [W.KNOWN_VANDIVER_IN_P1E9]
+    assert near[0][1] == wv.WV_KIND_EULER | wv.WV_KIND_NEAR_E
+    hits, pr, rb, re = api.search(*W.P1E9_WINDOW, with_residues=True)
+    ps = u64(pr)
+    assert np.array_equal(ps, orc.sieve(*W.P1E9_WINDOW))
+    gb, ge = gpu_residues(ps)
+    assert np.array_equal(u64(rb), gb) and np.array_equal(u64(re), ge)
+
+
+def test_search_near_miss_table_windows():
+    """Each row of Tables 1-2 below 1e10 is found as a near miss in a window around it."""
+    for fname, bit in (("near_miss_bernoulli.txt", wv.WV_KIND_NEAR_B),
+                       ("near_miss_euler.txt", wv.WV_KIND_NEAR_E)):
+        for p, v in [(int(a), int(b)) for a, b in read_golden(fname)]:
+            if p > 1e10:
+                continue
+            near = api.search(p - 2000, p + 2000, near=50)
+            assert (p, bit) in [(q, k & bit) for q, k in near]

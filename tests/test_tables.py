@@ -1,0 +1,105 @@
+"""The library's congruence tables (read through the C ABI, host only, no GPU)
+checked against the oracle's definitions of B_{p-3}, E_{p-3} mod p for every
+prime 11 <= p < 700, and against the costs the paper states for each
+congruence (Sec. 2-5).  Transcription slips in an endpoint, a coefficient or a
+sign fail one or the other."""
+from fractions import Fraction
+
+import pytest
+
+from paper_2101_11157_gb300 import wv
+from paper_2101_11157_gb300.workloads import is_prime
+
+# congruence -> (eqn, family, cost / p) as stated in the paper
+PAPER = {
+    "BB1": ("3.2", 0, Fraction(1, 12)),
+    "BB2": ("3.1", 0, Fraction(1, 15)),
+    "BB6": ("3.3", 0, Fraction(5, 96)),
+    "BB9": ("3.4", 0, Fraction(1, 20)),
+    "BB16": ("3.5", 0, Fraction(1, 24)),
+    "BB22": ("3.6", 0, Fraction(3, 80)),
+    "BB30": ("3.7", 0, Fraction(227, 6480)),
+    "EE3": ("5.1", 1, Fraction(3, 16)),
+    "EE5": ("5.2", 1, Fraction(9, 64)),
+    "EE9": ("5.3", 1, Fraction(43, 384)),
+    "EE16": ("5.4", 1, Fraction(205, 2304)),
+    "EE24": ("5.5", 1, Fraction(115, 1536)),
+    "EE33": ("5.6", 1, Fraction(27, 512)),
+}
+
+
+def tables():
+    out = {}
+    for cid in range(wv.wv_congruence_count()):
+        name, kind, n, lhs = wv.wv_congruence_info(cid)
+        rows = [wv.wv_congruence_row(cid, j) for j in range(n)]
+        out[name] = (cid, kind, lhs, rows)
+    return out
+
+
+@pytest.fixture(scope="module")
+def T():
+    return tables()
+
+
+def test_all_congruences_present(T):
+    assert set(T) == set(PAPER)
+    assert len(T) == 13
+    assert [len(T[k][3]) for k in ("BB1", "BB2", "BB6", "BB9", "BB16", "BB22", "BB30")] == \
+        [1, 2, 6, 9, 16, 22, 30]
+    assert [len(T[k][3]) for k in ("EE3", "EE5", "EE9", "EE16", "EE24", "EE33")] == \
+        [3, 5, 9, 16, 24, 33]
+
+
+@pytest.mark.parametrize("name", sorted(PAPER))
+def test_cost_matches_paper(T, name):
+    cid, kind, lhs, rows = T[name]
+    assert kind == PAPER[name][1]
+    cost = sum(Fraction(yn, yd) - Fraction(xn, xd) for _, xn, xd, yn, yd in rows)
+    assert cost == PAPER[name][2]
+    # intervals are disjoint, ascending, inside [0, 1/2], 2,3,5-smooth denominators
+    prev = Fraction(0)
+    for _, xn, xd, yn, yd in rows:
+        x, y = Fraction(xn, xd), Fraction(yn, yd)
+        assert prev <= x < y <= Fraction(1, 2)
+        prev = y
+        for d in (xd, yd):
+            for q in (2, 3, 5):
+                while d % q == 0:
+                    d //= q
+            assert d == 1
+
+
+def _S(p, x, y, e):
+    lo = x.numerator * p // x.denominator + 1
+    hi = (y.numerator * p + y.denominator - 1) // y.denominator - 1
+    return sum(pow(s, -e, p) for s in range(lo, hi + 1)) % p
+
+
+@pytest.mark.parametrize("name", sorted(PAPER))
+def test_congruence_gives_definition(T, orc, name):
+    cid, kind, lhs, rows = T[name]
+    e = 3 if kind == 0 else 2
+    for p in [p for p in range(11, 700) if is_prime(p)]:
+        if lhs % p == 0:
+            continue
+        rhs = sum(c * _S(p, Fraction(xn, xd), Fraction(yn, yd), e) for c, xn, xd, yn, yd in rows)
+        val = rhs * pow(lhs, -1, p) % p
+        ref = orc.bernoulli_def(p - 3, p) if kind == 0 else orc.euler_def(p - 3, p)
+        assert val == ref, (name, p)
+
+
+def test_count_terms_matches_rows(T):
+    cid_b, cid_e = T["BB30"][0], T["EE33"][0]
+    p = 1_062_232_319
+    tb, te = wv.wv_count_terms([p], cid_b, cid_e)
+
+    def terms(rows):
+        tot = 0
+        for _, xn, xd, yn, yd in rows:
+            lo = xn * p // xd + 1
+            hi = yn * p // yd
+            tot += max(0, hi - lo + 1)
+        return tot
+    assert tb == terms(T["BB30"][3]) and te == terms(T["EE33"][3])
+    assert abs(tb / p - 227 / 6480) < 1e-6 and abs(te / p - 27 / 512) < 1e-6
