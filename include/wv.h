@@ -121,7 +121,8 @@ typedef struct {
   int tile_terms;   /* target terms per warp tile */
   int max_tiles;    /* maximum tiles per (prime, sum) */
   int blocks_per_sm;/* persistent grid = SMs x this */
-  int reserved[9];
+  int arith;        /* hot-loop formulation for p < 2^30: 1 = shared t p^-1, 2 = wide product */
+  int reserved[8];
 } wv_options;
 
 /* wv_residues_pm3 with explicit congruence choice and launch shape.

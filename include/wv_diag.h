@@ -25,6 +25,13 @@ extern "C" {
 #define WV_DIAG_IMNMX 4     /* min.u32                                      */
 #define WV_DIAG_TERM_B 5    /* one term of the p < 2^30 Bernoulli hot loop  */
 #define WV_DIAG_TERM_E 6    /* one term of the p < 2^30 Euler hot loop      */
+#define WV_DIAG_TERM_B_WIDE 7 /* the same, wide-product formulation         */
+#define WV_DIAG_TERM_E_WIDE 8 /* the same, wide-product formulation         */
+#define WV_DIAG_IMAD_WIDE_S 9 /* mul.wide.s32                               */
+#define WV_DIAG_IMAD_HI_U 10  /* mul.hi.u32                                 */
+#define WV_DIAG_MONT_MUL 11   /* one signed Montgomery product (4 instr.)   */
+#define WV_DIAG_SHOUP_MUL 12  /* one Shoup product (3 instr.)               */
+#define WV_DIAG_TERM_E_SHOUP 13 /* Euler term with Shoup products           */
 
 /*
  * Runs diagnostic `op` on the current device with one full wave of resident

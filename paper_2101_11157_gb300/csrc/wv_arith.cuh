@@ -74,6 +74,37 @@ __host__ __device__ inline PrimeCtx make_ctx(uint64_t p, uint32_t orig) {
   return c;
 }
 
+// ---------------------------------------------------------------- wide products
+// a * b as a 64-bit product, and a * b + c with a 64-bit addend, each one
+// instruction (PTX mul.wide / mad.wide).
+__device__ __forceinline__ int64_t mul_wide(int32_t a, int32_t b) {
+  int64_t d;
+  asm("mul.wide.s32 %0, %1, %2;" : "=l"(d) : "r"(a), "r"(b));
+  return d;
+}
+__device__ __forceinline__ int64_t mad_wide(int32_t a, int32_t b, int64_t c) {
+  int64_t d;
+  asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+  return d;
+}
+// high word of a 64-bit value (no instruction: the upper register of the pair)
+__device__ __forceinline__ int32_t hi32(int64_t v) {
+  int32_t hi;
+  asm("{\n\t.reg .b32 t;\n\tmov.b64 {t, %0}, %1;\n\t}" : "=r"(hi) : "l"(v));
+  return hi;
+}
+__device__ __forceinline__ int32_t lo32(int64_t v) {
+  int32_t lo;
+  asm("{\n\t.reg .b32 t;\n\tmov.b64 {%0, t}, %1;\n\t}" : "=r"(lo) : "l"(v));
+  return lo;
+}
+// the 64-bit value with high word h and low word 0
+__device__ __forceinline__ int64_t hi_word(int32_t h) {
+  int64_t v;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(v) : "r"(0), "r"(h));
+  return v;
+}
+
 // ---------------------------------------------------------------- M31
 __device__ __forceinline__ int32_t m31_redc(int32_t a, int32_t b, int32_t p, uint32_t q) {
   int32_t hi = __mulhi(a, b);

@@ -31,6 +31,27 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag(int iters, uint32_t seed,
       }
       if (OP == 3) asm volatile("add.u32 %0, %0, %1;" : "+r"(a[i]) : "r"(x));
       if (OP == 4) asm volatile("min.u32 %0, %0, %1;" : "+r"(a[i]) : "r"(y));
+      if (OP == 9) {
+        int64_t w;
+        asm volatile("mul.wide.s32 %0, %1, %2;" : "=l"(w) : "r"(a[i]), "r"(x));
+        a[i] = (uint32_t)(w >> 32) ^ (uint32_t)w;
+      }
+      if (OP == 10) asm volatile("mul.hi.u32 %0, %0, %1;" : "+r"(a[i]) : "r"(x));
+      if (OP == 11) {  // one signed Montgomery product: wide, lo * q, hi(m p), subtract
+        int64_t w;
+        uint32_t m, u;
+        asm volatile("mul.wide.s32 %0, %1, %2;" : "=l"(w) : "r"(a[i]), "r"(x));
+        asm volatile("mul.lo.u32 %0, %1, %2;" : "=r"(m) : "r"((uint32_t)w), "r"(y));
+        asm volatile("mul.hi.s32 %0, %1, %2;" : "=r"(u) : "r"(m), "r"(x));
+        a[i] = (uint32_t)(w >> 32) - u;
+      }
+      if (OP == 12) {  // Shoup product: hi(c t'), c t - q p
+        uint32_t qq, r;
+        asm volatile("mul.hi.u32 %0, %1, %2;" : "=r"(qq) : "r"(a[i]), "r"(y));
+        asm volatile("mul.lo.u32 %0, %1, %2;" : "=r"(r) : "r"(a[i]), "r"(x));
+        asm volatile("mad.lo.u32 %0, %1, %2, %0;" : "+r"(r) : "r"(qq), "r"(0u - x));
+        a[i] = r;
+      }
     }
   }
   __syncthreads();
@@ -43,7 +64,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag(int iters, uint32_t seed,
 }
 
 // The hot-loop term body of the p < 2^30 accumulation (2 independent chains).
-template <bool CUBES>
+template <bool CUBES, int AR>
 __global__ void __launch_bounds__(kDiagThreads) k_diag_term(int iters, uint32_t seed, uint64_t *cycles,
                                                             uint32_t *sink) {
   const int32_t p = 1062232319;  // < 2^30
@@ -64,14 +85,24 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_term(int iters, uint32_t 
   for (int it = 0; it < iters; ++it) {
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-      const uint32_t tq = (uint32_t)t[k] * q;
-      const int32_t m0 = (int32_t)((uint32_t)c0[k] * tq);
-      const int32_t m1 = (int32_t)((uint32_t)c1[k] * tq);
-      const int32_t h0 = __mulhi(c0[k], t[k]);
-      const int32_t h1 = __mulhi(c1[k], t[k]);
-      const int32_t n1 = h1 - __mulhi(m1, p) + c0[k];
-      c0[k] = h0 - __mulhi(m0, p);
-      c1[k] = n1;
+      if (AR == 1) {
+        const uint32_t tq = (uint32_t)t[k] * q;
+        const int32_t m0 = (int32_t)((uint32_t)c0[k] * tq);
+        const int32_t m1 = (int32_t)((uint32_t)c1[k] * tq);
+        const int32_t h0 = __mulhi(c0[k], t[k]);
+        const int32_t h1 = __mulhi(c1[k], t[k]);
+        const int32_t n1 = h1 - __mulhi(m1, p) + c0[k];
+        c0[k] = h0 - __mulhi(m0, p);
+        c1[k] = n1;
+      } else {
+        const int64_t w0 = (int64_t)c0[k] * (int64_t)t[k];
+        const int64_t w1 = (int64_t)c1[k] * (int64_t)t[k];
+        const int32_t m0 = (int32_t)((uint32_t)w0 * q);
+        const int32_t m1 = (int32_t)((uint32_t)w1 * q);
+        const int32_t n1 = (int32_t)(w1 >> 32) - __mulhi(m1, p) + c0[k];
+        c0[k] = (int32_t)(w0 >> 32) - __mulhi(m0, p);
+        c1[k] = n1;
+      }
       uint32_t x = (uint32_t)t[k] + (uint32_t)d1[k];
       t[k] = (int32_t)min(x, x - up);
       if (CUBES) {
@@ -91,13 +122,58 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_term(int iters, uint32_t 
   if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
 }
 
+// Euler hot-loop body with Shoup products: c t mod p = c t - hi(c t') p with
+// t' = floor(t 2^32 / p) carried along the forward differences.
+__global__ void __launch_bounds__(kDiagThreads) k_diag_shoup_e(int iters, uint32_t seed,
+                                                               uint64_t *cycles, uint32_t *sink) {
+  const uint32_t p = 1062232319u, np = 0u - p;
+  uint32_t c0[2], c1[2], t[2], tp[2], th[2], d[2], dp[2], dh[2];
+  const uint32_t twop = (uint32_t)((2ull << 32) / p) + 1u, twoh = (uint32_t)((2ull << 32) % p);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    c0[k] = (seed + threadIdx.x * 7u + k) % p; c1[k] = 0;
+    t[k] = (seed * 3u + threadIdx.x + k) % p; tp[k] = t[k] * 3u; th[k] = t[k] >> 1;
+    d[k] = (seed * 5u + threadIdx.x) % p; dp[k] = d[k] * 5u; dh[k] = d[k] >> 2;
+  }
+  __syncthreads();
+  const uint64_t t0 = clock64();
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const uint32_t q0 = __umulhi(c0[k], tp[k]);
+      const uint32_t q1 = __umulhi(c1[k], tp[k]);
+      const uint32_t n1 = c1[k] * t[k] + c0[k] + q1 * np;
+      c0[k] = c0[k] * t[k] + q0 * np;
+      c1[k] = n1;
+      // t, t', t^ += d, d', d^
+      int32_t sg = (int32_t)(th[k] + dh[k] - p);
+      int32_t sgn = sg >> 31;
+      th[k] = (uint32_t)sg + (p & (uint32_t)sgn);
+      tp[k] = tp[k] + dp[k] + (uint32_t)sgn;
+      uint32_t x = t[k] + d[k];
+      t[k] = min(x, x - p);
+      // d, d', d^ += 2, 2', 2^
+      d[k] += 2u;
+      sg = (int32_t)(dh[k] + twoh - p);
+      sgn = sg >> 31;
+      dh[k] = (uint32_t)sg + (p & (uint32_t)sgn);
+      dp[k] = dp[k] + twop + (uint32_t)sgn;
+    }
+  }
+  __syncthreads();
+  const uint64_t t1 = clock64();
+  uint32_t acc = c0[0] ^ c1[0] ^ c0[1] ^ c1[1] ^ t[0] ^ tp[1] ^ dp[0] ^ th[1];
+  if (acc == 0x12345678u) sink[0] = acc;
+  if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+}
+
 }  // namespace wv
 
 using namespace wv;
 
 extern "C" wv_status wv_diag_throughput(int op, int iters, double *per_clk) {
   clear_error();
-  if (!per_clk || iters < 1 || op < 0 || op > 6) return set_error(WV_EINVAL, "bad diag arguments");
+  if (!per_clk || iters < 1 || op < 0 || op > 13) return set_error(WV_EINVAL, "bad diag arguments");
   DeviceState *dev = nullptr;
   WV_CHECK(device_state(&dev));
   void (*kern)(int, uint32_t, uint64_t *, uint32_t *) = nullptr;
@@ -107,8 +183,15 @@ extern "C" wv_status wv_diag_throughput(int op, int iters, double *per_clk) {
     case 2: kern = k_diag<2>; break;
     case 3: kern = k_diag<3>; break;
     case 4: kern = k_diag<4>; break;
-    case 5: kern = k_diag_term<true>; break;
-    default: kern = k_diag_term<false>; break;
+    case 5: kern = k_diag_term<true, 1>; break;
+    case 6: kern = k_diag_term<false, 1>; break;
+    case 7: kern = k_diag_term<true, 2>; break;
+    case 8: kern = k_diag_term<false, 2>; break;
+    case 9: kern = k_diag<9>; break;
+    case 10: kern = k_diag<10>; break;
+    case 11: kern = k_diag<11>; break;
+    case 12: kern = k_diag<12>; break;
+    default: kern = k_diag_shoup_e; break;
   }
   int occ = 0;
   WV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kDiagThreads, 0));
@@ -132,7 +215,8 @@ extern "C" wv_status wv_diag_throughput(int op, int iters, double *per_clk) {
   uint64_t mx = 0;
   for (int i = 0; i < blocks; ++i) mx = h[i] > mx ? h[i] : mx;
   delete[] h;
-  const double per_thread = (op >= 5) ? 2.0 * iters : 8.0 * iters;  // ops (or terms) per thread
+  const bool term = (op >= 5 && op <= 8) || op == 13;
+  const double per_thread = term ? 2.0 * iters : 8.0 * iters;  // ops (or terms) per thread
   *per_clk = (double)occ * kDiagThreads * per_thread / (double)mx;
   return WV_OK;
 }

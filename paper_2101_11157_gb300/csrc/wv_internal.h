@@ -94,9 +94,10 @@ struct ResidueConfig {
   int cong_e = 12;       // EE33; -2 = skip
   int block = 256;
   int ilp = 2;
-  int tile_terms = 65536;
-  int max_tiles = 32;
+  int tile_terms = 1 << 20;
+  int max_tiles = 8;
   int blocks_per_sm = 0;  // 0 = occupancy
+  int arith = 9;          // p < 2^30 hot-loop formulation (see wv_residue.cu)
 };
 wv_status resolve_config(const wv_options *opt, bool want_b, bool want_e, ResidueConfig *cfg);
 

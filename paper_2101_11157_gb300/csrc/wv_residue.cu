@@ -40,6 +40,7 @@ namespace wv {
 constexpr int kAccThreads = 256;
 constexpr int kMaxRowsPP = 66;  // B rows + E rows for one prime (30 + 33 for BB30 + EE33)
 constexpr uint32_t kChunkPrimes = 16384;  // primes per internal launch sequence
+constexpr uint64_t kGroupMinChain = 48;   // grouped path only for chains of >= 48 terms
 
 struct Plan {
   uint32_t n;                   // primes in this chunk
@@ -125,8 +126,10 @@ __device__ __forceinline__ void warp_merge(const Mont &M, int64_t &a0, int64_t &
   }
 }
 
-// p < 2^30: signed 32-bit Montgomery, R = 2^32.
-template <int ILP, bool CUBES>
+// p < 2^30: signed 32-bit Montgomery, R = 2^32.  AR selects the product
+// formulation: 1 = hi(c t) and lo(c tq) with tq = t p^-1 shared by c0 and c1;
+// 2 = the full 64-bit product c t (one wide multiply) and m = lo(c t) p^-1.
+template <int ILP, bool CUBES, int AR>
 __device__ __forceinline__ void tile_m31(const PrimeCtx &ctx, uint64_t start, uint64_t n,
                                          int64_t &r0, int64_t &r1) {
   const int lane = threadIdx.x & 31;
@@ -154,38 +157,225 @@ __device__ __forceinline__ void tile_m31(const PrimeCtx &ctx, uint64_t start, ui
     c0[k] = (int32_t)ctx.one;
     c1[k] = 0;
   }
-  auto step = [&](int k) {
+  // z: a runtime zero (the context's upper flag bits are never set) that the
+  // compiler cannot fold.  Written into otherwise two-input additions it makes
+  // them genuine three-input adds, which only the integer ALU executes, so
+  // they stay off the multiply pipe the products saturate (AR >= 3).
+  const int32_t z = (int32_t)(ctx.flags >> 16);
+  const int32_t np = -p;
+  auto step = [&](int k, int32_t zi) {
     // eqn 3.12 with REDC against the plain term t
-    const uint32_t tq = (uint32_t)t[k] * q;
-    const int32_t m0 = (int32_t)((uint32_t)c0[k] * tq);
-    const int32_t m1 = (int32_t)((uint32_t)c1[k] * tq);
-    const int32_t h0 = __mulhi(c0[k], t[k]);
-    const int32_t h1 = __mulhi(c1[k], t[k]);
-    const int32_t n1 = h1 - __mulhi(m1, p) + c0[k];
-    c0[k] = h0 - __mulhi(m0, p);
-    c1[k] = n1;
-    // forward differences, each a modular add as min(x, x - p) on unsigned words
-    uint32_t x = (uint32_t)t[k] + (uint32_t)d1[k];
-    t[k] = (int32_t)min(x, x - up);
-    if (CUBES) {
-      x = (uint32_t)d1[k] + (uint32_t)d2[k];
-      d1[k] = (int32_t)min(x, x - up);
-      x = (uint32_t)d2[k] + 6u;
-      d2[k] = (int32_t)min(x, x - up);
+    if (AR == 1) {
+      const uint32_t tq = (uint32_t)t[k] * q;
+      const int32_t m0 = (int32_t)((uint32_t)c0[k] * tq);
+      const int32_t m1 = (int32_t)((uint32_t)c1[k] * tq);
+      const int32_t h0 = __mulhi(c0[k], t[k]);
+      const int32_t h1 = __mulhi(c1[k], t[k]);
+      const int32_t n1 = h1 - __mulhi(m1, p) + c0[k];
+      c0[k] = h0 - __mulhi(m0, p);
+      c1[k] = n1;
+    } else if (AR >= 6) {
+      // REDC folded into a wide multiply-add: d = w - m p is an exact
+      // multiple of 2^32 whose high word is the reduced value, and c0 rides
+      // in the high word of c1's product, so no separate add is needed.
+      const int64_t w0 = mul_wide(c0[k], t[k]);
+      const int64_t w1 = mad_wide(c1[k], t[k], hi_word(c0[k]));
+      const int32_t m0 = (int32_t)((uint32_t)lo32(w0) * q);
+      const int32_t m1 = (int32_t)((uint32_t)lo32(w1) * q);
+      c0[k] = hi32(mad_wide(m0, np, w0));
+      c1[k] = hi32(mad_wide(m1, np, w1));
     } else {
-      d1[k] += 2;
+      const int64_t w0 = (int64_t)c0[k] * (int64_t)t[k];
+      const int64_t w1 = (int64_t)c1[k] * (int64_t)t[k];
+      const int32_t m0 = (int32_t)((uint32_t)w0 * q);
+      const int32_t m1 = (int32_t)((uint32_t)w1 * q);
+      const int32_t n1 = (int32_t)(w1 >> 32) - __mulhi(m1, p) + c0[k];
+      if (AR >= 3) c0[k] = (int32_t)(w0 >> 32) - __mulhi(m0, p) + zi;
+      else c0[k] = (int32_t)(w0 >> 32) - __mulhi(m0, p);
+      c1[k] = n1;
+    }
+    // forward differences, each a modular add as min(x, x - p) on unsigned words
+    const uint32_t uz = (uint32_t)(AR >= 3 && AR < 6 ? z : 0);
+    const uint32_t uzi = (uint32_t)(AR >= 4 && AR < 6 ? zi : 0);
+    uint32_t x = (uint32_t)t[k] + (uint32_t)d1[k] + uz;
+    uint32_t y = (uint32_t)t[k] + (uint32_t)d1[k] - up;
+    t[k] = (int32_t)min(x, y);
+    if (CUBES) {
+      x = (uint32_t)d1[k] + (uint32_t)d2[k] + uz;
+      y = (uint32_t)d1[k] + (uint32_t)d2[k] - up;
+      d1[k] = (int32_t)min(x, y);
+      x = (uint32_t)d2[k] + 6u + uzi;
+      y = (uint32_t)d2[k] + (6u - up) + uzi;
+      d2[k] = (int32_t)min(x, y);
+    } else {
+      d1[k] = (int32_t)((uint32_t)d1[k] + 2u + uzi);
     }
   };
 #pragma unroll 2
   for (uint64_t it = 0; it < len; ++it) {
+    // a per-iteration zero (chains never reach 2^63 terms)
+    const int32_t zi = (AR >= 4 && AR < 6) ? (int32_t)(it >> 63) : z;
 #pragma unroll
-    for (int k = 0; k < ILP; ++k) step(k);
+    for (int k = 0; k < ILP; ++k) step(k, zi);
   }
 #pragma unroll
   for (int k = 0; k < ILP; ++k)
-    if ((uint32_t)(k * 32 + lane) < rem) step(k);
+    if ((uint32_t)(k * 32 + lane) < rem) step(k, z);
 
   const Mont M(ctx);
+  int64_t a0 = m31_canon(c0[0], p), a1 = m31_canon(c1[0], p);
+#pragma unroll
+  for (int k = 1; k < ILP; ++k) M.combine(a0, a1, m31_canon(c0[k], p), m31_canon(c1[k], p));
+  warp_merge(M, a0, a1);
+  r0 = a0;
+  r1 = a1;
+}
+
+// ---- grouped accumulation (p < 2^30) ------------------------------------
+// eqn 3.14 applied to a GROUP of K consecutive terms: the group's factor
+// prod_{i<K} (z + (s+i)^e) = G0(s) + G1(s) z + O(z^2) with
+//   G0(s) = prod_i (s+i)^e,   G1(s) = sum_i prod_{j!=i} (s+j)^e,
+// polynomials in s of degree K e and (K-1) e.  Both are stepped s -> s+K by
+// forward differences (additions only), and each group costs three products:
+//   c0 <- c0 G0,   c1 <- c1 G0 + c0 G1.
+// G1 is kept in Montgomery form so that, as in the single-term step, the
+// ratio c1/c0 accumulates R * sum t^-1 (see the bookkeeping note above).
+
+// G0(x) (plain) and G1(x) R (Montgomery) for the group x, x+1, ..., x+K-1.
+template <int K, int EX>
+__device__ __forceinline__ void group_poly(const Mont &M, uint64_t x, int64_t &g0, int64_t &g1m) {
+  int64_t tm[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    uint64_t v = x + i;
+    if (v >= (uint64_t)M.p) v -= (uint64_t)M.p;
+    const int64_t b = M.to_mont((int64_t)v);
+    int64_t t = M.mul(b, b);
+    if (EX == 3) t = M.mul(t, b);
+    tm[i] = t;  // (x+i)^e in Montgomery form
+  }
+  int64_t all = M.one, g1 = 0;
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    int64_t others = M.one;
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+      if (j != i) others = M.mul(others, tm[j]);
+    g1 = M.add(g1, others);
+    all = M.mul(all, tm[i]);
+  }
+  g0 = M.from_mont(all);
+  g1m = g1;
+}
+
+template <int ILP, bool CUBES, int AR>
+__device__ __forceinline__ void tile_m31_grouped(const PrimeCtx &ctx, uint64_t start, uint64_t n,
+                                                 int64_t &r0, int64_t &r1) {
+  constexpr int K = CUBES ? 2 : 3;     // terms per group
+  constexpr int EX = CUBES ? 3 : 2;    // t = s^EX
+  constexpr int DA = K * EX;           // degree of G0
+  constexpr int DB = (K - 1) * EX;     // degree of G1
+  const int lane = threadIdx.x & 31;
+  const Mont M(ctx);
+  const int32_t p = (int32_t)ctx.p;
+  const uint32_t up = (uint32_t)ctx.p;
+  const uint32_t q = (uint32_t)ctx.q;
+  const uint32_t uz = (AR >= 7) ? 0u : (ctx.flags >> 16);  // runtime zero (AR 5: three-input adds)
+  const int32_t np = -p;
+  const uint64_t nch = 32 * ILP;
+  const uint64_t len = n / nch;
+  const uint32_t rem = (uint32_t)(n - len * nch);
+  const uint64_t G = len / K;  // groups per chain, the same for every lane
+  int32_t c0[ILP], c1[ILP], ga[ILP][DA + 1], gb[ILP][DB + 1];
+  uint64_t s_tail[ILP];
+  uint32_t n_tail[ILP];
+#pragma unroll
+  for (int k = 0; k < ILP; ++k) {
+    const uint32_t ch = k * 32 + lane;
+    const uint64_t s = start + ch * len + (ch < rem ? ch : rem);
+    const uint64_t L = len + (ch < rem ? 1 : 0);
+    s_tail[k] = s + G * K;
+    n_tail[k] = (uint32_t)(L - G * K);
+    // difference tables of G0 and G1 at s, s+K, s+2K, ...
+    int64_t va[DA + 1], vb[DB + 1];
+#pragma unroll
+    for (int i = 0; i <= DA; ++i) {
+      int64_t a, b;
+      group_poly<K, EX>(M, s + (uint64_t)i * K, a, b);
+      va[i] = a;
+      if (i <= DB) vb[i] = b;
+    }
+#pragma unroll
+    for (int j = 1; j <= DA; ++j)
+#pragma unroll
+      for (int i = DA; i >= j; --i) va[i] = M.sub(va[i], va[i - 1]);
+#pragma unroll
+    for (int j = 1; j <= DB; ++j)
+#pragma unroll
+      for (int i = DB; i >= j; --i) vb[i] = M.sub(vb[i], vb[i - 1]);
+#pragma unroll
+    for (int i = 0; i <= DA; ++i) ga[k][i] = (int32_t)va[i];
+#pragma unroll
+    for (int i = 0; i <= DB; ++i) gb[k][i] = (int32_t)vb[i];
+    c0[k] = (int32_t)ctx.one;
+    c1[k] = 0;
+  }
+  auto modadd = [&](int32_t &a, int32_t b) {
+    const uint32_t x = (uint32_t)a + (uint32_t)b + uz;
+    const uint32_t y = (uint32_t)a + (uint32_t)b - up;
+    a = (int32_t)min(x, y);
+  };
+#pragma unroll 1
+  for (uint64_t g = 0; g < G; ++g) {
+#pragma unroll
+    for (int k = 0; k < ILP; ++k) {
+      const int32_t A = ga[k][0], B = gb[k][0];
+      if (AR >= 7) {
+        // one REDC for c1 G0 + c0 G1 R, folded into wide multiply-adds
+        const int64_t w0 = mul_wide(c0[k], A);
+        const int64_t w1 = mad_wide(c0[k], B, mul_wide(c1[k], A));
+        const int32_t m0 = (int32_t)((uint32_t)lo32(w0) * q);
+        const int32_t m1 = (int32_t)((uint32_t)lo32(w1) * q);
+        c0[k] = hi32(mad_wide(m0, np, w0));
+        c1[k] = hi32(mad_wide(m1, np, w1));
+      } else {
+        const int64_t w0 = (int64_t)c0[k] * (int64_t)A;
+        const int64_t w1 = (int64_t)c1[k] * (int64_t)A;
+        const int64_t w2 = (int64_t)c0[k] * (int64_t)B;
+        const int32_t m0 = (int32_t)((uint32_t)w0 * q);
+        const int32_t m1 = (int32_t)((uint32_t)w1 * q);
+        const int32_t m2 = (int32_t)((uint32_t)w2 * q);
+        const int32_t n1 = ((int32_t)(w1 >> 32) - __mulhi(m1, p)) + ((int32_t)(w2 >> 32) - __mulhi(m2, p));
+        c0[k] = (int32_t)(w0 >> 32) - __mulhi(m0, p) + (int32_t)uz;
+        c1[k] = n1;
+      }
+      // step both difference tables by one group (low order first)
+#pragma unroll
+      for (int j = 0; j < DA; ++j) modadd(ga[k][j], ga[k][j + 1]);
+#pragma unroll
+      for (int j = 0; j < DB; ++j) modadd(gb[k][j], gb[k][j + 1]);
+    }
+  }
+  // the last (at most K) terms of each chain one at a time (eqn 3.12)
+#pragma unroll
+  for (int k = 0; k < ILP; ++k) {
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      if ((uint32_t)i < n_tail[k]) {
+        const int64_t b = M.to_mont((int64_t)(s_tail[k] + i));
+        int64_t tm = M.mul(b, b);
+        if (EX == 3) tm = M.mul(tm, b);
+        const int32_t t = (int32_t)M.from_mont(tm);
+        const int64_t w0 = (int64_t)c0[k] * (int64_t)t;
+        const int64_t w1 = (int64_t)c1[k] * (int64_t)t;
+        const int32_t m0 = (int32_t)((uint32_t)w0 * q);
+        const int32_t m1 = (int32_t)((uint32_t)w1 * q);
+        const int32_t n1 = (int32_t)(w1 >> 32) - __mulhi(m1, p) + c0[k];
+        c0[k] = (int32_t)(w0 >> 32) - __mulhi(m0, p);
+        c1[k] = n1;
+      }
+    }
+  }
   int64_t a0 = m31_canon(c0[0], p), a1 = m31_canon(c1[0], p);
 #pragma unroll
   for (int k = 1; k < ILP; ++k) M.combine(a0, a1, m31_canon(c0[k], p), m31_canon(c1[k], p));
@@ -262,7 +452,7 @@ __device__ __forceinline__ void tile_m64(const PrimeCtx &ctx, uint64_t start, ui
 }
 
 // ------------------------------------------------------------------ accumulate
-template <bool WIDE, int ILP>
+template <bool WIDE, int ILP, int AR>
 __global__ void __launch_bounds__(kAccThreads) k_accumulate(Plan P) {
   const int lane = threadIdx.x & 31;
   const uint32_t total = *P.total_tiles, split = *P.split_tile;
@@ -290,9 +480,19 @@ __global__ void __launch_bounds__(kAccThreads) k_accumulate(Plan P) {
     const uint64_t b0 = cnt * k / T, b1 = cnt * (k + 1) / T;
     const uint64_t start = P.seg_lo[s] + b0, n = b1 - b0;
     int64_t r0, r1;
-    if (!WIDE) {
-      if (j < P.rows_b) tile_m31<ILP, true>(ctx, start, n, r0, r1);
-      else tile_m31<ILP, false>(ctx, start, n, r0, r1);
+    // single-term form used beside the grouped one
+    constexpr int AS = (AR == 5 || AR == 8 || AR == 9) ? 4 : AR;
+    const bool grp_ok = n >= 32ull * ILP * kGroupMinChain;
+    if (!WIDE && AR == 5 && grp_ok) {
+      if (j < P.rows_b) tile_m31_grouped<ILP, true, 5>(ctx, start, n, r0, r1);
+      else tile_m31_grouped<ILP, false, 5>(ctx, start, n, r0, r1);
+    } else if (!WIDE && AR >= 7 && grp_ok && j >= P.rows_b) {
+      tile_m31_grouped<ILP, false, 7>(ctx, start, n, r0, r1);
+    } else if (!WIDE && AR == 9 && grp_ok) {
+      tile_m31_grouped<ILP, true, 7>(ctx, start, n, r0, r1);
+    } else if (!WIDE) {
+      if (j < P.rows_b) tile_m31<ILP, true, AS>(ctx, start, n, r0, r1);
+      else tile_m31<ILP, false, AS>(ctx, start, n, r0, r1);
     } else {
       if (j < P.rows_b) tile_m64<ILP, true>(ctx, start, n, r0, r1);
       else tile_m64<ILP, false>(ctx, start, n, r0, r1);
@@ -373,11 +573,19 @@ template <bool WIDE>
 static wv_status launch_accumulate(const Plan &P, const ResidueConfig &cfg, int sms, cudaStream_t s) {
   const char *name = WIDE ? "accumulate_m64" : "accumulate_m31";
   void (*kern)(Plan) = nullptr;
+  const int ar = WIDE ? 1 : cfg.arith;
+#define WV_PICK(I)                                                          \
+  (ar == 1 ? k_accumulate<WIDE, I, 1> : ar == 2 ? k_accumulate<WIDE, I, 2> \
+   : ar == 3 ? k_accumulate<WIDE, I, 3> : ar == 4 ? k_accumulate<WIDE, I, 4> \
+   : ar == 5 ? k_accumulate<WIDE, I, 5> : ar == 6 ? k_accumulate<WIDE, I, 6>  \
+   : ar == 7 ? k_accumulate<WIDE, I, 7> : ar == 8 ? k_accumulate<WIDE, I, 8>  \
+   : k_accumulate<WIDE, I, 9>)
   switch (cfg.ilp) {
-    case 1: kern = k_accumulate<WIDE, 1>; break;
-    case 2: kern = k_accumulate<WIDE, 2>; break;
-    default: kern = k_accumulate<WIDE, 4>; break;
+    case 1: kern = WV_PICK(1); break;
+    case 2: kern = WV_PICK(2); break;
+    default: kern = WV_PICK(4); break;
   }
+#undef WV_PICK
   int occ = cfg.blocks_per_sm;
   if (occ <= 0) {
     WV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kAccThreads, 0));
@@ -418,8 +626,8 @@ wv_status residues_device(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,
     P.lhs_e = c.lhs;
   }
   P.rows_pp = r;
-  P.tile_terms = (uint32_t)(cfg.tile_terms > 0 ? cfg.tile_terms : 65536);
-  P.max_tiles = (uint32_t)(cfg.max_tiles > 0 ? cfg.max_tiles : 32);
+  P.tile_terms = (uint32_t)(cfg.tile_terms > 0 ? cfg.tile_terms : (1 << 20));
+  P.max_tiles = (uint32_t)(cfg.max_tiles > 0 ? cfg.max_tiles : 8);
 
   const uint32_t chunk = (uint32_t)(n < kChunkPrimes ? n : kChunkPrimes);
   const size_t nseg = (size_t)chunk * P.rows_pp;

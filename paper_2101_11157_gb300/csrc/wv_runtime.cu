@@ -266,6 +266,7 @@ wv_status resolve_config(const wv_options *opt, bool want_b, bool want_e, Residu
     if (opt->tile_terms > 0) c.tile_terms = opt->tile_terms;
     if (opt->max_tiles > 0) c.max_tiles = opt->max_tiles;
     if (opt->blocks_per_sm > 0) c.blocks_per_sm = opt->blocks_per_sm;
+    if (opt->arith > 0) c.arith = opt->arith;
   }
   if (c.cong_b >= 0 && (c.cong_b >= kWvNumCongruences || kWvCongruences[c.cong_b].kind != 0))
     return set_error(WV_EINVAL, "cong_b=%d is not a Bernoulli congruence", c.cong_b);
@@ -275,6 +276,7 @@ wv_status resolve_config(const wv_options *opt, bool want_b, bool want_e, Residu
     return set_error(WV_EINVAL, "block=%d must be a multiple of 32 in [32,1024]", c.block);
   if (c.ilp != 1 && c.ilp != 2 && c.ilp != 4)
     return set_error(WV_EINVAL, "ilp=%d must be 1, 2 or 4", c.ilp);
+  if (c.arith < 1 || c.arith > 9) return set_error(WV_EINVAL, "arith=%d must be in 1..9", c.arith);
   if (c.max_tiles > 4096) return set_error(WV_EINVAL, "max_tiles=%d > 4096", c.max_tiles);
   *cfg = c;
   return WV_OK;

@@ -39,7 +39,8 @@ class wv_hit(ctypes.Structure):
 class wv_options(ctypes.Structure):
     _fields_ = [("cong_b", ctypes.c_int), ("cong_e", ctypes.c_int), ("block", ctypes.c_int),
                 ("ilp", ctypes.c_int), ("tile_terms", ctypes.c_int), ("max_tiles", ctypes.c_int),
-                ("blocks_per_sm", ctypes.c_int), ("reserved", ctypes.c_int * 9)]
+                ("blocks_per_sm", ctypes.c_int), ("arith", ctypes.c_int),
+                ("reserved", ctypes.c_int * 8)]
 
 
 _lock = threading.Lock()
@@ -268,7 +269,9 @@ def wv_profile_get(idx: int):
     return nm.value.decode(), la.value, ms.value
 
 
-DIAG_OPS = {"imad": 0, "imad_hi": 1, "imad_wide": 2, "iadd": 3, "imnmx": 4, "term_b": 5, "term_e": 6}
+DIAG_OPS = {"imad": 0, "imad_hi": 1, "imad_wide": 2, "iadd": 3, "imnmx": 4, "term_b": 5, "term_e": 6,
+            "term_b_wide": 7, "term_e_wide": 8, "imad_wide_s": 9, "imad_hi_u": 10,
+            "mont_mul": 11, "shoup_mul": 12, "term_e_shoup": 13}
 
 
 def wv_diag_throughput(op, iters: int = 4096) -> float:
