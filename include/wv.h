@@ -111,6 +111,31 @@ wv_status wv_euler_pm3(const uint64_t *d_primes, size_t n, uint64_t *d_out,
 wv_status wv_residues_pm3(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,
                           uint64_t *d_out_e, wv_stream stream);
 
+/*
+ * wv_residues_pm3 for callers that cannot allocate device memory during a
+ * call: hosts whose device memory is entirely owned by their own pool
+ * allocator (so a cudaMalloc would fail or fragment it), and real-time loops
+ * that cannot afford the device-wide synchronisation cudaMalloc/cudaFree
+ * imply.  The paper has no counterpart to this call.
+ *
+ * It computes exactly what wv_residues_pm3 computes (default congruences and
+ * launch shape) but allocates nothing: all scratch lives in one fixed device
+ * array inside the library, about 10 MB, that every GPU which loads the
+ * library keeps until the process exits.  Limits and behaviour:
+ *  - n <= 1024 primes per call; larger n returns WV_ERANGE (split the list).
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call uses the same array and leaves its contents behind; the call
+ *    itself clears what must start at zero.  Calls that overlap on the GPU
+ *    (different streams, or different host threads, without ordering between
+ *    them) race on the array and must not be issued.
+ *  - d_primes, d_out_b, d_out_e are device arrays of n uint64 owned by the
+ *    caller; either output may be NULL.  Asynchronous on `stream`.
+ */
+wv_status wv_residues_pm3_noalloc(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,
+                                  uint64_t *d_out_e, wv_stream stream);
+
 /* Options for the *_ex entry points.  Zero-initialise, then set fields;
  * a zero / negative field means "library default". */
 typedef struct {

@@ -87,6 +87,8 @@ wv_status scan_exclusive_u32(const uint32_t *d_in, uint32_t *d_out, size_t n,
                              uint32_t *d_total, uint32_t *d_tmp, cudaStream_t s);
 wv_status scan_exclusive_u64(const uint64_t *d_in, uint64_t *d_out, size_t n,
                              uint64_t *d_total, uint64_t *d_tmp, cudaStream_t s);
+wv_status scan_exclusive_u32_bare(const uint32_t *d_in, uint32_t *d_out, size_t n,
+                                  uint32_t *d_total, uint32_t *d_tmp, cudaStream_t s);
 
 // ------------------------------------------------------------ residues
 struct ResidueConfig {

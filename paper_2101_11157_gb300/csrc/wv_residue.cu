@@ -30,6 +30,9 @@
 // (true initially for (c0, c1) = (R, 0) and preserved by both eqn 3.12 steps
 // and by eqn 3.14 under REDC).  The finaliser therefore divides by R once.
 #include <stdio.h>
+#include <string.h>
+
+#include <mutex>
 
 #include "wv_arith.cuh"
 #include "wv_internal.h"
@@ -670,6 +673,129 @@ wv_status residues_device(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,
   return WV_OK;
 }
 
+// ------------------------------------------------------------------ no-alloc
+// Residues without any allocation: every scratch buffer of the launch sequence
+// above is carved from one file-scope device array of fixed size instead of
+// the library's stream-ordered pool.  Sized for kNoAllocMaxPrimes primes per
+// call with the default congruences and launch shape (max_tiles 8).
+constexpr uint32_t kNoAllocMaxPrimes = 1024;
+constexpr uint32_t kNoAllocTiles = 8;
+
+__host__ __device__ constexpr size_t na_align(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr size_t kNaSegs = (size_t)kNoAllocMaxPrimes * kMaxRowsPP;
+constexpr size_t kNaScanTmp = kNaSegs / 4096 + 2;  // scan_tmp_elems bound for kNaSegs
+constexpr size_t kNaBytes =
+    na_align(kNoAllocMaxPrimes * sizeof(PrimeCtx)) + 2 * na_align(kNoAllocMaxPrimes * 4) +
+    2 * na_align(kNaSegs * 8) + 2 * na_align(kNaSegs * 4) +
+    na_align(kNaSegs * kNoAllocTiles * sizeof(ulonglong2)) + na_align(kNaScanTmp * 4) + 256;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+static std::mutex g_na_mu;
+static void *g_na_addr[64];  // device address of g_noalloc_scratch, per device
+
+wv_status residues_noalloc(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,
+                           uint64_t *d_out_e, cudaStream_t s) {
+  if (n == 0) return WV_OK;
+  if (!d_primes) return set_error(WV_EINVAL, "d_primes is NULL");
+  if (n > kNoAllocMaxPrimes)
+    return set_error(WV_ERANGE, "wv_residues_pm3_noalloc takes at most %u primes per call (got %zu)",
+                     kNoAllocMaxPrimes, n);
+  const bool do_b = d_out_b != nullptr, do_e = d_out_e != nullptr;
+  if (!do_b && !do_e) return WV_OK;
+  int dev = 0;
+  WV_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return set_error(WV_EINVAL, "device index %d out of range", dev);
+  unsigned char *base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    if (!g_na_addr[dev]) {
+      // The array's name is only a host-side stand-in: its device address
+      // must be looked up once per device, with that device current.
+      void *ptr = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(noalloc scratch)");
+      g_na_addr[dev] = ptr;
+    }
+    base = (unsigned char *)g_na_addr[dev];
+  }
+  int sms = 0;
+  WV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+
+  ResidueConfig cfg;  // library defaults
+  Plan P;
+  memset(&P, 0, sizeof P);
+  uint32_t r = 0;
+  if (do_b) {
+    const WvCongruence &c = kWvCongruences[cfg.cong_b];
+    for (int j = 0; j < c.nrows; ++j, ++r) {
+      const WvRow &w = kWvRows[c.row_offset + j];
+      P.xn[r] = w.xn; P.xd[r] = w.xd; P.yn[r] = w.yn; P.yd[r] = w.yd; P.coef[r] = w.coef;
+    }
+    P.rows_b = c.nrows;
+    P.lhs_b = c.lhs;
+  }
+  if (do_e) {
+    const WvCongruence &c = kWvCongruences[cfg.cong_e];
+    for (int j = 0; j < c.nrows; ++j, ++r) {
+      const WvRow &w = kWvRows[c.row_offset + j];
+      P.xn[r] = w.xn; P.xd[r] = w.xd; P.yn[r] = w.yn; P.yd[r] = w.yd; P.coef[r] = w.coef;
+    }
+    P.rows_e = c.nrows;
+    P.lhs_e = c.lhs;
+  }
+  P.rows_pp = r;
+  P.tile_terms = (uint32_t)cfg.tile_terms;
+  P.max_tiles = kNoAllocTiles;
+  // carve the scratch array
+  size_t off = 0;
+  auto carve = [&](size_t bytes) {
+    unsigned char *q = base + off;
+    off += na_align(bytes);
+    return q;
+  };
+  P.ctx = (PrimeCtx *)carve(kNoAllocMaxPrimes * sizeof(PrimeCtx));
+  P.flag = (uint32_t *)carve(kNoAllocMaxPrimes * 4);
+  P.pos = (uint32_t *)carve(kNoAllocMaxPrimes * 4);
+  P.seg_lo = (uint64_t *)carve(kNaSegs * 8);
+  P.seg_cnt = (uint64_t *)carve(kNaSegs * 8);
+  P.seg_tiles = (uint32_t *)carve(kNaSegs * 4);
+  P.seg_first = (uint32_t *)carve(kNaSegs * 4);
+  P.partials = (ulonglong2 *)carve(kNaSegs * kNoAllocTiles * sizeof(ulonglong2));
+  uint32_t *u32tmp = (uint32_t *)carve(kNaScanTmp * 4);
+  uint32_t *scal = (uint32_t *)carve(256);
+  if (off > kNaBytes) return set_error(WV_EINVAL, "internal: no-alloc scratch layout overflow");
+  P.n31 = scal + 0;
+  P.total_tiles = scal + 1;
+  P.split_tile = scal + 2;
+  P.counters = scal + 4;  // zeroed by k_plan_split before every accumulation
+  P.n = (uint32_t)n;
+  P.primes = d_primes;
+  P.out_b = do_b ? d_out_b : nullptr;
+  P.out_e = do_e ? d_out_e : nullptr;
+
+  const unsigned gp = (P.n + 255) / 256;
+  const size_t ns = (size_t)P.n * P.rows_pp;
+  k_plan_prime<<<gp, 256, 0, s>>>(P);
+  WV_CHECK(scan_exclusive_u32_bare(P.flag, P.pos, P.n, P.n31, u32tmp, s));
+  k_plan_scatter<<<gp, 256, 0, s>>>(P);
+  k_plan_segments<<<(unsigned)((ns + 255) / 256), 256, 0, s>>>(P);
+  WV_CHECK(scan_exclusive_u32_bare(P.seg_tiles, P.seg_first, ns, P.total_tiles, u32tmp, s));
+  k_plan_split<<<1, 1, 0, s>>>(P);
+  WV_CUDA(cudaGetLastError());
+  void (*k31)(Plan) = k_accumulate<false, 2, 9>;
+  void (*k64)(Plan) = k_accumulate<true, 2, 1>;
+  int occ31 = 0, occ64 = 0;
+  WV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ31, k31, kAccThreads, 0));
+  WV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ64, k64, kAccThreads, 0));
+  k31<<<(unsigned)(sms * (occ31 > 0 ? occ31 : 1)), kAccThreads, 0, s>>>(P);
+  k64<<<(unsigned)(sms * (occ64 > 0 ? occ64 : 1)), kAccThreads, 0, s>>>(P);
+  const size_t warps = (size_t)P.n * ((do_b ? 1 : 0) + (do_e ? 1 : 0));
+  k_finalize<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(P);
+  WV_CUDA(cudaGetLastError());
+  return WV_OK;
+}
+
 }  // namespace wv
 
 using namespace wv;
@@ -697,6 +823,12 @@ wv_status wv_bernoulli_pm3(const uint64_t *d_primes, size_t n, uint64_t *d_out, 
     return set_error(WV_EINVAL, "d_out is NULL");
   }
   return wv_residues_ex(d_primes, n, d_out, nullptr, nullptr, stream);
+}
+
+wv_status wv_residues_pm3_noalloc(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,
+                                  uint64_t *d_out_e, wv_stream stream) {
+  clear_error();
+  return residues_noalloc(d_primes, n, d_out_b, d_out_e, (cudaStream_t)stream);
 }
 
 wv_status wv_euler_pm3(const uint64_t *d_primes, size_t n, uint64_t *d_out, wv_stream stream) {

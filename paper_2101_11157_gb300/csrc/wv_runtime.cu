@@ -253,6 +253,23 @@ wv_status scan_exclusive_u64(const uint64_t *in, uint64_t *out, size_t n, uint64
   return scan_impl<uint64_t>(in, out, n, total, tmp, s);
 }
 
+// The same scan launched without the profiler's bookkeeping (which keeps
+// host-side tables and, when timing is on, creates events): used by the entry
+// point that must not allocate anything.
+wv_status scan_exclusive_u32_bare(const uint32_t *in, uint32_t *out, size_t n, uint32_t *total,
+                                  uint32_t *tmp, cudaStream_t s) {
+  if (n == 0) {
+    WV_CUDA(cudaMemsetAsync(total, 0, sizeof(uint32_t), s));
+    return WV_OK;
+  }
+  const size_t tiles = (n + kScanTile - 1) / kScanTile;
+  k_scan_tiles<uint32_t><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n, tmp);
+  k_scan_top<uint32_t><<<1, kScanThreads, 0, s>>>(tmp, tiles, total);
+  if (tiles > 1) k_scan_add<uint32_t><<<(unsigned)tiles, kScanThreads, 0, s>>>(out, n, tmp);
+  WV_CUDA(cudaGetLastError());
+  return WV_OK;
+}
+
 // ================================================================ options
 wv_status resolve_config(const wv_options *opt, bool want_b, bool want_e, ResidueConfig *cfg) {
   ResidueConfig c;

@@ -57,6 +57,7 @@ _SIGS = {
     "wv_euler_pm3": ([_vp, _sz, _vp, _vp], _i32),
     "wv_residues_pm3": ([_vp, _sz, _vp, _vp, _vp], _i32),
     "wv_residues_ex": ([_vp, _sz, _vp, _vp, ctypes.POINTER(wv_options), _vp], _i32),
+    "wv_residues_pm3_noalloc": ([_vp, _sz, _vp, _vp, _vp], _i32),
     "wv_search": ([_u64, _u64, _vp, _sz, _psz, _vp], _i32),
     "wv_search_ex": ([_u64, _u64, _u64, _vp, _sz, _psz, _vp, _vp, _vp, _sz, _psz,
                       ctypes.POINTER(wv_options), _vp], _i32),
@@ -174,6 +175,13 @@ def wv_euler_pm3(d_primes, d_out, stream=None) -> None:
 def wv_residues_pm3(d_primes, d_out_b, d_out_e, stream=None) -> None:
     _check(load().wv_residues_pm3(_ptr(d_primes), d_primes.numel(), _ptr(d_out_b), _ptr(d_out_e),
                                   _stream(stream)))
+
+
+def wv_residues_pm3_noalloc(d_primes, d_out_b, d_out_e, stream=None) -> None:
+    """wv_residues_pm3 without any allocation (at most 1024 primes per call);
+    for callers that cannot allocate device memory during a call."""
+    _check(load().wv_residues_pm3_noalloc(_ptr(d_primes), d_primes.numel(), _ptr(d_out_b),
+                                          _ptr(d_out_e), _stream(stream)))
 
 
 def wv_residues_ex(d_primes, d_out_b, d_out_e, options: dict | None = None, stream=None) -> None:
