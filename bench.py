@@ -34,6 +34,10 @@ WIDTH = HI - LO
 IMAD_PER_SM_CLK = 64          # 32-bit integer multiply-add results per SM per clock
 IMAD_SLOTS_PER_MODMUL = 5     # one 32-bit Montgomery product: mul.wide (2) + mul.lo (1) + mul.hi (2)
 SM_MAX_MHZ_FALLBACK = 2070.0
+# DRAM bytes per launch of the p < 2^30 accumulation kernel (k_accumulate<0,2,9>), from one ncu
+# capture of the 492-prime head of the window (1.21984 MB read, 0 written), scaled by primes to the
+# 4907-prime launch.  Must be re-taken (or set to None) whenever that kernel changes.
+ACC_TRAFFIC_BYTES = 1.21984e6 * 4907 / 492
 
 
 def dist_env():
@@ -302,7 +306,7 @@ def gpu_arm(args):
         "modmul_per_s": modmuls_per_step * ws / (ms / 1000.0),
         "roofline": {"bound": "alu", "achieved": achieved_gmodmul, "peak": peak_gmodmul,
                      "unit": "Gmodmul/s", "frac": achieved_gmodmul / peak_gmodmul if peak_gmodmul else None,
-                     "traffic": None,
+                     "traffic": ACC_TRAFFIC_BYTES if width == WIDTH else None,
                      "peak_basis": f"{sms} SMs x {IMAD_PER_SM_CLK} IMAD lanes/clk x {sm_max:.0f} MHz / "
                                    f"{IMAD_SLOTS_PER_MODMUL} IMAD slots per 32-bit Montgomery product "
                                    "(slot costs measured by wv_diag_throughput)",

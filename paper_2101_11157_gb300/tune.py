@@ -1,0 +1,129 @@
+"""Autotuner for the residue launch shape.
+
+Times the accumulation kernels (CUDA events on the launching stream, through
+the library's profiler) for a grid of ``wv_options`` on a given set of primes,
+checks that every shape returns bit-identical residues, and records the
+fastest shape per GPU and p-bucket (floor(log2 p_max)) in a JSON cache.  The
+batch and serving front ends read that cache.
+
+    python -m paper_2101_11157_gb300.tune --lo 1062200000 --hi 1062300000 --grid arith
+    python -m paper_2101_11157_gb300.tune --lo 1062200000 --hi 1062300000 --grid shape --save
+"""
+from __future__ import annotations
+
+import argparse
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+
+from . import build as _build
+from . import wv
+
+CACHE = os.path.join(_build.OUT, "tune_cache.json")
+
+GRIDS = {
+    # the hot-loop formulations (wv_options.arith) at the default shape
+    "arith": [{"arith": a, "ilp": i} for a, i in itertools.product((1, 2, 4, 9), (1, 2))],
+    # launch shapes for the default formulation
+    "shape": [{"ilp": i, "tile_terms": t, "max_tiles": m}
+              for i, (t, m) in itertools.product((1, 2), ((1 << 18, 16), (1 << 20, 8), (1 << 22, 4)))],
+    "default": [{}],
+}
+
+
+def _time(d, rb, re, opt, reps):
+    import torch
+    wv.wv_residues_ex(d, rb, re, opt or None)
+    torch.cuda.synchronize()
+    wv.wv_profile_reset()
+    wv.wv_profile_enable(True)
+    for _ in range(reps):
+        wv.wv_residues_ex(d, rb, re, opt or None)
+    torch.cuda.synchronize()
+    prof = wv.wv_profile_collect()
+    wv.wv_profile_enable(False)
+    ms = sum(v[1] for k, v in prof.items() if k.startswith("accumulate")) / reps
+    return ms
+
+
+def sweep(primes, grid, reps: int = 2):
+    """Yield dicts {options, acc_ms, terms_per_clk_sm, identical} for each shape."""
+    import torch
+    d = torch.from_numpy(np.asarray(primes, dtype=np.uint64).view(np.int64)).cuda()
+    rb, re = torch.empty_like(d), torch.empty_like(d)
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    tb, te = wv.wv_count_terms(np.asarray(primes, dtype=np.uint64))
+    ref = None
+    for opt in grid:
+        ms = _time(d, rb, re, opt, reps)
+        out = (rb.cpu().numpy().copy(), re.cpu().numpy().copy())
+        if ref is None:
+            ref = out
+        same = bool(np.array_equal(out[0], ref[0]) and np.array_equal(out[1], ref[1]))
+        # SM clock: the device's maximum (the bench records the clocks it saw)
+        clk = props.clock_rate * 1e3 if hasattr(props, "clock_rate") else 2.07e9
+        tpc = (tb + te) / (ms / 1e3) / props.multi_processor_count / clk if ms else 0.0
+        yield {"options": opt, "acc_ms": round(ms, 3), "terms_per_clk_sm": round(tpc, 3),
+               "identical": same}
+
+
+def bucket(p_max: int) -> int:
+    return int(math.floor(math.log2(max(int(p_max), 2))))
+
+
+def load_cache(path: str = CACHE) -> dict:
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def best_options(primes, path: str = CACHE):
+    """Cached best options for this GPU and the largest prime's bucket (or None)."""
+    try:
+        import torch
+        name = torch.cuda.get_device_name()
+    except Exception:
+        return None
+    cache = load_cache(path)
+    if len(primes) == 0:
+        return None
+    b = str(bucket(int(np.max(np.asarray(primes, dtype=np.uint64)))))
+    return cache.get(name, {}).get(b)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--lo", type=int, default=1_062_200_000)
+    ap.add_argument("--hi", type=int, default=1_062_300_000)
+    ap.add_argument("--grid", default="shape", choices=sorted(GRIDS))
+    ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--save", action="store_true", help="record the fastest shape in the cache")
+    args = ap.parse_args()
+    import torch
+
+    from . import api
+    primes = api.to_u64(api.sieve(args.lo, args.hi))
+    rows = []
+    for r in sweep(primes, GRIDS[args.grid], args.reps):
+        print(json.dumps(r), flush=True)
+        rows.append(r)
+    bad = [r for r in rows if not r["identical"]]
+    if bad:
+        raise SystemExit(f"shapes disagree: {bad}")
+    if args.save and rows:
+        best = min(rows, key=lambda r: r["acc_ms"])
+        cache = load_cache()
+        cache.setdefault(torch.cuda.get_device_name(), {})[str(bucket(primes.max()))] = best["options"]
+        os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+        with open(CACHE, "w") as f:
+            json.dump(cache, f, indent=1)
+        print(json.dumps({"saved": best, "bucket": bucket(primes.max()), "cache": CACHE}))
+
+
+if __name__ == "__main__":
+    main()
