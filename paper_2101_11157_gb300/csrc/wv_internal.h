@@ -100,6 +100,7 @@ struct ResidueConfig {
   int max_tiles = 8;
   int blocks_per_sm = 0;  // 0 = occupancy
   int arith = 9;          // p < 2^30 hot-loop formulation (see wv_residue.cu)
+  size_t chunk = 0;       // primes per launch sequence (0: library default 16384)
 };
 wv_status resolve_config(const wv_options *opt, bool want_b, bool want_e, ResidueConfig *cfg);
 

@@ -52,7 +52,8 @@ struct Plan {
   const uint64_t *primes;       // caller's primes (chunk base)
   uint64_t *out_b, *out_e;      // caller's outputs (chunk base), may be null
   PrimeCtx *ctx;                // per slot (M31 slots first, then M64)
-  uint32_t *flag, *pos, *n31;   // path partition
+  uint32_t *flag, *pos, *n31;   // flag: p-bucket per prime; n31: slots with p < 2^30
+  uint32_t *bk;                 // 3 x 64 words: bucket counts, offsets, cursors
   uint64_t *seg_lo, *seg_cnt;   // per segment (slot * rows_pp + row)
   uint32_t *seg_tiles, *seg_first;
   uint32_t *total_tiles, *split_tile;
@@ -65,18 +66,45 @@ struct Plan {
 };
 
 // ------------------------------------------------------------------ planner
+// Primes are ordered into slots by p-bucket floor(log2 p), ascending (a
+// counting sort; order inside a bucket is arbitrary and does not affect any
+// result).  Buckets 0..29 are the p < 2^30 slots; the accumulation kernels
+// walk slots from the top, so the largest primes start first.
+__device__ __forceinline__ uint32_t p_bucket(uint64_t p) {
+  const bool valid = (p >= 11) && (p & 1) && (p < kPMax);
+  return valid ? (uint32_t)(63 - __clzll((long long)p)) : 0u;  // special/invalid: no sums
+}
+
 __global__ void k_plan_prime(Plan P) {
   uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= P.n) return;
-  uint64_t p = P.primes[i];
-  P.flag[i] = (p < kM31Limit) ? 1u : 0u;  // invalid values also go with the M31 slots
+  const uint32_t b = p_bucket(P.primes[i]);
+  P.flag[i] = b;
+  atomicAdd(&P.bk[b], 1u);
+}
+
+__global__ void k_plan_buckets(Plan P) {  // one warp: offsets of the 64 buckets
+  const int lane = threadIdx.x;
+  uint32_t c0 = P.bk[lane], c1 = P.bk[32 + lane];
+  uint32_t x0 = c0, x1 = c1;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y0 = __shfl_up_sync(0xffffffffu, x0, o), y1 = __shfl_up_sync(0xffffffffu, x1, o);
+    if (lane >= o) { x0 += y0; x1 += y1; }
+  }
+  const uint32_t tot0 = __shfl_sync(0xffffffffu, x0, 31);
+  P.bk[64 + lane] = x0 - c0;
+  P.bk[96 + lane] = tot0 + x1 - c1;
+  const uint32_t below30 = __shfl_sync(0xffffffffu, x0, 29);  // buckets 0..29
+  if (lane == 0) *P.n31 = below30;
 }
 
 __global__ void k_plan_scatter(Plan P) {
   uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= P.n) return;
   uint64_t p = P.primes[i];
-  uint32_t slot = P.flag[i] ? P.pos[i] : *P.n31 + (i - P.pos[i]);
+  const uint32_t b = P.flag[i];
+  const uint32_t slot = P.bk[64 + b] + atomicAdd(&P.bk[128 + b], 1u);
   PrimeCtx c;
   bool valid = (p >= 5) && (p & 1) && (p < kPMax);
   if (valid && p >= 11) {
@@ -632,7 +660,8 @@ wv_status residues_device(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,
   P.tile_terms = (uint32_t)(cfg.tile_terms > 0 ? cfg.tile_terms : (1 << 20));
   P.max_tiles = (uint32_t)(cfg.max_tiles > 0 ? cfg.max_tiles : 8);
 
-  const uint32_t chunk = (uint32_t)(n < kChunkPrimes ? n : kChunkPrimes);
+  const size_t cap = cfg.chunk > 0 ? (size_t)cfg.chunk : kChunkPrimes;
+  const uint32_t chunk = (uint32_t)(n < cap ? n : cap);
   const size_t nseg = (size_t)chunk * P.rows_pp;
   Scratch sc(s);
   uint32_t *u32tmp = nullptr, *scal = nullptr;
@@ -645,7 +674,8 @@ wv_status residues_device(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,
   WV_CHECK(sc.get(&P.seg_first, nseg));
   WV_CHECK(sc.get(&P.partials, nseg * P.max_tiles));
   WV_CHECK(sc.get(&u32tmp, scan_tmp_elems(nseg)));
-  WV_CHECK(sc.get(&scal, 8));
+  WV_CHECK(sc.get(&scal, 256));
+  P.bk = scal + 64;
   P.n31 = scal + 0;
   P.total_tiles = scal + 1;
   P.split_tile = scal + 2;
@@ -657,8 +687,9 @@ wv_status residues_device(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,
     P.out_b = do_b ? d_out_b + base : nullptr;
     P.out_e = do_e ? d_out_e + base : nullptr;
     const unsigned gp = (P.n + 255) / 256;
+    WV_CUDA(cudaMemsetAsync(P.bk, 0, 192 * sizeof(uint32_t), s));
     WV_LAUNCH("plan_prime", k_plan_prime, gp, 256, 0, s, P);
-    WV_CHECK(scan_exclusive_u32(P.flag, P.pos, P.n, P.n31, u32tmp, s));
+    WV_LAUNCH("plan_buckets", k_plan_buckets, 1, 32, 0, s, P);
     WV_LAUNCH("plan_scatter", k_plan_scatter, gp, 256, 0, s, P);
     const size_t ns = (size_t)P.n * P.rows_pp;
     WV_LAUNCH("plan_segments", k_plan_segments, (unsigned)((ns + 255) / 256), 256, 0, s, P);
@@ -687,7 +718,7 @@ constexpr size_t kNaScanTmp = kNaSegs / 4096 + 2;  // scan_tmp_elems bound for k
 constexpr size_t kNaBytes =
     na_align(kNoAllocMaxPrimes * sizeof(PrimeCtx)) + 2 * na_align(kNoAllocMaxPrimes * 4) +
     2 * na_align(kNaSegs * 8) + 2 * na_align(kNaSegs * 4) +
-    na_align(kNaSegs * kNoAllocTiles * sizeof(ulonglong2)) + na_align(kNaScanTmp * 4) + 256;
+    na_align(kNaSegs * kNoAllocTiles * sizeof(ulonglong2)) + na_align(kNaScanTmp * 4) + 1024;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
@@ -763,8 +794,9 @@ wv_status residues_noalloc(const uint64_t *d_primes, size_t n, uint64_t *d_out_b
   P.seg_first = (uint32_t *)carve(kNaSegs * 4);
   P.partials = (ulonglong2 *)carve(kNaSegs * kNoAllocTiles * sizeof(ulonglong2));
   uint32_t *u32tmp = (uint32_t *)carve(kNaScanTmp * 4);
-  uint32_t *scal = (uint32_t *)carve(256);
+  uint32_t *scal = (uint32_t *)carve(256 * sizeof(uint32_t));
   if (off > kNaBytes) return set_error(WV_EINVAL, "internal: no-alloc scratch layout overflow");
+  P.bk = scal + 64;
   P.n31 = scal + 0;
   P.total_tiles = scal + 1;
   P.split_tile = scal + 2;
@@ -776,8 +808,9 @@ wv_status residues_noalloc(const uint64_t *d_primes, size_t n, uint64_t *d_out_b
 
   const unsigned gp = (P.n + 255) / 256;
   const size_t ns = (size_t)P.n * P.rows_pp;
+  WV_CUDA(cudaMemsetAsync(P.bk, 0, 192 * sizeof(uint32_t), s));
   k_plan_prime<<<gp, 256, 0, s>>>(P);
-  WV_CHECK(scan_exclusive_u32_bare(P.flag, P.pos, P.n, P.n31, u32tmp, s));
+  k_plan_buckets<<<1, 32, 0, s>>>(P);
   k_plan_scatter<<<gp, 256, 0, s>>>(P);
   k_plan_segments<<<(unsigned)((ns + 255) / 256), 256, 0, s>>>(P);
   WV_CHECK(scan_exclusive_u32_bare(P.seg_tiles, P.seg_first, ns, P.total_tiles, u32tmp, s));

@@ -136,8 +136,12 @@ void prof_begin(const char *name, cudaStream_t s) {
   }
   it->second.launches++;
   if (g_prof_on) {
-    t_begin_ev = take_event();
-    cudaEventRecord(t_begin_ev, s);
+    // no timing events inside a stream capture: they would become graph nodes
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+      t_begin_ev = take_event();
+      cudaEventRecord(t_begin_ev, s);
+    }
   }
 }
 void prof_end(const char *name, cudaStream_t s) {

@@ -36,6 +36,11 @@ class wv_hit(ctypes.Structure):
     _fields_ = [("p", ctypes.c_uint64), ("kind", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
 
 
+class wv_request(ctypes.Structure):
+    _fields_ = [("d_primes", ctypes.c_void_p), ("n", ctypes.c_size_t),
+                ("d_out_b", ctypes.c_void_p), ("d_out_e", ctypes.c_void_p)]
+
+
 class wv_options(ctypes.Structure):
     _fields_ = [("cong_b", ctypes.c_int), ("cong_e", ctypes.c_int), ("block", ctypes.c_int),
                 ("ilp", ctypes.c_int), ("tile_terms", ctypes.c_int), ("max_tiles", ctypes.c_int),
@@ -75,6 +80,10 @@ _SIGS = {
     "wv_profile_launches": ([], _u64),
     "wv_count_terms": ([_pu64, _sz, _i32, _i32, _pu64, _pu64], _i32),
     "wv_diag_throughput": ([_i32, _i32, ctypes.POINTER(ctypes.c_double)], _i32),
+    "wv_batch_create": ([ctypes.c_void_p, _sz, ctypes.POINTER(wv_options), ctypes.POINTER(_vp)], _i32),
+    "wv_batch_run": ([_vp, _vp], _i32),
+    "wv_batch_info": ([_vp, _psz, _psz, _psz], _i32),
+    "wv_batch_destroy": ([_vp], _i32),
 }
 
 
@@ -287,3 +296,49 @@ def wv_diag_throughput(op, iters: int = 4096) -> float:
     v = ctypes.c_double()
     _check(load().wv_diag_throughput(DIAG_OPS.get(op, op), iters, ctypes.byref(v)))
     return v.value
+
+
+class Batch:
+    """Handle of a captured batch; keeps the request tensors alive."""
+
+    def __init__(self, handle, tensors):
+        self.handle = handle
+        self._tensors = tensors
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.wv_batch_destroy(self.handle)
+            self.handle = None
+
+
+def wv_batch_create(requests, options: dict | None = None) -> Batch:
+    """requests: list of (d_primes, d_out_b, d_out_e) device tensors (outputs may be None)."""
+    arr = (wv_request * len(requests))()
+    keep = []
+    for i, (dp, ob, oe) in enumerate(requests):
+        arr[i].d_primes = _ptr(dp).value if dp.numel() else None
+        arr[i].n = dp.numel()
+        arr[i].d_out_b = _ptr(ob).value if ob is not None else None
+        arr[i].d_out_e = _ptr(oe).value if oe is not None else None
+        keep += [dp, ob, oe]
+    h = ctypes.c_void_p()
+    _check(load().wv_batch_create(ctypes.cast(arr, ctypes.c_void_p), len(requests), _options(options),
+                                  ctypes.byref(h)))
+    return Batch(h, keep)
+
+
+def wv_batch_run(batch: Batch, stream=None) -> None:
+    _check(load().wv_batch_run(batch.handle, _stream(stream)))
+
+
+def wv_batch_info(batch: Batch):
+    """(requests, primes, graph nodes)."""
+    a, b, c = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+    _check(load().wv_batch_info(batch.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def wv_batch_destroy(batch: Batch) -> None:
+    if batch.handle:
+        _check(load().wv_batch_destroy(batch.handle))
+        batch.handle = None
