@@ -482,6 +482,201 @@ __device__ __forceinline__ void tile_m64(const PrimeCtx &ctx, uint64_t start, ui
   r1 = a1;
 }
 
+// ---- grouped accumulation for 2^30 <= p < 2^37 ------------------------------
+// Montgomery with R = 2^64 done as two 32-bit rounds on unsigned words:
+// p = p0 + p1 2^32 (p1 < 32), q = -p^-1 mod 2^32.  A product T = c g is held
+// as a low word T0 and a 64-bit rest TY (T = T0 + TY 2^32); each round adds
+// m p with m = (low word) q, which clears the low word exactly.  For
+// c < 2^38 and g < 2^53 every intermediate fits its word and the result is
+// below p + 2^24 (one conditional subtraction makes it canonical).
+//
+// The group polynomials of the grouped scheme above are stepped with plain
+// 64-bit additions and no reduction; every kM64Block groups the tables are
+// brought back below 10 p by an approximate Barrett step (quotient from the
+// high word times floor(2^62 / p)).  Starting below 10 p, a degree-6 table
+// stays below 10 p C(8+6, 6) < 2^52 over a block, inside the product bound.
+constexpr uint32_t kM64Block = 8;
+
+struct M64K {
+  uint32_t p0, p1, q, mhi;  // mhi = floor(2^62 / p)
+  uint64_t p;
+};
+
+__device__ __forceinline__ uint64_t umul_wide(uint32_t a, uint32_t b) {
+  uint64_t d;
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(d) : "r"(a), "r"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t umad_wide(uint32_t a, uint32_t b, uint64_t c) {
+  uint64_t d;
+  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ uint32_t ulo(uint64_t v) {
+  uint32_t lo;
+  asm("{\n\t.reg .b32 t;\n\tmov.b64 {%0, t}, %1;\n\t}" : "=r"(lo) : "l"(v));
+  return lo;
+}
+__device__ __forceinline__ uint32_t uhi(uint64_t v) {
+  uint32_t hi;
+  asm("{\n\t.reg .b32 t;\n\tmov.b64 {t, %0}, %1;\n\t}" : "=r"(hi) : "l"(v));
+  return hi;
+}
+__device__ __forceinline__ uint64_t upack(uint32_t lo, uint32_t hi) {
+  uint64_t v;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(v) : "r"(lo), "r"(hi));
+  return v;
+}
+
+// (T0 + TY 2^32) 2^-64 mod p, result < p + 2^24
+__device__ __forceinline__ uint64_t m64_redc2(uint32_t T0, uint64_t TY, const M64K &K) {
+  const uint32_t m0 = T0 * K.q;
+  const uint64_t A = umad_wide(m0, K.p0, (uint64_t)T0);       // low word is 0
+  const uint64_t U = umad_wide(m0, K.p1, TY) + uhi(A);        // (T + m0 p) / 2^32
+  const uint32_t m1 = ulo(U) * K.q;
+  const uint64_t B = umad_wide(m1, K.p0, (uint64_t)ulo(U));   // low word is 0
+  return umad_wide(m1, K.p1, (uint64_t)uhi(U)) + uhi(B);      // (U + m1 p) / 2^32
+}
+// T = c g as (T0, TY); c < 2^38, g < 2^53
+__device__ __forceinline__ void m64_prod(uint64_t c, uint64_t g, uint32_t &T0, uint64_t &TY) {
+  const uint32_t c0 = ulo(c), c1 = uhi(c), g0 = ulo(g), g1 = uhi(g);
+  const uint64_t X = umul_wide(c0, g0);
+  T0 = ulo(X);
+  uint64_t Y = umad_wide(c0, g1, (uint64_t)uhi(X));
+  Y = umad_wide(c1, g0, Y);
+  TY = upack(ulo(Y), uhi(Y) + c1 * g1);
+}
+// T = ca ga + cb gb as (T0, TY)
+__device__ __forceinline__ void m64_prod2(uint64_t ca, uint64_t ga, uint64_t cb, uint64_t gb,
+                                          uint32_t &T0, uint64_t &TY) {
+  const uint32_t a0 = ulo(ca), a1 = uhi(ca), x0 = ulo(ga), x1 = uhi(ga);
+  const uint32_t b0 = ulo(cb), b1 = uhi(cb), y0 = ulo(gb), y1 = uhi(gb);
+  const uint64_t Xa = umul_wide(a0, x0);
+  const uint64_t Xb = umad_wide(b0, y0, (uint64_t)ulo(Xa));
+  T0 = ulo(Xb);
+  uint64_t Y = umad_wide(a0, x1, (uint64_t)uhi(Xa));
+  Y = umad_wide(a1, x0, Y);
+  Y = umad_wide(b0, y1, Y);
+  Y = umad_wide(b1, y0, Y) + uhi(Xb);
+  TY = upack(ulo(Y), uhi(Y) + a1 * x1 + b1 * y1);
+}
+// v < 2^64  ->  v' = v (mod p) with v' < 10 p
+__device__ __forceinline__ uint64_t m64_shrink(uint64_t v, const M64K &K) {
+  const uint64_t qq = umul_wide(uhi(v), K.mhi) >> 30;  // <= floor(v / p), short by < 10
+  const uint32_t q0 = ulo(qq), q1 = uhi(qq);
+  const uint64_t qp = umul_wide(q0, K.p0) + ((uint64_t)(q0 * K.p1 + q1 * K.p0) << 32);
+  return v - qp;
+}
+
+template <int ILP, bool CUBES>
+__device__ __forceinline__ void tile_m64_grouped(const PrimeCtx &ctx, uint64_t start, uint64_t n,
+                                                 int64_t &r0, int64_t &r1) {
+  constexpr int K = CUBES ? 2 : 3;
+  constexpr int EX = CUBES ? 3 : 2;
+  constexpr int DA = K * EX;
+  constexpr int DB = (K - 1) * EX;
+  const int lane = threadIdx.x & 31;
+  const Mont M(ctx);
+  M64K KK;
+  KK.p = ctx.p;
+  KK.p0 = (uint32_t)ctx.p;
+  KK.p1 = (uint32_t)(ctx.p >> 32);
+  KK.q = 0u - (uint32_t)ctx.q;  // -p^-1 mod 2^32
+  KK.mhi = (uint32_t)((1ull << 62) / ctx.p);
+  const uint64_t nch = 32 * ILP;
+  const uint64_t len = n / nch;
+  const uint32_t rem = (uint32_t)(n - len * nch);
+  const uint64_t G = len / K;
+  uint64_t c0[ILP], c1[ILP], ga[ILP][DA + 1], gb[ILP][DB + 1];
+  uint64_t s_tail[ILP];
+  uint32_t n_tail[ILP];
+#pragma unroll
+  for (int k = 0; k < ILP; ++k) {
+    const uint32_t ch = k * 32 + lane;
+    const uint64_t s = start + ch * len + (ch < rem ? ch : rem);
+    const uint64_t L = len + (ch < rem ? 1 : 0);
+    s_tail[k] = s + G * K;
+    n_tail[k] = (uint32_t)(L - G * K);
+    int64_t va[DA + 1], vb[DB + 1];
+#pragma unroll
+    for (int i = 0; i <= DA; ++i) {
+      int64_t a, b;
+      group_poly<K, EX>(M, s + (uint64_t)i * K, a, b);
+      va[i] = a;
+      if (i <= DB) vb[i] = b;
+    }
+#pragma unroll
+    for (int j = 1; j <= DA; ++j)
+#pragma unroll
+      for (int i = DA; i >= j; --i) va[i] = M.sub(va[i], va[i - 1]);
+#pragma unroll
+    for (int j = 1; j <= DB; ++j)
+#pragma unroll
+      for (int i = DB; i >= j; --i) vb[i] = M.sub(vb[i], vb[i - 1]);
+#pragma unroll
+    for (int i = 0; i <= DA; ++i) ga[k][i] = (uint64_t)va[i];
+#pragma unroll
+    for (int i = 0; i <= DB; ++i) gb[k][i] = (uint64_t)vb[i];
+    c0[k] = ctx.one;
+    c1[k] = 0;
+  }
+  for (uint64_t g = 0; g < G;) {
+    const uint32_t nb = (G - g < kM64Block) ? (uint32_t)(G - g) : kM64Block;
+#pragma unroll 1
+    for (uint32_t r = 0; r < nb; ++r) {
+#pragma unroll
+      for (int k = 0; k < ILP; ++k) {
+        uint32_t T0;
+        uint64_t TY;
+        m64_prod(c0[k], ga[k][0], T0, TY);
+        const uint64_t n0 = m64_redc2(T0, TY, KK);
+        m64_prod2(c1[k], ga[k][0], c0[k], gb[k][0], T0, TY);
+        c1[k] = m64_redc2(T0, TY, KK);
+        c0[k] = n0;
+#pragma unroll
+        for (int j = 0; j < DA; ++j) ga[k][j] += ga[k][j + 1];
+#pragma unroll
+        for (int j = 0; j < DB; ++j) gb[k][j] += gb[k][j + 1];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < ILP; ++k) {
+#pragma unroll
+      for (int j = 0; j < DA; ++j) ga[k][j] = m64_shrink(ga[k][j], KK);
+#pragma unroll
+      for (int j = 0; j < DB; ++j) gb[k][j] = m64_shrink(gb[k][j], KK);
+    }
+    g += nb;
+  }
+  // canonical accumulators, then the last (at most K) terms one at a time
+  int64_t a0 = 0, a1 = 0;
+#pragma unroll
+  for (int k = 0; k < ILP; ++k) {
+    int64_t x0 = (int64_t)(c0[k] >= ctx.p ? c0[k] - ctx.p : c0[k]);
+    int64_t x1 = (int64_t)(c1[k] >= ctx.p ? c1[k] - ctx.p : c1[k]);
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      if ((uint32_t)i < n_tail[k]) {
+        const int64_t b = M.to_mont((int64_t)(s_tail[k] + i));
+        int64_t tm = M.mul(b, b);
+        if (EX == 3) tm = M.mul(tm, b);
+        const int64_t t = M.from_mont(tm);
+        x1 = M.add(M.mul(x1, t), x0);  // REDC(c1 t) + c0, as in eqn 3.12's single step
+        x0 = M.mul(x0, t);
+      }
+    }
+    if (k == 0) {
+      a0 = x0;
+      a1 = x1;
+    } else {
+      M.combine(a0, a1, x0, x1);
+    }
+  }
+  warp_merge(M, a0, a1);
+  r0 = a0;
+  r1 = a1;
+}
+
 // ------------------------------------------------------------------ accumulate
 template <bool WIDE, int ILP, int AR>
 __global__ void __launch_bounds__(kAccThreads) k_accumulate(Plan P) {
@@ -524,6 +719,9 @@ __global__ void __launch_bounds__(kAccThreads) k_accumulate(Plan P) {
     } else if (!WIDE) {
       if (j < P.rows_b) tile_m31<ILP, true, AS>(ctx, start, n, r0, r1);
       else tile_m31<ILP, false, AS>(ctx, start, n, r0, r1);
+    } else if (AR >= 9 && grp_ok) {
+      if (j < P.rows_b) tile_m64_grouped<ILP, true>(ctx, start, n, r0, r1);
+      else tile_m64_grouped<ILP, false>(ctx, start, n, r0, r1);
     } else {
       if (j < P.rows_b) tile_m64<ILP, true>(ctx, start, n, r0, r1);
       else tile_m64<ILP, false>(ctx, start, n, r0, r1);
@@ -604,7 +802,7 @@ template <bool WIDE>
 static wv_status launch_accumulate(const Plan &P, const ResidueConfig &cfg, int sms, cudaStream_t s) {
   const char *name = WIDE ? "accumulate_m64" : "accumulate_m31";
   void (*kern)(Plan) = nullptr;
-  const int ar = WIDE ? 1 : cfg.arith;
+  const int ar = WIDE ? (cfg.arith >= 9 ? 9 : 1) : cfg.arith;
 #define WV_PICK(I)                                                          \
   (ar == 1 ? k_accumulate<WIDE, I, 1> : ar == 2 ? k_accumulate<WIDE, I, 2> \
    : ar == 3 ? k_accumulate<WIDE, I, 3> : ar == 4 ? k_accumulate<WIDE, I, 4> \

@@ -259,3 +259,15 @@ def test_search_near_miss_table_windows():
                 continue
             near = api.search(p - 2000, p + 2000, near=50)
             assert (p, bit) in [(q, k & bit) for q, k in near]
+
+
+def test_wide_path_formulations_agree_up_to_2_37():
+    """The grouped 64-bit path against the plain 64-bit Montgomery path, on primes
+    just above 2^30, near 1e10, and just below 2^37 (the top of the range)."""
+    ps = np.concatenate([u64(api.sieve(2**30, 2**30 + 2000)), u64(api.sieve(10**10, 10**10 + 2000)),
+                         u64(api.sieve(2**37 - 2000, 2**37))])
+    ref_b, ref_e = gpu_residues(ps, {"arith": 1})
+    for opt in ({}, {"ilp": 1}, {"tile_terms": 20000, "max_tiles": 256}):
+        gb, ge = gpu_residues(ps, opt)
+        assert np.array_equal(gb, ref_b), opt
+        assert np.array_equal(ge, ref_e), opt
