@@ -328,6 +328,139 @@ def gpu_arm(args):
     return 0
 
 
+# ---------------------------------------------------------------- batch / serve
+def _pctl(xs, q):
+    import numpy as np
+    return float(np.percentile(np.asarray(xs), q)) if len(xs) else None
+
+
+def batch_arm(args):
+    """64 seeded requests of uneven cost: one graph-captured batch vs one call per request."""
+    import numpy as np
+    import torch
+
+    from paper_2101_11157_gb300 import wv, workloads as W
+    torch.cuda.set_device(0)
+    reqs_np = W.batch_requests(seed=7, k=args.requests, max_len=args.max_len)
+    reqs = []
+    for a in reqs_np:
+        d = torch.from_numpy(a.view(np.int64)).cuda()
+        reqs.append((d, torch.empty_like(d), torch.empty_like(d)))
+    n = sum(a.size for a in reqs_np)
+    tb = te = 0
+    for a in reqs_np:
+        x, y = wv.wv_count_terms(a)
+        tb, te = tb + x, te + y
+    stream = torch.cuda.current_stream()
+    b = wv.wv_batch_create(reqs)
+    _, _, nodes = wv.wv_batch_info(b)
+
+    def timed(fn, k):
+        ms = []
+        for _ in range(k):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms
+
+    run_batch = lambda: wv.wv_batch_run(b, stream)
+    run_plain = lambda: [wv.wv_residues_pm3(d, rb, re, stream) for d, rb, re in reqs]
+    for _ in range(args.warmup):
+        run_batch()
+    torch.cuda.synchronize()
+    ms_b = timed(run_batch, args.steps)
+    out_b = [(rb.clone(), re.clone()) for _, rb, re in reqs]
+    run_plain()
+    torch.cuda.synchronize()
+    ms_p = timed(run_plain, args.steps)
+    same = all(torch.equal(rb, x) and torch.equal(re, y) for (_, rb, re), (x, y) in zip(reqs, out_b))
+    mb, mp = statistics.median(ms_b), statistics.median(ms_p)
+    line = {"workload": "batch", "metric": "primes/s, 64 requests in one launch vs one launch per request",
+            "value": n / (mb / 1e3), "unit": "primes/s", "plain_value": n / (mp / 1e3),
+            "speedup_vs_plain": mp / mb, "ms_per_step": mb, "plain_ms_per_step": mp,
+            "modmul_per_s": 2 * (tb + te) / (mb / 1e3), "steps": args.steps, "warmup": args.warmup,
+            "identical_results": bool(same), "graph_nodes": nodes,
+            "config": {"requests": len(reqs_np), "primes": int(n), "terms": int(tb + te),
+                       "lengths": "floor(2^U(0,12)) clamped to [1, %d]" % args.max_len,
+                       "primes_from": "next_prime(10^U(5,10)), seed 7"}}
+    wv.wv_batch_destroy(b)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def serve_arm(args):
+    """A seeded Poisson stream of range and single-prime queries, served with
+    continuous batching and, for comparison, one query at a time."""
+    import numpy as np
+    import torch
+
+    from paper_2101_11157_gb300 import api, wv, workloads as W
+    torch.cuda.set_device(0)
+    stream = W.serving_stream(seed=11, n=args.queries, rate=args.rate)
+    if args.max_range:
+        for q in stream:
+            if q["kind"] == "range":
+                q["hi"] = min(q["hi"], q["lo"] + args.max_range)
+    # served
+    srv = wv.wv_server_create(epoch_terms=args.epoch_terms)
+    t0 = time.perf_counter()
+    ids = []
+    for q in stream:
+        dt = q["t"] - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        ids.append(wv.wv_server_submit_range(srv, q["lo"], q["hi"]) if q["kind"] == "range"
+                   else wv.wv_server_submit_prime(srv, q["p"]))
+    infos = [wv.wv_server_wait(srv, i) for i in ids]
+    makespan = time.perf_counter() - t0
+    st = wv.wv_server_stats(srv)
+    served_res = [wv.wv_server_result(srv, i) for i in ids]
+    wv.wv_server_destroy(srv)
+    lat = [i["t_done"] - i["t_submit"] for i in infos]
+    n_primes = sum(i["n_primes"] for i in infos)
+    # plain: one query at a time, in arrival order
+    t0 = time.perf_counter()
+    lat_p = []
+    same = True
+    for q, res in zip(stream, served_res):
+        dt = q["t"] - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        if q["kind"] == "range":
+            lo = max(q["lo"], 5)
+            if q["hi"] > lo:
+                _, pr, rb, re = api.search(lo, q["hi"], with_residues=True)
+            else:
+                pr = rb = re = torch.empty(0, dtype=torch.int64, device="cuda")
+        else:
+            pr = torch.tensor([q["p"]], dtype=torch.int64, device="cuda")
+            rb, re = api.residues(pr)
+        torch.cuda.synchronize()
+        lat_p.append(time.perf_counter() - t0 - q["t"])
+        same = same and np.array_equal(api.to_u64(rb), res[1]) and np.array_equal(api.to_u64(re), res[2])
+    makespan_p = time.perf_counter() - t0
+    kinds = [q["kind"] for q in stream]
+
+    def stats(ls):
+        out = {}
+        for k in ("prime", "range"):
+            xs = [x for x, kk in zip(ls, kinds) if kk == k]
+            out[k] = {"p50_s": _pctl(xs, 50), "p99_s": _pctl(xs, 99), "n": len(xs)}
+        return out
+    line = {"workload": "serve", "metric": "primes/s and p50/p99 latency, continuous batching vs one query at a time",
+            "value": n_primes / makespan, "unit": "primes/s", "plain_value": n_primes / makespan_p,
+            "makespan_s": makespan, "plain_makespan_s": makespan_p,
+            "latency": stats(lat), "plain_latency": stats(lat_p), "identical_results": bool(same),
+            "server": st, "config": {"queries": len(stream), "rate_per_s": args.rate, "seed": 11,
+                                     "range_len_cap": args.max_range or None,
+                                     "epoch_terms": args.epoch_terms, "primes": int(n_primes)}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -336,9 +469,20 @@ def main():
     ap.add_argument("--impl", default="wv", choices=["wv", "reference"])
     ap.add_argument("--width", type=int, default=WIDTH, help="window width (smaller for profiling)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--workload", default="window", choices=["window", "batch", "serve"])
+    ap.add_argument("--requests", type=int, default=64, help="batch: number of requests")
+    ap.add_argument("--max-len", type=int, default=4096, help="batch: longest request")
+    ap.add_argument("--queries", type=int, default=256, help="serve: queries in the stream")
+    ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrivals per second")
+    ap.add_argument("--max-range", type=int, default=0, help="serve: cap on range length (0: none)")
+    ap.add_argument("--epoch-terms", type=float, default=4e10, help="serve: terms per epoch")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload == "batch":
+        return batch_arm(args)
+    if args.workload == "serve":
+        return serve_arm(args)
     return gpu_arm(args)
 
 

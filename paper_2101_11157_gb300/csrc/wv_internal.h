@@ -108,6 +108,44 @@ wv_status resolve_config(const wv_options *opt, bool want_b, bool want_e, Residu
 wv_status residues_device(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,
                           uint64_t *d_out_e, const ResidueConfig &cfg, cudaStream_t s);
 
+// ---- phases of one residue computation, for the serving loop
+struct Plan;  // device-side plan of one prime list (wv_residue.cu)
+struct EpochItem {
+  uint32_t plan;    // index into the epoch's plan array
+  uint32_t first;   // first tile of the item's range
+  uint32_t count;   // tiles in the range
+  uint32_t prefix;  // tiles of all earlier items
+};
+struct PlanState {
+  Plan *host = nullptr;     // host copy of the plan (device pointers inside)
+  void *blocks[16] = {};
+  int nblocks = 0;
+  size_t bytes = 0;         // device bytes held
+  uint32_t n = 0, total = 0, split = 0;  // primes, tiles, first 64-bit tile
+};
+// Allocate (stream-ordered) and plan n <= 65536 primes; asynchronous.
+wv_status plan_build(const uint64_t *d_primes, uint32_t n, const ResidueConfig &cfg,
+                     PlanState *ps, cudaStream_t s);
+// Device bytes plan_build will hold for n primes.
+size_t plan_bytes(uint32_t n, const ResidueConfig &cfg);
+// Synchronise s and read the plan's tile totals into ps.
+wv_status plan_totals(PlanState *ps, cudaStream_t s);
+// Copy the plan struct to device memory at d_plan (asynchronous).
+wv_status plan_upload(const PlanState *ps, Plan *d_plan, cudaStream_t s);
+size_t plan_struct_bytes();
+// Epoch launch over items (device array) of plans (device array).
+wv_status epoch_launch(bool wide, const EpochItem *d_items, uint32_t n_items, uint32_t total,
+                       const Plan *d_plans, uint32_t *d_counter, const ResidueConfig &cfg,
+                       int sms, cudaStream_t s);
+// One launch for items of both paths (bit 31 of EpochItem::plan marks 64-bit items).
+// `reserve_blocks` leaves room on the SMs for concurrent kernels of other streams.
+wv_status epoch_launch_mixed(const EpochItem *d_items, uint32_t n_items, uint32_t total,
+                             const Plan *d_plans, uint32_t *d_counter, const ResidueConfig &cfg,
+                             int sms, int reserve_blocks, cudaStream_t s);
+// Finalise every prime of the plan into d_out_b / d_out_e (asynchronous).
+wv_status plan_finalize(PlanState *ps, uint64_t *d_out_b, uint64_t *d_out_e, cudaStream_t s);
+void plan_free(PlanState *ps, cudaStream_t s);
+
 // Sieve primitives
 wv_status sieve_device(uint64_t lo, uint64_t hi, uint64_t *d_out, size_t cap,
                        uint64_t *count_host, cudaStream_t s);

@@ -678,6 +678,49 @@ __device__ __forceinline__ void tile_m64_grouped(const PrimeCtx &ctx, uint64_t s
 }
 
 // ------------------------------------------------------------------ accumulate
+// One warp tile g of plan P: find its (prime, row) segment, sum its range of
+// terms, merge the lanes, and store the tile's (c0, c1) pair.
+template <bool WIDE, int ILP, int AR>
+__device__ __forceinline__ void process_tile(const Plan &P, uint32_t g) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t nsegs = P.n * P.rows_pp;
+  // segment owning tile g: the last s with seg_first[s] <= g
+  uint32_t lo = 0, hi = nsegs;
+  while (hi - lo > 1) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (__ldg(&P.seg_first[mid]) <= g) lo = mid; else hi = mid;
+  }
+  const uint32_t s = lo;
+  const uint32_t slot = s / P.rows_pp, j = s - slot * P.rows_pp;
+  const PrimeCtx ctx = P.ctx[slot];
+  const uint32_t k = g - P.seg_first[s], T = P.seg_tiles[s];
+  const uint64_t cnt = P.seg_cnt[s];
+  const uint64_t b0 = cnt * k / T, b1 = cnt * (k + 1) / T;
+  const uint64_t start = P.seg_lo[s] + b0, n = b1 - b0;
+  int64_t r0, r1;
+  // single-term form used beside the grouped one
+  constexpr int AS = (AR == 5 || AR == 8 || AR == 9) ? 4 : AR;
+  const bool grp_ok = n >= 32ull * ILP * kGroupMinChain;
+  if (!WIDE && AR == 5 && grp_ok) {
+    if (j < P.rows_b) tile_m31_grouped<ILP, true, 5>(ctx, start, n, r0, r1);
+    else tile_m31_grouped<ILP, false, 5>(ctx, start, n, r0, r1);
+  } else if (!WIDE && AR >= 7 && grp_ok && j >= P.rows_b) {
+    tile_m31_grouped<ILP, false, 7>(ctx, start, n, r0, r1);
+  } else if (!WIDE && AR == 9 && grp_ok) {
+    tile_m31_grouped<ILP, true, 7>(ctx, start, n, r0, r1);
+  } else if (!WIDE) {
+    if (j < P.rows_b) tile_m31<ILP, true, AS>(ctx, start, n, r0, r1);
+    else tile_m31<ILP, false, AS>(ctx, start, n, r0, r1);
+  } else if (AR >= 9 && grp_ok) {
+    if (j < P.rows_b) tile_m64_grouped<ILP, true>(ctx, start, n, r0, r1);
+    else tile_m64_grouped<ILP, false>(ctx, start, n, r0, r1);
+  } else {
+    if (j < P.rows_b) tile_m64<ILP, true>(ctx, start, n, r0, r1);
+    else tile_m64<ILP, false>(ctx, start, n, r0, r1);
+  }
+  if (lane == 0) P.partials[g] = make_ulonglong2((unsigned long long)r0, (unsigned long long)r1);
+}
+
 template <bool WIDE, int ILP, int AR>
 __global__ void __launch_bounds__(kAccThreads) k_accumulate(Plan P) {
   const int lane = threadIdx.x & 31;
@@ -685,48 +728,59 @@ __global__ void __launch_bounds__(kAccThreads) k_accumulate(Plan P) {
   const uint32_t t_begin = WIDE ? split : 0u, t_end = WIDE ? total : split;
   const uint32_t ntiles = t_end - t_begin;
   uint32_t *counter = P.counters + (WIDE ? 1 : 0);
-  const uint32_t nsegs = P.n * P.rows_pp;
   for (;;) {
     uint32_t g = 0;
     if (lane == 0) g = atomicAdd(counter, 1u);
     g = __shfl_sync(0xffffffffu, g, 0);
     if (g >= ntiles) break;
-    g = t_end - 1 - g;  // largest slots (largest primes of an ascending list) first
-    // segment owning tile g: the last s with seg_first[s] <= g
-    uint32_t lo = 0, hi = nsegs;
+    process_tile<WIDE, ILP, AR>(P, t_end - 1 - g);  // largest primes first
+  }
+}
+
+// Epoch form: tiles of several plans (one per request of a serving loop),
+// given as items {plan, first tile, count, prefix}; the items' tiles are
+// taken from one counter, each item from its top tile down.
+template <bool WIDE, int ILP, int AR>
+__global__ void __launch_bounds__(kAccThreads)
+    k_epoch(const EpochItem *items, uint32_t n_items, uint32_t total, const Plan *plans,
+            uint32_t *counter) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    uint32_t g = 0;
+    if (lane == 0) g = atomicAdd(counter, 1u);
+    g = __shfl_sync(0xffffffffu, g, 0);
+    if (g >= total) break;
+    uint32_t lo = 0, hi = n_items;
     while (hi - lo > 1) {
       uint32_t mid = (lo + hi) >> 1;
-      if (__ldg(&P.seg_first[mid]) <= g) lo = mid; else hi = mid;
+      if (__ldg(&items[mid].prefix) <= g) lo = mid; else hi = mid;
     }
-    const uint32_t s = lo;
-    const uint32_t slot = s / P.rows_pp, j = s - slot * P.rows_pp;
-    const PrimeCtx ctx = P.ctx[slot];
-    const uint32_t k = g - P.seg_first[s], T = P.seg_tiles[s];
-    const uint64_t cnt = P.seg_cnt[s];
-    const uint64_t b0 = cnt * k / T, b1 = cnt * (k + 1) / T;
-    const uint64_t start = P.seg_lo[s] + b0, n = b1 - b0;
-    int64_t r0, r1;
-    // single-term form used beside the grouped one
-    constexpr int AS = (AR == 5 || AR == 8 || AR == 9) ? 4 : AR;
-    const bool grp_ok = n >= 32ull * ILP * kGroupMinChain;
-    if (!WIDE && AR == 5 && grp_ok) {
-      if (j < P.rows_b) tile_m31_grouped<ILP, true, 5>(ctx, start, n, r0, r1);
-      else tile_m31_grouped<ILP, false, 5>(ctx, start, n, r0, r1);
-    } else if (!WIDE && AR >= 7 && grp_ok && j >= P.rows_b) {
-      tile_m31_grouped<ILP, false, 7>(ctx, start, n, r0, r1);
-    } else if (!WIDE && AR == 9 && grp_ok) {
-      tile_m31_grouped<ILP, true, 7>(ctx, start, n, r0, r1);
-    } else if (!WIDE) {
-      if (j < P.rows_b) tile_m31<ILP, true, AS>(ctx, start, n, r0, r1);
-      else tile_m31<ILP, false, AS>(ctx, start, n, r0, r1);
-    } else if (AR >= 9 && grp_ok) {
-      if (j < P.rows_b) tile_m64_grouped<ILP, true>(ctx, start, n, r0, r1);
-      else tile_m64_grouped<ILP, false>(ctx, start, n, r0, r1);
-    } else {
-      if (j < P.rows_b) tile_m64<ILP, true>(ctx, start, n, r0, r1);
-      else tile_m64<ILP, false>(ctx, start, n, r0, r1);
+    const EpochItem it = items[lo];
+    process_tile<WIDE, ILP, AR>(plans[it.plan], it.first + it.count - 1 - (g - it.prefix));
+  }
+}
+
+// Epoch form with both arithmetic paths in one launch: items with bit 31 of
+// `plan` set are 64-bit-path tiles.  One launch (and one tail) per epoch.
+template <int ILP>
+__global__ void __launch_bounds__(kAccThreads)
+    k_epoch_mixed(const EpochItem *items, uint32_t n_items, uint32_t total, const Plan *plans,
+                  uint32_t *counter) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    uint32_t g = 0;
+    if (lane == 0) g = atomicAdd(counter, 1u);
+    g = __shfl_sync(0xffffffffu, g, 0);
+    if (g >= total) break;
+    uint32_t lo = 0, hi = n_items;
+    while (hi - lo > 1) {
+      uint32_t mid = (lo + hi) >> 1;
+      if (__ldg(&items[mid].prefix) <= g) lo = mid; else hi = mid;
     }
-    if (lane == 0) P.partials[g] = make_ulonglong2((unsigned long long)r0, (unsigned long long)r1);
+    const EpochItem it = items[lo];
+    const uint32_t tile = it.first + it.count - 1 - (g - it.prefix);
+    if (it.plan >> 31) process_tile<true, ILP, 9>(plans[it.plan & 0x7fffffffu], tile);
+    else process_tile<false, ILP, 9>(plans[it.plan], tile);
   }
 }
 
@@ -900,6 +954,162 @@ wv_status residues_device(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,
     WV_LAUNCH("finalize", k_finalize, (unsigned)((warps * 32 + 255) / 256), 256, 0, s, P);
   }
   return WV_OK;
+}
+
+// ------------------------------------------------------------------ phases
+// The launch sequence of residues_device split into its phases, for callers
+// that interleave the accumulation of several prime lists (the serving loop):
+// plan_build -> plan_totals -> epoch_launch (any number of times, over any
+// tile ranges) -> plan_finalize -> plan_free.
+
+static void fill_rows(Plan &P, const ResidueConfig &cfg) {
+  uint32_t r = 0;
+  if (cfg.cong_b >= 0) {
+    const WvCongruence &c = kWvCongruences[cfg.cong_b];
+    for (int j = 0; j < c.nrows; ++j, ++r) {
+      const WvRow &w = kWvRows[c.row_offset + j];
+      P.xn[r] = w.xn; P.xd[r] = w.xd; P.yn[r] = w.yn; P.yd[r] = w.yd; P.coef[r] = w.coef;
+    }
+    P.rows_b = c.nrows;
+    P.lhs_b = c.lhs;
+  }
+  if (cfg.cong_e >= 0) {
+    const WvCongruence &c = kWvCongruences[cfg.cong_e];
+    for (int j = 0; j < c.nrows; ++j, ++r) {
+      const WvRow &w = kWvRows[c.row_offset + j];
+      P.xn[r] = w.xn; P.xd[r] = w.xd; P.yn[r] = w.yn; P.yd[r] = w.yd; P.coef[r] = w.coef;
+    }
+    P.rows_e = c.nrows;
+    P.lhs_e = c.lhs;
+  }
+  P.rows_pp = r;
+  P.tile_terms = (uint32_t)(cfg.tile_terms > 0 ? cfg.tile_terms : (1 << 20));
+  P.max_tiles = (uint32_t)(cfg.max_tiles > 0 ? cfg.max_tiles : 8);
+}
+
+static size_t rows_of(const ResidueConfig &cfg) {
+  size_t r = 0;
+  if (cfg.cong_b >= 0) r += kWvCongruences[cfg.cong_b].nrows;
+  if (cfg.cong_e >= 0) r += kWvCongruences[cfg.cong_e].nrows;
+  return r;
+}
+
+size_t plan_bytes(uint32_t n, const ResidueConfig &cfg) {
+  const size_t ns = (size_t)n * rows_of(cfg);
+  const size_t mt = cfg.max_tiles > 0 ? cfg.max_tiles : 8;
+  return n * (sizeof(PrimeCtx) + 8) + ns * (8 + 8 + 4 + 4) + ns * mt * sizeof(ulonglong2) +
+         scan_tmp_elems(ns) * 4 + 1024 + 16 * 256;
+}
+
+size_t plan_struct_bytes() { return sizeof(Plan); }
+
+wv_status plan_build(const uint64_t *d_primes, uint32_t n, const ResidueConfig &cfg, PlanState *ps,
+                     cudaStream_t s) {
+  if (n == 0 || n > 65536) return set_error(WV_EINVAL, "plan_build: n=%u not in [1, 65536]", n);
+  ps->host = new Plan();
+  Plan &P = *ps->host;
+  memset(&P, 0, sizeof P);
+  fill_rows(P, cfg);
+  const size_t ns = (size_t)n * P.rows_pp;
+  auto get = [&](void **p, size_t bytes) -> wv_status {
+    WV_CHECK(scratch_alloc(p, bytes + 256, s));
+    ps->blocks[ps->nblocks++] = *p;
+    ps->bytes += bytes + 256;
+    return WV_OK;
+  };
+  uint32_t *u32tmp = nullptr, *scal = nullptr;
+  WV_CHECK(get((void **)&P.ctx, n * sizeof(PrimeCtx)));
+  WV_CHECK(get((void **)&P.flag, n * 4));
+  WV_CHECK(get((void **)&P.seg_lo, ns * 8));
+  WV_CHECK(get((void **)&P.seg_cnt, ns * 8));
+  WV_CHECK(get((void **)&P.seg_tiles, ns * 4));
+  WV_CHECK(get((void **)&P.seg_first, ns * 4));
+  WV_CHECK(get((void **)&P.partials, ns * P.max_tiles * sizeof(ulonglong2)));
+  WV_CHECK(get((void **)&u32tmp, scan_tmp_elems(ns) * 4));
+  WV_CHECK(get((void **)&scal, 1024));
+  P.pos = nullptr;
+  P.bk = scal + 64;
+  P.n31 = scal + 0;
+  P.total_tiles = scal + 1;
+  P.split_tile = scal + 2;
+  P.counters = scal + 4;
+  P.n = n;
+  P.primes = d_primes;
+  ps->n = n;
+  const unsigned gp = (n + 255) / 256;
+  WV_CUDA(cudaMemsetAsync(P.bk, 0, 192 * sizeof(uint32_t), s));
+  WV_LAUNCH("plan_prime", k_plan_prime, gp, 256, 0, s, P);
+  WV_LAUNCH("plan_buckets", k_plan_buckets, 1, 32, 0, s, P);
+  WV_LAUNCH("plan_scatter", k_plan_scatter, gp, 256, 0, s, P);
+  WV_LAUNCH("plan_segments", k_plan_segments, (unsigned)((ns + 255) / 256), 256, 0, s, P);
+  WV_CHECK(scan_exclusive_u32(P.seg_tiles, P.seg_first, ns, P.total_tiles, u32tmp, s));
+  WV_LAUNCH("plan_split", k_plan_split, 1, 1, 0, s, P);
+  return WV_OK;
+}
+
+wv_status plan_totals(PlanState *ps, cudaStream_t s) {
+  uint32_t v[3] = {0, 0, 0};
+  WV_CUDA(cudaMemcpyAsync(v, ps->host->n31, 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  WV_CUDA(cudaStreamSynchronize(s));
+  ps->total = v[1];
+  ps->split = v[2];
+  return WV_OK;
+}
+
+wv_status plan_upload(const PlanState *ps, Plan *d_plan, cudaStream_t s) {
+  WV_CUDA(cudaMemcpyAsync(d_plan, ps->host, sizeof(Plan), cudaMemcpyHostToDevice, s));
+  return WV_OK;
+}
+
+wv_status epoch_launch(bool wide, const EpochItem *d_items, uint32_t n_items, uint32_t total,
+                       const Plan *d_plans, uint32_t *d_counter, const ResidueConfig &cfg, int sms,
+                       cudaStream_t s) {
+  if (total == 0) return WV_OK;
+  void (*kern)(const EpochItem *, uint32_t, uint32_t, const Plan *, uint32_t *) =
+      wide ? (cfg.ilp == 1 ? k_epoch<true, 1, 9> : k_epoch<true, 2, 9>)
+           : (cfg.ilp == 1 ? k_epoch<false, 1, 9> : k_epoch<false, 2, 9>);
+  int occ = 0;
+  WV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kAccThreads, 0));
+  if (occ < 1) occ = 1;
+  WV_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(uint32_t), s));
+  WV_LAUNCH(wide ? "epoch_m64" : "epoch_m31", kern, (unsigned)(sms * occ), kAccThreads, 0, s,
+            d_items, n_items, total, d_plans, d_counter);
+  return WV_OK;
+}
+
+wv_status epoch_launch_mixed(const EpochItem *d_items, uint32_t n_items, uint32_t total,
+                             const Plan *d_plans, uint32_t *d_counter, const ResidueConfig &cfg,
+                             int sms, int reserve_blocks, cudaStream_t s) {
+  if (total == 0) return WV_OK;
+  void (*kern)(const EpochItem *, uint32_t, uint32_t, const Plan *, uint32_t *) =
+      cfg.ilp == 1 ? k_epoch_mixed<1> : k_epoch_mixed<2>;
+  int occ = 0;
+  WV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kAccThreads, 0));
+  if (occ < 1) occ = 1;
+  WV_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(uint32_t), s));
+  int grid = sms * occ - reserve_blocks;
+  if (grid < 1) grid = 1;
+  WV_LAUNCH("epoch", kern, (unsigned)grid, kAccThreads, 0, s, d_items, n_items, total, d_plans,
+            d_counter);
+  return WV_OK;
+}
+
+wv_status plan_finalize(PlanState *ps, uint64_t *d_out_b, uint64_t *d_out_e, cudaStream_t s) {
+  Plan P = *ps->host;
+  P.out_b = P.rows_b ? d_out_b : nullptr;
+  P.out_e = P.rows_e ? d_out_e : nullptr;
+  const uint32_t nk = (P.rows_b ? 1u : 0u) + (P.rows_e ? 1u : 0u);
+  const size_t warps = (size_t)P.n * nk;
+  WV_LAUNCH("finalize", k_finalize, (unsigned)((warps * 32 + 255) / 256), 256, 0, s, P);
+  return WV_OK;
+}
+
+void plan_free(PlanState *ps, cudaStream_t s) {
+  for (int i = ps->nblocks - 1; i >= 0; --i) scratch_free(ps->blocks[i], s);
+  ps->nblocks = 0;
+  ps->bytes = 0;
+  delete ps->host;
+  ps->host = nullptr;
 }
 
 // ------------------------------------------------------------------ no-alloc

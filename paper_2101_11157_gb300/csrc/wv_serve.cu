@@ -1,0 +1,634 @@
+// wv_serve.cu -- step a9: a continuous-batching serving loop (see include/wv_serve.h).
+//
+// One worker thread per server owns a CUDA stream and loops:
+//   1. admit pending queries while active slots, plan slots and the device
+//      memory budget allow (a range query is sieved on the device first);
+//      each admitted query gets its prime list, residue buffers and one plan
+//      per <= 65536 primes, all resident;
+//   2. run one epoch: the active queries, ordered by remaining work
+//      (smallest first), contribute ranges of their not-yet-run tiles until
+//      the epoch's term budget is filled; one persistent launch per
+//      arithmetic path runs all of them (k_epoch);
+//   3. finalise every plan whose tiles are all done; a query whose plans are
+//      all finalised is copied to the host, marked done and its device memory
+//      released.
+// Queries arriving meanwhile are admitted at the next iteration, so their
+// tiles share epochs with long-running ones.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/wv_serve.h"
+#include "wv_internal.h"
+#include "wv_tables.h"
+
+namespace wv {
+
+constexpr uint32_t kPlanPrimes = 65536;  // primes per plan
+constexpr uint32_t kMaxPlans = 2048;     // plan slots per server
+constexpr double kWideWeight = 3.0;      // cost of a 64-bit-path term relative to a 32-bit one
+constexpr size_t kAdmitPerIter = 8;      // queries admitted per loop turn (epochs keep running meanwhile)
+constexpr double kMinEpochTerms = 5e9;   // shortest epoch
+// Epoch grids leave this many blocks' room so that admission work (sieve,
+// planner: a few small kernels) runs beside a running epoch instead of after it.
+constexpr int kReserveBlocks = 4;
+
+struct SChunk {
+  PlanState plan;
+  uint32_t off = 0, n = 0;
+  uint32_t slot = 0;       // index in the device plan array
+  int64_t last_epoch = -1; // last epoch that ran tiles of this plan
+  uint32_t hi31 = 0;       // 32-bit-path tiles [0, hi31) not yet run
+  uint32_t hi64 = 0;       // 64-bit-path tiles [split, hi64) not yet run
+  double tpt31 = 1, tpt64 = 1;  // estimated terms per tile
+  bool finalized = false;
+};
+
+struct SQuery {
+  uint64_t id = 0;
+  int kind = 0;
+  uint64_t lo = 0, hi = 0;
+  int state = 0;  // 0 pending, 1 active, 2 done, 3 failed, 4 cancelled
+  wv_status status = WV_OK;
+  std::string err;
+  double t_submit = 0, t_admit = 0, t_done = 0;
+  uint64_t *d_primes = nullptr, *d_rb = nullptr, *d_re = nullptr;
+  size_t n = 0, bytes = 0;
+  std::vector<SChunk> chunks;
+  std::vector<uint64_t> h_primes, h_rb, h_re;
+  uint64_t n_hits = 0;
+  double remaining = 0;
+};
+
+static uint64_t row_terms_host(const WvRow &r, uint64_t p) {
+  const uint64_t lo = (uint64_t)r.xn * p / r.xd + 1;
+  const uint64_t hi = (uint64_t)r.yn * p / r.yd + 1;
+  return hi > lo ? hi - lo : 0;
+}
+
+static void terms_host(const uint64_t *ps, size_t n, const ResidueConfig &cfg, double *t31,
+                       double *t64) {
+  double a = 0, b = 0;
+  for (size_t i = 0; i < n; ++i) {
+    const uint64_t p = ps[i];
+    if (p < 11 || p >= WV_P_MAX || !(p & 1)) continue;
+    uint64_t t = 0;
+    for (int kind = 0; kind < 2; ++kind) {
+      const int id = kind ? cfg.cong_e : cfg.cong_b;
+      if (id < 0) continue;
+      const WvCongruence &c = kWvCongruences[id];
+      for (int j = 0; j < c.nrows; ++j) t += row_terms_host(kWvRows[c.row_offset + j], p);
+    }
+    if (p < (1ull << 30)) a += (double)t;
+    else b += (double)t;
+  }
+  *t31 = a;
+  *t64 = b;
+}
+
+}  // namespace wv
+
+using namespace wv;
+
+struct wv_server_s {
+  wv_server_config cfg{};
+  int device = 0, sms = 0;
+  cudaStream_t st = nullptr;       // admission, finalisation, copies
+  cudaStream_t se[2] = {};         // epochs alternate between two streams
+  cudaEvent_t ev[2] = {};          // epoch completion
+  std::thread worker;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<SQuery *> pending;
+  std::vector<SQuery *> active;
+  std::unordered_map<uint64_t, SQuery *> queries;
+  bool stop = false;
+  uint64_t next_id = 1;
+  size_t bytes_in_use = 0;
+  Plan *d_plans = nullptr;
+  std::vector<uint32_t> free_slots;
+  EpochItem *d_items = nullptr, *h_items = nullptr;  // two halves, one per epoch stream
+  uint32_t *d_counter = nullptr;                     // 2 x 2 counters
+  ResidueConfig rcfg;
+  std::chrono::steady_clock::time_point t0;
+  uint64_t epochs = 0, tiles = 0;
+  uint32_t peak_active = 0;
+
+  double now() const {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+};
+
+namespace {
+
+void release_device(wv_server_s *S, SQuery *q) {
+  for (auto &c : q->chunks) {
+    if (c.plan.host) {
+      plan_free(&c.plan, S->st);
+      S->free_slots.push_back(c.slot);
+    }
+  }
+  q->chunks.clear();
+  scratch_free(q->d_primes, S->st);
+  scratch_free(q->d_rb, S->st);
+  scratch_free(q->d_re, S->st);
+  q->d_primes = q->d_rb = q->d_re = nullptr;
+}
+
+// Admit one query: sieve / copy its primes, allocate, plan.  Called by the
+// worker without the lock.  Returns false if it must wait (memory or slots).
+bool admit(wv_server_s *S, SQuery *q, size_t bytes_now, size_t free_slots, bool alone) {
+  wv_status st = WV_OK;
+  uint64_t n = 0;
+  if (q->kind == 0) {
+    st = sieve_device(q->lo, q->hi, nullptr, 0, &n, S->st);
+  } else {
+    n = 1;
+  }
+  if (st != WV_OK) {
+    q->state = 3;
+    q->status = st;
+    q->err = wv_last_error();
+    return true;
+  }
+  const size_t nplans = (size_t)((n + kPlanPrimes - 1) / kPlanPrimes);
+  size_t need = n * 24;
+  for (size_t i = 0; i < nplans; ++i) {
+    const uint32_t m = (uint32_t)std::min<uint64_t>(kPlanPrimes, n - i * kPlanPrimes);
+    need += plan_bytes(m, S->rcfg);
+  }
+  if (!alone && (bytes_now + need > S->cfg.mem_budget || nplans > free_slots)) return false;
+  if (nplans > free_slots) {  // cannot fit even alone
+    q->state = 3;
+    q->status = WV_ENOMEM;
+    q->err = "query needs more plan slots than the server has";
+    return true;
+  }
+  q->n = n;
+  q->bytes = need;
+  q->t_admit = S->now();
+  if (n == 0) {
+    q->state = 2;
+    q->t_done = q->t_admit;
+    return true;
+  }
+  auto fail = [&](wv_status s2) {
+    q->state = 3;
+    q->status = s2;
+    q->err = wv_last_error();
+    release_device(S, q);
+    return true;
+  };
+  if ((st = scratch_alloc((void **)&q->d_primes, n * 8, S->st)) != WV_OK) return fail(st);
+  if ((st = scratch_alloc((void **)&q->d_rb, n * 8, S->st)) != WV_OK) return fail(st);
+  if ((st = scratch_alloc((void **)&q->d_re, n * 8, S->st)) != WV_OK) return fail(st);
+  q->h_primes.resize(n);
+  if (q->kind == 0) {
+    uint64_t n2 = 0;
+    if ((st = sieve_device(q->lo, q->hi, q->d_primes, n, &n2, S->st)) != WV_OK) return fail(st);
+    if (cudaMemcpyAsync(q->h_primes.data(), q->d_primes, n * 8, cudaMemcpyDeviceToHost, S->st) !=
+        cudaSuccess)
+      return fail(cuda_fail(cudaGetLastError(), "serve: copy primes"));
+  } else {
+    q->h_primes[0] = q->lo;
+    if (cudaMemcpyAsync(q->d_primes, q->h_primes.data(), 8, cudaMemcpyHostToDevice, S->st) !=
+        cudaSuccess)
+      return fail(cuda_fail(cudaGetLastError(), "serve: copy prime"));
+  }
+  if (cudaStreamSynchronize(S->st) != cudaSuccess)
+    return fail(cuda_fail(cudaGetLastError(), "serve: admit"));
+  q->remaining = 0;
+  for (size_t i = 0; i < nplans; ++i) {
+    SChunk c;
+    c.off = (uint32_t)(i * kPlanPrimes);
+    c.n = (uint32_t)std::min<uint64_t>(kPlanPrimes, n - c.off);
+    c.slot = S->free_slots.back();
+    S->free_slots.pop_back();
+    q->chunks.push_back(c);
+    SChunk &cc = q->chunks.back();
+    if ((st = plan_build(q->d_primes + cc.off, cc.n, S->rcfg, &cc.plan, S->st)) != WV_OK)
+      return fail(st);
+    if ((st = plan_totals(&cc.plan, S->st)) != WV_OK) return fail(st);
+    Plan *dst = (Plan *)((char *)S->d_plans + (size_t)cc.slot * plan_struct_bytes());
+    if ((st = plan_upload(&cc.plan, dst, S->st)) != WV_OK) return fail(st);
+    cc.hi31 = cc.plan.split;
+    cc.hi64 = cc.plan.total;
+    double t31 = 0, t64 = 0;
+    terms_host(q->h_primes.data() + cc.off, cc.n, S->rcfg, &t31, &t64);
+    cc.tpt31 = cc.plan.split ? t31 / cc.plan.split : 1.0;
+    cc.tpt64 = (cc.plan.total > cc.plan.split) ? t64 / (cc.plan.total - cc.plan.split) : 1.0;
+    q->remaining += t31 + kWideWeight * t64;
+  }
+  q->state = 1;
+  return true;
+}
+
+void finish_query(wv_server_s *S, SQuery *q) {
+  q->h_rb.resize(q->n);
+  q->h_re.resize(q->n);
+  cudaError_t e = cudaMemcpyAsync(q->h_rb.data(), q->d_rb, q->n * 8, cudaMemcpyDeviceToHost, S->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(q->h_re.data(), q->d_re, q->n * 8, cudaMemcpyDeviceToHost, S->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(S->st);
+  release_device(S, q);
+  if (e != cudaSuccess) {
+    q->state = 3;
+    q->status = cuda_fail(e, "serve: results");
+    q->err = wv_last_error();
+  } else {
+    uint64_t h = 0;
+    for (size_t i = 0; i < q->n; ++i) h += (q->h_rb[i] == 0 || q->h_re[i] == 0) ? 1 : 0;
+    q->n_hits = h;
+    q->state = 2;
+  }
+  q->t_done = S->now();
+}
+
+void worker_main(wv_server_s *S) {
+  cudaSetDevice(S->device);
+  int64_t epoch_k = 0, completed = -1;
+  std::deque<int64_t> inflight;
+  for (;;) {
+    std::vector<SQuery *> cand;
+    size_t bytes_now;
+    bool none_active;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv_work.wait(lk, [&] { return S->stop || !S->pending.empty() || !S->active.empty(); });
+      if (S->stop) {
+        lk.unlock();
+        for (int b = 0; b < 2; ++b) cudaStreamSynchronize(S->se[b]);
+        return;
+      }
+      while (!S->pending.empty() && S->active.size() + cand.size() < S->cfg.max_active &&
+             cand.size() < kAdmitPerIter) {
+        cand.push_back(S->pending.front());
+        S->pending.pop_front();
+      }
+      bytes_now = S->bytes_in_use;
+      none_active = S->active.empty();
+    }
+    // ---- launch one epoch over the active queries, smallest remaining work first
+    std::vector<SQuery *> act;
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      act = S->active;
+    }
+    std::sort(act.begin(), act.end(),
+              [](const SQuery *a, const SQuery *b) { return a->remaining < b->remaining; });
+    // epoch size: short while a small query waits (its latency is at least one
+    // epoch), up to the configured size when only large work remains
+    double budget = S->cfg.epoch_terms;
+    if (!act.empty()) {
+      const double smallest = std::max(act.front()->remaining, 0.0);
+      budget = std::min(budget, std::max(kMinEpochTerms, 2.0 * smallest));
+    }
+    std::vector<EpochItem> items;
+    uint32_t tot = 0;
+    const int64_t k = epoch_k;
+    for (SQuery *q : act) {
+      for (SChunk &c : q->chunks) {
+        if (budget <= 0 || items.size() + 2 > 2 * kMaxPlans) break;
+        if (c.hi31 > 0) {
+          uint32_t kk = (uint32_t)std::min<double>(c.hi31, std::max(1.0, budget / c.tpt31));
+          items.push_back({c.slot, c.hi31 - kk, kk, tot});
+          tot += kk;
+          c.hi31 -= kk;
+          budget -= kk * c.tpt31;
+          q->remaining -= kk * c.tpt31;
+          c.last_epoch = k;
+        }
+        if (budget > 0 && c.hi64 > c.plan.split) {
+          const uint32_t avail = c.hi64 - c.plan.split;
+          uint32_t kk = (uint32_t)std::min<double>(avail, std::max(1.0, budget / (kWideWeight * c.tpt64)));
+          items.push_back({c.slot | 0x80000000u, c.hi64 - kk, kk, tot});
+          tot += kk;
+          c.hi64 -= kk;
+          budget -= kWideWeight * kk * c.tpt64;
+          q->remaining -= kWideWeight * kk * c.tpt64;
+          c.last_epoch = k;
+        }
+      }
+      if (budget <= 0) break;
+    }
+    wv_status st = WV_OK;
+    const bool launched = !items.empty();
+    if (launched) {
+      const int b = (int)(k & 1);
+      cudaStream_t es = S->se[b];
+      // this half of the item buffers was used by epoch k-2, which has completed
+      EpochItem *h = S->h_items + (size_t)b * 2 * kMaxPlans;
+      EpochItem *d = S->d_items + (size_t)b * 2 * kMaxPlans;
+      std::copy(items.begin(), items.end(), h);
+      cudaError_t e = cudaMemcpyAsync(d, h, items.size() * sizeof(EpochItem), cudaMemcpyHostToDevice, es);
+      if (e != cudaSuccess) st = cuda_fail(e, "serve: items");
+      if (st == WV_OK)
+        st = epoch_launch_mixed(d, (uint32_t)items.size(), tot, S->d_plans, S->d_counter + 2 * b,
+                                S->rcfg, S->sms, kReserveBlocks, es);
+      if (st == WV_OK && (e = cudaEventRecord(S->ev[b], es)) != cudaSuccess) st = cuda_fail(e, "serve: event");
+      inflight.push_back(k);
+      epoch_k++;
+      S->epochs++;
+      S->tiles += tot;
+    }
+    // ---- admission, in arrival order
+    std::vector<SQuery *> admitted, finished, deferred;
+    for (size_t i = 0; i < cand.size(); ++i) {
+      SQuery *q = cand[i];
+      const bool alone = none_active && admitted.empty();
+      if (!deferred.empty() || !admit(S, q, bytes_now, S->free_slots.size(), alone)) {
+        deferred.push_back(q);
+        continue;
+      }
+      if (q->state == 1) {
+        admitted.push_back(q);
+        bytes_now += q->bytes;
+      } else {
+        finished.push_back(q);
+      }
+    }
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      for (auto it = deferred.rbegin(); it != deferred.rend(); ++it) S->pending.push_front(*it);
+      for (SQuery *q : admitted) {
+        S->active.push_back(q);
+        S->bytes_in_use += q->bytes;
+      }
+      S->peak_active = std::max<uint32_t>(S->peak_active, (uint32_t)S->active.size());
+      if (!finished.empty()) S->cv_done.notify_all();
+    }
+    // ---- retire the oldest epoch once two are in flight (or when nothing new could start)
+    if (st == WV_OK && !inflight.empty() && (inflight.size() >= 2 || !launched)) {
+      const int64_t done_k = inflight.front();
+      inflight.pop_front();
+      cudaError_t e = cudaEventSynchronize(S->ev[done_k & 1]);
+      if (e != cudaSuccess) st = cuda_fail(e, "serve: epoch");
+      else completed = done_k;
+    }
+    // ---- finalise plans whose tiles have all run; finish complete queries
+    finished.clear();
+    for (SQuery *q : act) {
+      if (st != WV_OK) {
+        q->state = 3;
+        q->status = st;
+        q->err = wv_last_error();
+        for (int b = 0; b < 2; ++b) cudaStreamSynchronize(S->se[b]);
+        release_device(S, q);
+        q->t_done = S->now();
+        finished.push_back(q);
+        continue;
+      }
+      bool all = true;
+      for (SChunk &c : q->chunks) {
+        if (!c.finalized && c.hi31 == 0 && c.hi64 == c.plan.split && c.last_epoch <= completed) {
+          wv_status s2 = plan_finalize(&c.plan, q->d_rb + c.off, q->d_re + c.off, S->st);
+          if (s2 != WV_OK) st = s2;
+          c.finalized = true;
+        }
+        all = all && c.finalized;
+      }
+      if (all) {
+        finish_query(S, q);
+        finished.push_back(q);
+      }
+    }
+    if (!finished.empty()) {
+      std::lock_guard<std::mutex> lk(S->mu);
+      for (SQuery *q : finished) {
+        S->active.erase(std::remove(S->active.begin(), S->active.end(), q), S->active.end());
+        S->bytes_in_use -= std::min(S->bytes_in_use, q->bytes);
+      }
+      S->cv_done.notify_all();
+    }
+  }
+}
+
+void fill_info(const SQuery *q, wv_query_info *info) {
+  info->id = q->id;
+  info->kind = q->kind;
+  info->state = q->state;
+  info->status = q->status;
+  info->n_primes = q->n;
+  info->n_hits = q->n_hits;
+  info->t_submit = q->t_submit;
+  info->t_admit = q->t_admit;
+  info->t_done = q->t_done;
+}
+
+}  // namespace
+
+extern "C" {
+
+wv_status wv_server_create(const wv_server_config *cfg, wv_server *out) {
+  clear_error();
+  if (!out) return set_error(WV_EINVAL, "out is NULL");
+  *out = nullptr;
+  wv_server_s *S = new wv_server_s();
+  if (cfg) S->cfg = *cfg;
+  if (S->cfg.mem_budget == 0) S->cfg.mem_budget = (size_t)4 << 30;
+  if (S->cfg.max_active == 0) S->cfg.max_active = 256;
+  if (S->cfg.epoch_terms <= 0) S->cfg.epoch_terms = 4e10;
+  int dev = S->cfg.device;
+  if (dev < 0) {
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+      delete S;
+      return cuda_fail(e, "wv_server_create");
+    }
+  }
+  S->device = dev;
+  cudaError_t e = cudaSetDevice(dev);
+  DeviceState *ds = nullptr;
+  wv_status st = (e == cudaSuccess) ? device_state(&ds) : cuda_fail(e, "cudaSetDevice");
+  if (st == WV_OK) {
+    S->sms = ds->sms;
+    WV_CHECK(resolve_config(nullptr, true, true, &S->rcfg));
+    int lo_prio = 0, hi_prio = 0;
+    cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
+    // admission and finalisation go first whenever SMs free up
+    e = cudaStreamCreateWithPriority(&S->st, cudaStreamNonBlocking, hi_prio);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+      e = cudaStreamCreateWithFlags(&S->se[b], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev[b], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&S->d_plans, kMaxPlans * plan_struct_bytes());
+    if (e == cudaSuccess) e = cudaMalloc(&S->d_items, 4 * kMaxPlans * sizeof(EpochItem));
+    if (e == cudaSuccess) e = cudaMallocHost(&S->h_items, 4 * kMaxPlans * sizeof(EpochItem));
+    if (e == cudaSuccess) e = cudaMalloc(&S->d_counter, 4 * sizeof(uint32_t));
+    if (e != cudaSuccess) st = cuda_fail(e, "wv_server_create");
+  }
+  if (st != WV_OK) {
+    if (S->st) cudaStreamDestroy(S->st);
+    for (int b = 0; b < 2; ++b) {
+      if (S->se[b]) cudaStreamDestroy(S->se[b]);
+      if (S->ev[b]) cudaEventDestroy(S->ev[b]);
+    }
+    cudaFree(S->d_plans);
+    cudaFree(S->d_items);
+    cudaFreeHost(S->h_items);
+    cudaFree(S->d_counter);
+    delete S;
+    return st;
+  }
+  for (uint32_t i = 0; i < kMaxPlans; ++i) S->free_slots.push_back(kMaxPlans - 1 - i);
+  S->t0 = std::chrono::steady_clock::now();
+  S->worker = std::thread(worker_main, S);
+  *out = S;
+  return WV_OK;
+}
+
+static wv_status submit(wv_server s, int kind, uint64_t lo, uint64_t hi, uint64_t *id) {
+  clear_error();
+  if (!s || !id) return set_error(WV_EINVAL, "invalid server or id pointer");
+  SQuery *q = new SQuery();
+  q->kind = kind;
+  q->lo = lo;
+  q->hi = hi;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->stop) {
+    delete q;
+    return set_error(WV_ECANCELLED, "server is stopping");
+  }
+  q->id = s->next_id++;
+  q->t_submit = s->now();
+  s->queries[q->id] = q;
+  s->pending.push_back(q);
+  *id = q->id;
+  s->cv_work.notify_one();
+  return WV_OK;
+}
+
+wv_status wv_server_submit_range(wv_server s, uint64_t lo, uint64_t hi, uint64_t *id) {
+  if (hi > WV_P_MAX || lo > hi) {
+    clear_error();
+    return set_error(WV_EINVAL, "range [%llu, %llu) invalid", (unsigned long long)lo,
+                     (unsigned long long)hi);
+  }
+  return submit(s, 0, lo < 5 ? 5 : lo, hi < 5 ? 5 : hi, id);
+}
+
+wv_status wv_server_submit_prime(wv_server s, uint64_t p, uint64_t *id) {
+  if (p < 5 || p >= WV_P_MAX || !(p & 1)) {
+    clear_error();
+    return set_error(WV_EINVAL, "p=%llu outside 5 <= p < 2^37 or even", (unsigned long long)p);
+  }
+  return submit(s, 1, p, p + 1, id);
+}
+
+wv_status wv_server_wait(wv_server s, uint64_t id, double timeout_s, wv_query_info *info) {
+  clear_error();
+  if (!s) return set_error(WV_EINVAL, "invalid server");
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->queries.find(id);
+  if (it == s->queries.end()) return set_error(WV_EINVAL, "unknown query %llu", (unsigned long long)id);
+  SQuery *q = it->second;
+  auto done = [&] { return q->state >= 2; };
+  if (timeout_s < 0) {
+    s->cv_done.wait(lk, done);
+  } else if (!s->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), done)) {
+    if (info) fill_info(q, info);
+    return set_error(WV_ETIMEOUT, "query %llu not finished", (unsigned long long)id);
+  }
+  if (info) fill_info(q, info);
+  if (q->state == 3) return set_error(q->status, "%s", q->err.c_str());
+  if (q->state == 4) return set_error(WV_ECANCELLED, "query cancelled");
+  return WV_OK;
+}
+
+wv_status wv_server_query(wv_server s, uint64_t id, wv_query_info *info) {
+  clear_error();
+  if (!s || !info) return set_error(WV_EINVAL, "invalid arguments");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->queries.find(id);
+  if (it == s->queries.end()) return set_error(WV_EINVAL, "unknown query %llu", (unsigned long long)id);
+  fill_info(it->second, info);
+  return WV_OK;
+}
+
+wv_status wv_server_result(wv_server s, uint64_t id, uint64_t *h_primes, uint64_t *h_res_b,
+                           uint64_t *h_res_e, size_t cap, size_t *n) {
+  clear_error();
+  if (!s || !n) return set_error(WV_EINVAL, "invalid arguments");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->queries.find(id);
+  if (it == s->queries.end()) return set_error(WV_EINVAL, "unknown query %llu", (unsigned long long)id);
+  SQuery *q = it->second;
+  if (q->state != 2) return set_error(WV_EBUSY, "query %llu is not done", (unsigned long long)id);
+  *n = q->n;
+  const size_t m = std::min(cap, q->n);
+  if (h_primes) std::copy(q->h_primes.begin(), q->h_primes.begin() + m, h_primes);
+  if (h_res_b) std::copy(q->h_rb.begin(), q->h_rb.begin() + m, h_res_b);
+  if (h_res_e) std::copy(q->h_re.begin(), q->h_re.begin() + m, h_res_e);
+  if (cap < q->n) return set_error(WV_ERANGE, "%zu primes, capacity %zu", q->n, cap);
+  return WV_OK;
+}
+
+wv_status wv_server_release(wv_server s, uint64_t id) {
+  clear_error();
+  if (!s) return set_error(WV_EINVAL, "invalid server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->queries.find(id);
+  if (it == s->queries.end()) return WV_OK;
+  if (it->second->state < 2) return set_error(WV_EBUSY, "query %llu still running", (unsigned long long)id);
+  delete it->second;
+  s->queries.erase(it);
+  return WV_OK;
+}
+
+wv_status wv_server_stats(wv_server s, uint64_t *epochs, uint64_t *tiles, size_t *bytes_in_use,
+                          uint32_t *peak_active) {
+  clear_error();
+  if (!s) return set_error(WV_EINVAL, "invalid server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (epochs) *epochs = s->epochs;
+  if (tiles) *tiles = s->tiles;
+  if (bytes_in_use) *bytes_in_use = s->bytes_in_use;
+  if (peak_active) *peak_active = s->peak_active;
+  return WV_OK;
+}
+
+wv_status wv_server_destroy(wv_server s) {
+  clear_error();
+  if (!s) return WV_OK;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+    s->cv_work.notify_all();
+  }
+  if (s->worker.joinable()) s->worker.join();
+  cudaSetDevice(s->device);
+  for (int b = 0; b < 2; ++b) cudaStreamSynchronize(s->se[b]);
+  for (auto &kv : s->queries) {
+    SQuery *q = kv.second;
+    if (q->state < 2) {
+      release_device(s, q);
+      q->state = 4;
+    }
+  }
+  cudaStreamSynchronize(s->st);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->cv_done.notify_all();
+  }
+  for (auto &kv : s->queries) delete kv.second;
+  s->queries.clear();
+  cudaFree(s->d_plans);
+  cudaFree(s->d_items);
+  cudaFreeHost(s->h_items);
+  cudaFree(s->d_counter);
+  cudaStreamDestroy(s->st);
+  for (int b = 0; b < 2; ++b) {
+    cudaStreamDestroy(s->se[b]);
+    cudaEventDestroy(s->ev[b]);
+  }
+  delete s;
+  return WV_OK;
+}
+
+}  // extern "C"

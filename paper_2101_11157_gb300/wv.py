@@ -41,6 +41,18 @@ class wv_request(ctypes.Structure):
                 ("d_out_b", ctypes.c_void_p), ("d_out_e", ctypes.c_void_p)]
 
 
+class wv_server_config(ctypes.Structure):
+    _fields_ = [("mem_budget", ctypes.c_size_t), ("max_active", ctypes.c_uint32),
+                ("epoch_terms", ctypes.c_double), ("device", ctypes.c_int),
+                ("reserved", ctypes.c_int * 7)]
+
+
+class wv_query_info(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("kind", ctypes.c_int), ("state", ctypes.c_int),
+                ("status", ctypes.c_int), ("n_primes", ctypes.c_uint64), ("n_hits", ctypes.c_uint64),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
 class wv_options(ctypes.Structure):
     _fields_ = [("cong_b", ctypes.c_int), ("cong_e", ctypes.c_int), ("block", ctypes.c_int),
                 ("ilp", ctypes.c_int), ("tile_terms", ctypes.c_int), ("max_tiles", ctypes.c_int),
@@ -84,6 +96,15 @@ _SIGS = {
     "wv_batch_run": ([_vp, _vp], _i32),
     "wv_batch_info": ([_vp, _psz, _psz, _psz], _i32),
     "wv_batch_destroy": ([_vp], _i32),
+    "wv_server_create": ([ctypes.POINTER(wv_server_config), ctypes.POINTER(_vp)], _i32),
+    "wv_server_submit_range": ([_vp, _u64, _u64, _pu64], _i32),
+    "wv_server_submit_prime": ([_vp, _u64, _pu64], _i32),
+    "wv_server_wait": ([_vp, _u64, ctypes.c_double, ctypes.POINTER(wv_query_info)], _i32),
+    "wv_server_query": ([_vp, _u64, ctypes.POINTER(wv_query_info)], _i32),
+    "wv_server_result": ([_vp, _u64, _pu64, _pu64, _pu64, _sz, _psz], _i32),
+    "wv_server_release": ([_vp, _u64], _i32),
+    "wv_server_stats": ([_vp, _pu64, _pu64, _psz, ctypes.POINTER(ctypes.c_uint32)], _i32),
+    "wv_server_destroy": ([_vp], _i32),
 }
 
 
@@ -342,3 +363,72 @@ def wv_batch_destroy(batch: Batch) -> None:
     if batch.handle:
         _check(load().wv_batch_destroy(batch.handle))
         batch.handle = None
+
+
+
+# ------------------------------------------------------------------ serving
+def _info(i: wv_query_info) -> dict:
+    return {"id": i.id, "kind": ("range", "prime")[i.kind], "state": i.state, "status": i.status,
+            "n_primes": i.n_primes, "n_hits": i.n_hits, "t_submit": i.t_submit,
+            "t_admit": i.t_admit, "t_done": i.t_done}
+
+
+def wv_server_create(mem_budget: int = 0, max_active: int = 0, epoch_terms: float = 0.0,
+                     device: int = -1):
+    cfg = wv_server_config()
+    cfg.mem_budget, cfg.max_active, cfg.epoch_terms, cfg.device = mem_budget, max_active, epoch_terms, device
+    h = ctypes.c_void_p()
+    _check(load().wv_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def wv_server_submit_range(server, lo: int, hi: int) -> int:
+    i = ctypes.c_uint64()
+    _check(load().wv_server_submit_range(server, lo, hi, ctypes.byref(i)))
+    return i.value
+
+
+def wv_server_submit_prime(server, p: int) -> int:
+    i = ctypes.c_uint64()
+    _check(load().wv_server_submit_prime(server, p, ctypes.byref(i)))
+    return i.value
+
+
+def wv_server_wait(server, qid: int, timeout_s: float = -1.0) -> dict:
+    info = wv_query_info()
+    _check(load().wv_server_wait(server, qid, timeout_s, ctypes.byref(info)))
+    return _info(info)
+
+
+def wv_server_query(server, qid: int) -> dict:
+    info = wv_query_info()
+    _check(load().wv_server_query(server, qid, ctypes.byref(info)))
+    return _info(info)
+
+
+def wv_server_result(server, qid: int):
+    """(primes, B residues, E residues) of a finished query as numpy uint64 arrays."""
+    n = ctypes.c_size_t()
+    lib = load()
+    st = lib.wv_server_result(server, qid, None, None, None, 0, ctypes.byref(n))
+    if st not in (WV_OK, WV_ERANGE):
+        _check(st)
+    out = [np.zeros(max(n.value, 1), dtype=np.uint64) for _ in range(3)]
+    ptrs = [a.ctypes.data_as(_pu64) for a in out]
+    _check(lib.wv_server_result(server, qid, *ptrs, n.value, ctypes.byref(n)))
+    return tuple(a[:n.value] for a in out)
+
+
+def wv_server_release(server, qid: int) -> None:
+    _check(load().wv_server_release(server, qid))
+
+
+def wv_server_stats(server) -> dict:
+    e, t, b, pk = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_size_t(), ctypes.c_uint32()
+    _check(load().wv_server_stats(server, ctypes.byref(e), ctypes.byref(t), ctypes.byref(b),
+                                  ctypes.byref(pk)))
+    return {"epochs": e.value, "tiles": t.value, "bytes_in_use": b.value, "peak_active": pk.value}
+
+
+def wv_server_destroy(server) -> None:
+    _check(load().wv_server_destroy(server))

@@ -1,0 +1,98 @@
+"""The serving loop: queries submitted while others run share epochs on the
+device (continuous batching), and each result equals the same query computed
+alone, bit for bit."""
+import time
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2101_11157_gb300 import api, wv  # noqa: E402
+
+
+def _alone_range(lo, hi):
+    lo = max(lo, 5)
+    if hi <= lo:
+        return (np.zeros(0, np.uint64),) * 3
+    _, pr, rb, re = api.search(lo, hi, with_residues=True)
+    torch.cuda.synchronize()
+    return api.to_u64(pr), api.to_u64(rb), api.to_u64(re)
+
+
+def _alone_prime(p):
+    d = torch.tensor([p], dtype=torch.int64, device="cuda")
+    rb, re = api.residues(d)
+    torch.cuda.synchronize()
+    return np.array([p], np.uint64), api.to_u64(rb), api.to_u64(re)
+
+
+QUERIES = [("range", 2 * 10**9, 2 * 10**9 + 30000),   # long-running, 64-bit path
+           ("prime", 1062232319, None),                  # the Vandiver prime
+           ("range", 5, 3000),
+           ("prime", 16843, None),                       # the Wolstenholme prime
+           ("range", 10**7, 10**7 + 20000),
+           ("prime", 2**30 + 3, None),
+           ("range", 999_999_000, 1_000_001_000),
+           ("prime", 99_999_999_977, None),              # near the top of the search range
+           ("range", 10, 10)]                            # empty
+
+
+def _run(server, stagger):
+    ids = []
+    for i, (kind, a, b) in enumerate(QUERIES):
+        ids.append(wv.wv_server_submit_range(server, a, b) if kind == "range"
+                   else wv.wv_server_submit_prime(server, a))
+        if stagger and i == 0:
+            time.sleep(0.05)  # the first query is already on the device when the rest arrive
+    infos = [wv.wv_server_wait(server, q, 300.0) for q in ids]
+    return ids, infos
+
+
+def test_serving_results_equal_alone_and_overlap():
+    s = wv.wv_server_create(epoch_terms=2e9)
+    try:
+        ids, infos = _run(s, stagger=True)
+        for (kind, a, b), q, info in zip(QUERIES, ids, infos):
+            assert info["state"] == 2
+            pr, rb, re = wv.wv_server_result(s, q)
+            ref = _alone_range(a, b) if kind == "range" else _alone_prime(a)
+            assert np.array_equal(pr, ref[0]) and np.array_equal(rb, ref[1]) and np.array_equal(re, ref[2])
+            assert info["n_primes"] == pr.size
+        # the known zeros came back
+        assert wv.wv_server_result(s, ids[1])[2][0] == 0
+        assert wv.wv_server_result(s, ids[3])[1][0] == 0
+        st = wv.wv_server_stats(s)
+        assert st["peak_active"] >= 2 and st["epochs"] >= 2 and st["bytes_in_use"] == 0
+        # the small queries submitted behind the long one finished before it
+        assert infos[2]["t_done"] < infos[0]["t_done"]
+    finally:
+        wv.wv_server_destroy(s)
+
+
+def test_serving_under_a_tight_memory_budget():
+    s = wv.wv_server_create(mem_budget=8 << 20, max_active=3, epoch_terms=1e9)
+    try:
+        ids, infos = _run(s, stagger=False)
+        for (kind, a, b), q, info in zip(QUERIES, ids, infos):
+            pr, rb, re = wv.wv_server_result(s, q)
+            ref = _alone_range(a, b) if kind == "range" else _alone_prime(a)
+            assert np.array_equal(rb, ref[1]) and np.array_equal(re, ref[2])
+        assert wv.wv_server_stats(s)["bytes_in_use"] == 0
+    finally:
+        wv.wv_server_destroy(s)
+
+
+def test_serving_rejects_bad_queries():
+    s = wv.wv_server_create()
+    try:
+        with pytest.raises(wv.WvError):
+            wv.wv_server_submit_prime(s, 4)
+        with pytest.raises(wv.WvError):
+            wv.wv_server_submit_range(s, 10, 2**38)
+    finally:
+        wv.wv_server_destroy(s)
