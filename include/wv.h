@@ -141,12 +141,25 @@ wv_status wv_residues_pm3_noalloc(const uint64_t *d_primes, size_t n, uint64_t *
 typedef struct {
   int cong_b;       /* congruence id (wv_congruence_info) for B; <0: default BB30 */
   int cong_e;       /* congruence id for E; <0: default EE33 */
-  int block;        /* accumulation block size (threads), multiple of 32 */
-  int ilp;          /* independent accumulator chains per thread: 1, 2 or 4 */
-  int tile_terms;   /* target terms per warp tile */
-  int max_tiles;    /* maximum tiles per (prime, sum) */
+  int block;        /* accumulation block size (threads): 32..256, multiple of 32;
+                       default 256.  Smaller blocks release their registers warp by
+                       warp at the end of a launch and round occupancy differently */
+  int ilp;          /* independent accumulator chains per thread for p < 2^30: 1, 2 or 4
+                       (4 only with arith >= 9; default 2).  The grouped 64-bit forms
+                       (arith >= 9) run one chain per thread; the single-term 64-bit
+                       form takes this value too */
+  int tile_terms;   /* target terms per warp tile (default 2^20) */
+  int max_tiles;    /* maximum tiles per (prime, sum) (default 8).  With neither set, a
+                       call with few primes gets more and shorter tiles (up to 64 per
+                       sum) so that one launch still holds ~1e5 tiles */
   int blocks_per_sm;/* persistent grid = SMs x this */
-  int arith;        /* hot-loop formulation for p < 2^30: 1 = shared t p^-1, 2 = wide product */
+  int arith;        /* hot-loop formulation, 1..17 (default 9: grouped terms, REDC folded
+                       into wide multiply-adds, on both paths).  1..8 select the single-
+                       term and intermediate forms of the 32-bit path for ablation, and
+                       any value below 9 the single-term 64-bit path; 10..17 select other
+                       grouped 64-bit forms (group sizes, shrink interval, instruction
+                       choices; one chain per thread) for ablation, with formulation 9
+                       on the 32-bit path */
   int reserved[8];
 } wv_options;
 

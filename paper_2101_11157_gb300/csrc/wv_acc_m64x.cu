@@ -1,0 +1,22 @@
+// wv_acc_m64x.cu -- the 64-bit-path formulations kept for ablation
+// (wv_options.arith 10..17: other group sizes, shrink intervals and the two
+// flags of M64Form), one chain per thread.  The code is in wv_accum.cuh.
+#include "wv_accum.cuh"
+
+namespace wv {
+
+AccKernel acc_kernel_m64x(int arith, int) {
+  constexpr int I = 1;
+  switch (arith) {
+    case 10: return k_accumulate<true, I, 10>;
+    case 11: return k_accumulate<true, I, 11>;
+    case 12: return k_accumulate<true, I, 12>;
+    case 13: return k_accumulate<true, I, 13>;
+    case 14: return k_accumulate<true, I, 14>;
+    case 15: return k_accumulate<true, I, 15>;
+    case 16: return k_accumulate<true, I, 16>;
+    default: return k_accumulate<true, I, 17>;
+  }
+}
+
+}  // namespace wv

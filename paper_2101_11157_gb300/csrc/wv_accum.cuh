@@ -1,0 +1,790 @@
+// wv_accum.cuh -- steps a3-a5 on the device: term generation, accumulation
+// of eqn 3.12 / eqn 3.14 per warp tile, and the lane/warp merge; the plan
+// layout the planner fills; and the accumulation kernels as templates.
+//
+// The kernels are instantiated in four translation units that compile in
+// parallel: wv_residue.cu (32-bit path), wv_acc_m64.cu (64-bit path),
+// wv_acc_epoch.cu (the serving loop's epoch kernels) and wv_acc_m64x.cu
+// (64-bit formulations kept for ablation).  The host side reaches them
+// through the getters at the end.
+#pragma once
+
+#include "wv_arith.cuh"
+#include "wv_internal.h"
+#include "wv_tables.h"
+
+namespace wv {
+
+constexpr int kAccThreads = 256;
+constexpr int kMaxRowsPP = 66;  // B rows + E rows for one prime (30 + 33 for BB30 + EE33)
+constexpr uint32_t kChunkPrimes = 16384;  // primes per internal launch sequence
+constexpr uint64_t kGroupMinChain = 48;   // grouped path only for chains of >= 48 terms
+
+struct Plan {
+  uint32_t n;                   // primes in this chunk
+  uint32_t rows_b, rows_e, rows_pp;
+  uint32_t tile_terms, max_tiles;
+  const uint64_t *primes;       // caller's primes (chunk base)
+  uint64_t *out_b, *out_e;      // caller's outputs (chunk base), may be null
+  PrimeCtx *ctx;                // per slot (M31 slots first, then M64)
+  uint32_t *flag, *pos, *n31;   // flag: p-bucket per prime; n31: slots with p < 2^30
+  uint32_t *bk;                 // 3 x 64 words: bucket counts, offsets, cursors
+  uint64_t *seg_lo, *seg_cnt;   // per segment (slot * rows_pp + row)
+  uint32_t *seg_tiles, *seg_first;
+  uint32_t *total_tiles, *split_tile;
+  uint32_t *counters;           // [0] M31 accumulation, [1] M64 accumulation
+  ulonglong2 *partials;         // per tile (c0, c1), canonical
+  // congruence rows: rows [0, rows_b) are B rows, [rows_b, rows_pp) E rows
+  uint32_t xn[kMaxRowsPP], xd[kMaxRowsPP], yn[kMaxRowsPP], yd[kMaxRowsPP];
+  int64_t coef[kMaxRowsPP];
+  int64_t lhs_b, lhs_e;
+};
+
+// ------------------------------------------------------------------ tiles
+// Warp-level merge of the per-lane pairs (eqn 3.14) through shuffles.
+__device__ __forceinline__ void warp_merge(const Mont &M, int64_t &a0, int64_t &a1) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    int64_t b0 = __shfl_xor_sync(0xffffffffu, a0, o);
+    int64_t b1 = __shfl_xor_sync(0xffffffffu, a1, o);
+    M.combine(a0, a1, b0, b1);
+  }
+}
+
+// p < 2^30: signed 32-bit Montgomery, R = 2^32.  AR selects the product
+// formulation: 1 = hi(c t) and lo(c tq) with tq = t p^-1 shared by c0 and c1;
+// 2 = the full 64-bit product c t (one wide multiply) and m = lo(c t) p^-1.
+template <int ILP, bool CUBES, int AR>
+__device__ __forceinline__ void tile_m31(const PrimeCtx &ctx, uint64_t start, uint64_t n,
+                                         int64_t &r0, int64_t &r1) {
+  const int lane = threadIdx.x & 31;
+  const int32_t p = (int32_t)ctx.p;
+  const uint32_t up = (uint32_t)ctx.p;
+  const uint32_t q = (uint32_t)ctx.q;
+  const uint64_t nch = 32 * ILP;
+  const uint64_t len = n / nch;
+  const uint32_t rem = (uint32_t)(n - len * nch);
+  int32_t c0[ILP], c1[ILP], t[ILP], d1[ILP], d2[ILP];
+#pragma unroll
+  for (int k = 0; k < ILP; ++k) {
+    const uint32_t ch = k * 32 + lane;
+    const uint64_t s = start + ch * len + (ch < rem ? ch : rem);
+    const uint64_t s2 = (s * s) % ctx.p;  // s < 2^30: exact in 64 bits
+    if (CUBES) {
+      t[k] = (int32_t)((s2 * s) % ctx.p);              // s^3
+      d1[k] = (int32_t)((3 * s2 + 3 * s + 1) % ctx.p); // (s+1)^3 - s^3
+      d2[k] = (int32_t)((6 * s + 6) % ctx.p);          // second difference
+    } else {
+      t[k] = (int32_t)s2;                              // s^2
+      d1[k] = (int32_t)(2 * s + 1);                    // (s+1)^2 - s^2 <= p (s < p/2)
+      d2[k] = 0;
+    }
+    c0[k] = (int32_t)ctx.one;
+    c1[k] = 0;
+  }
+  // z: a runtime zero (the context's upper flag bits are never set) that the
+  // compiler cannot fold.  Written into otherwise two-input additions it makes
+  // them genuine three-input adds, which only the integer ALU executes, so
+  // they stay off the multiply pipe the products saturate (AR >= 3).
+  const int32_t z = (int32_t)(ctx.flags >> 16);
+  const int32_t np = -p;
+  auto step = [&](int k, int32_t zi) {
+    // eqn 3.12 with REDC against the plain term t
+    if (AR == 1) {
+      const uint32_t tq = (uint32_t)t[k] * q;
+      const int32_t m0 = (int32_t)((uint32_t)c0[k] * tq);
+      const int32_t m1 = (int32_t)((uint32_t)c1[k] * tq);
+      const int32_t h0 = __mulhi(c0[k], t[k]);
+      const int32_t h1 = __mulhi(c1[k], t[k]);
+      const int32_t n1 = h1 - __mulhi(m1, p) + c0[k];
+      c0[k] = h0 - __mulhi(m0, p);
+      c1[k] = n1;
+    } else if (AR >= 6) {
+      // REDC folded into a wide multiply-add: d = w - m p is an exact
+      // multiple of 2^32 whose high word is the reduced value, and c0 rides
+      // in the high word of c1's product, so no separate add is needed.
+      const int64_t w0 = mul_wide(c0[k], t[k]);
+      const int64_t w1 = mad_wide(c1[k], t[k], hi_word(c0[k]));
+      const int32_t m0 = (int32_t)((uint32_t)lo32(w0) * q);
+      const int32_t m1 = (int32_t)((uint32_t)lo32(w1) * q);
+      c0[k] = hi32(mad_wide(m0, np, w0));
+      c1[k] = hi32(mad_wide(m1, np, w1));
+    } else {
+      const int64_t w0 = (int64_t)c0[k] * (int64_t)t[k];
+      const int64_t w1 = (int64_t)c1[k] * (int64_t)t[k];
+      const int32_t m0 = (int32_t)((uint32_t)w0 * q);
+      const int32_t m1 = (int32_t)((uint32_t)w1 * q);
+      const int32_t n1 = (int32_t)(w1 >> 32) - __mulhi(m1, p) + c0[k];
+      if (AR >= 3) c0[k] = (int32_t)(w0 >> 32) - __mulhi(m0, p) + zi;
+      else c0[k] = (int32_t)(w0 >> 32) - __mulhi(m0, p);
+      c1[k] = n1;
+    }
+    // forward differences, each a modular add as min(x, x - p) on unsigned words
+    const uint32_t uz = (uint32_t)(AR >= 3 && AR < 6 ? z : 0);
+    const uint32_t uzi = (uint32_t)(AR >= 4 && AR < 6 ? zi : 0);
+    uint32_t x = (uint32_t)t[k] + (uint32_t)d1[k] + uz;
+    uint32_t y = (uint32_t)t[k] + (uint32_t)d1[k] - up;
+    t[k] = (int32_t)min(x, y);
+    if (CUBES) {
+      x = (uint32_t)d1[k] + (uint32_t)d2[k] + uz;
+      y = (uint32_t)d1[k] + (uint32_t)d2[k] - up;
+      d1[k] = (int32_t)min(x, y);
+      x = (uint32_t)d2[k] + 6u + uzi;
+      y = (uint32_t)d2[k] + (6u - up) + uzi;
+      d2[k] = (int32_t)min(x, y);
+    } else {
+      d1[k] = (int32_t)((uint32_t)d1[k] + 2u + uzi);
+    }
+  };
+#pragma unroll 2
+  for (uint64_t it = 0; it < len; ++it) {
+    // a per-iteration zero (chains never reach 2^63 terms)
+    const int32_t zi = (AR >= 4 && AR < 6) ? (int32_t)(it >> 63) : z;
+#pragma unroll
+    for (int k = 0; k < ILP; ++k) step(k, zi);
+  }
+#pragma unroll
+  for (int k = 0; k < ILP; ++k)
+    if ((uint32_t)(k * 32 + lane) < rem) step(k, z);
+
+  const Mont M(ctx);
+  int64_t a0 = m31_canon(c0[0], p), a1 = m31_canon(c1[0], p);
+#pragma unroll
+  for (int k = 1; k < ILP; ++k) M.combine(a0, a1, m31_canon(c0[k], p), m31_canon(c1[k], p));
+  warp_merge(M, a0, a1);
+  r0 = a0;
+  r1 = a1;
+}
+
+// ---- grouped accumulation (p < 2^30) ------------------------------------
+// eqn 3.14 applied to a GROUP of K consecutive terms: the group's factor
+// prod_{i<K} (z + (s+i)^e) = G0(s) + G1(s) z + O(z^2) with
+//   G0(s) = prod_i (s+i)^e,   G1(s) = sum_i prod_{j!=i} (s+j)^e,
+// polynomials in s of degree K e and (K-1) e.  Both are stepped s -> s+K by
+// forward differences (additions only), and each group costs three products:
+//   c0 <- c0 G0,   c1 <- c1 G0 + c0 G1.
+// G1 is kept in Montgomery form so that, as in the single-term step, the
+// ratio c1/c0 accumulates R * sum t^-1 (see the bookkeeping note above).
+
+// G0(x) (plain) and G1(x) R (Montgomery) for the group x, x+1, ..., x+K-1.
+template <int K, int EX>
+__device__ __forceinline__ void group_poly(const Mont &M, uint64_t x, int64_t &g0, int64_t &g1m) {
+  int64_t tm[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    uint64_t v = x + i;
+    if (v >= (uint64_t)M.p) v -= (uint64_t)M.p;
+    const int64_t b = M.to_mont((int64_t)v);
+    int64_t t = M.mul(b, b);
+    if (EX == 3) t = M.mul(t, b);
+    tm[i] = t;  // (x+i)^e in Montgomery form
+  }
+  int64_t all = M.one, g1 = 0;
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    int64_t others = M.one;
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+      if (j != i) others = M.mul(others, tm[j]);
+    g1 = M.add(g1, others);
+    all = M.mul(all, tm[i]);
+  }
+  g0 = M.from_mont(all);
+  g1m = g1;
+}
+
+template <int ILP, bool CUBES, int AR>
+__device__ __forceinline__ void tile_m31_grouped(const PrimeCtx &ctx, uint64_t start, uint64_t n,
+                                                 int64_t &r0, int64_t &r1) {
+  constexpr int K = CUBES ? 2 : 3;     // terms per group
+  constexpr int EX = CUBES ? 3 : 2;    // t = s^EX
+  constexpr int DA = K * EX;           // degree of G0
+  constexpr int DB = (K - 1) * EX;     // degree of G1
+  const int lane = threadIdx.x & 31;
+  const Mont M(ctx);
+  const int32_t p = (int32_t)ctx.p;
+  const uint32_t up = (uint32_t)ctx.p;
+  const uint32_t q = (uint32_t)ctx.q;
+  const uint32_t uz = (AR >= 7) ? 0u : (ctx.flags >> 16);  // runtime zero (AR 5: three-input adds)
+  const int32_t np = -p;
+  const uint64_t nch = 32 * ILP;
+  const uint64_t len = n / nch;
+  const uint32_t rem = (uint32_t)(n - len * nch);
+  const uint64_t G = len / K;  // groups per chain, the same for every lane
+  int32_t c0[ILP], c1[ILP], ga[ILP][DA + 1], gb[ILP][DB + 1];
+  uint64_t s_tail[ILP];
+  uint32_t n_tail[ILP];
+#pragma unroll
+  for (int k = 0; k < ILP; ++k) {
+    const uint32_t ch = k * 32 + lane;
+    const uint64_t s = start + ch * len + (ch < rem ? ch : rem);
+    const uint64_t L = len + (ch < rem ? 1 : 0);
+    s_tail[k] = s + G * K;
+    n_tail[k] = (uint32_t)(L - G * K);
+    // difference tables of G0 and G1 at s, s+K, s+2K, ...
+    int64_t va[DA + 1], vb[DB + 1];
+#pragma unroll
+    for (int i = 0; i <= DA; ++i) {
+      int64_t a, b;
+      group_poly<K, EX>(M, s + (uint64_t)i * K, a, b);
+      va[i] = a;
+      if (i <= DB) vb[i] = b;
+    }
+#pragma unroll
+    for (int j = 1; j <= DA; ++j)
+#pragma unroll
+      for (int i = DA; i >= j; --i) va[i] = M.sub(va[i], va[i - 1]);
+#pragma unroll
+    for (int j = 1; j <= DB; ++j)
+#pragma unroll
+      for (int i = DB; i >= j; --i) vb[i] = M.sub(vb[i], vb[i - 1]);
+#pragma unroll
+    for (int i = 0; i <= DA; ++i) ga[k][i] = (int32_t)va[i];
+#pragma unroll
+    for (int i = 0; i <= DB; ++i) gb[k][i] = (int32_t)vb[i];
+    c0[k] = (int32_t)ctx.one;
+    c1[k] = 0;
+  }
+  auto modadd = [&](int32_t &a, int32_t b) {
+    const uint32_t x = (uint32_t)a + (uint32_t)b + uz;
+    const uint32_t y = (uint32_t)a + (uint32_t)b - up;
+    a = (int32_t)min(x, y);
+  };
+#pragma unroll 1
+  for (uint64_t g = 0; g < G; ++g) {
+#pragma unroll
+    for (int k = 0; k < ILP; ++k) {
+      const int32_t A = ga[k][0], B = gb[k][0];
+      if (AR >= 7) {
+        // one REDC for c1 G0 + c0 G1 R, folded into wide multiply-adds
+        const int64_t w0 = mul_wide(c0[k], A);
+        const int64_t w1 = mad_wide(c0[k], B, mul_wide(c1[k], A));
+        const int32_t m0 = (int32_t)((uint32_t)lo32(w0) * q);
+        const int32_t m1 = (int32_t)((uint32_t)lo32(w1) * q);
+        c0[k] = hi32(mad_wide(m0, np, w0));
+        c1[k] = hi32(mad_wide(m1, np, w1));
+      } else {
+        const int64_t w0 = (int64_t)c0[k] * (int64_t)A;
+        const int64_t w1 = (int64_t)c1[k] * (int64_t)A;
+        const int64_t w2 = (int64_t)c0[k] * (int64_t)B;
+        const int32_t m0 = (int32_t)((uint32_t)w0 * q);
+        const int32_t m1 = (int32_t)((uint32_t)w1 * q);
+        const int32_t m2 = (int32_t)((uint32_t)w2 * q);
+        const int32_t n1 = ((int32_t)(w1 >> 32) - __mulhi(m1, p)) + ((int32_t)(w2 >> 32) - __mulhi(m2, p));
+        c0[k] = (int32_t)(w0 >> 32) - __mulhi(m0, p) + (int32_t)uz;
+        c1[k] = n1;
+      }
+      // step both difference tables by one group (low order first)
+#pragma unroll
+      for (int j = 0; j < DA; ++j) modadd(ga[k][j], ga[k][j + 1]);
+#pragma unroll
+      for (int j = 0; j < DB; ++j) modadd(gb[k][j], gb[k][j + 1]);
+    }
+  }
+  // the last (at most K) terms of each chain one at a time (eqn 3.12)
+#pragma unroll
+  for (int k = 0; k < ILP; ++k) {
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      if ((uint32_t)i < n_tail[k]) {
+        const int64_t b = M.to_mont((int64_t)(s_tail[k] + i));
+        int64_t tm = M.mul(b, b);
+        if (EX == 3) tm = M.mul(tm, b);
+        const int32_t t = (int32_t)M.from_mont(tm);
+        const int64_t w0 = (int64_t)c0[k] * (int64_t)t;
+        const int64_t w1 = (int64_t)c1[k] * (int64_t)t;
+        const int32_t m0 = (int32_t)((uint32_t)w0 * q);
+        const int32_t m1 = (int32_t)((uint32_t)w1 * q);
+        const int32_t n1 = (int32_t)(w1 >> 32) - __mulhi(m1, p) + c0[k];
+        c0[k] = (int32_t)(w0 >> 32) - __mulhi(m0, p);
+        c1[k] = n1;
+      }
+    }
+  }
+  int64_t a0 = m31_canon(c0[0], p), a1 = m31_canon(c1[0], p);
+#pragma unroll
+  for (int k = 1; k < ILP; ++k) M.combine(a0, a1, m31_canon(c0[k], p), m31_canon(c1[k], p));
+  warp_merge(M, a0, a1);
+  r0 = a0;
+  r1 = a1;
+}
+
+// 2^30 <= p < 2^37: signed 64-bit Montgomery, R = 2^64.
+template <int ILP, bool CUBES>
+__device__ __forceinline__ void tile_m64(const PrimeCtx &ctx, uint64_t start, uint64_t n,
+                                         int64_t &r0, int64_t &r1) {
+  const int lane = threadIdx.x & 31;
+  const Mont M(ctx);
+  const int64_t p = (int64_t)ctx.p;
+  const uint64_t up = ctx.p;
+  const uint64_t q = ctx.q;
+  const uint64_t nch = 32 * ILP;
+  const uint64_t len = n / nch;
+  const uint32_t rem = (uint32_t)(n - len * nch);
+  int64_t c0[ILP], c1[ILP], t[ILP], d1[ILP], d2[ILP];
+#pragma unroll
+  for (int k = 0; k < ILP; ++k) {
+    const uint32_t ch = k * 32 + lane;
+    const uint64_t s = start + ch * len + (ch < rem ? ch : rem);
+    const int64_t s2 = M.mulmod((int64_t)s, (int64_t)s);
+    if (CUBES) {
+      t[k] = M.mulmod(s2, (int64_t)s);
+      d1[k] = (int64_t)((3 * (uint64_t)s2 + 3 * s + 1) % up);
+      d2[k] = (int64_t)((6 * s + 6) % up);
+    } else {
+      t[k] = s2;
+      d1[k] = (int64_t)(2 * s + 1);
+      d2[k] = 0;
+    }
+    c0[k] = (int64_t)ctx.one;
+    c1[k] = 0;
+  }
+  auto step = [&](int k) {
+    const uint64_t tq = (uint64_t)t[k] * q;
+    const int64_t m0 = (int64_t)((uint64_t)c0[k] * tq);
+    const int64_t m1 = (int64_t)((uint64_t)c1[k] * tq);
+    const int64_t h0 = __mul64hi(c0[k], t[k]);
+    const int64_t h1 = __mul64hi(c1[k], t[k]);
+    const int64_t n1 = h1 - __mul64hi(m1, p) + c0[k];
+    c0[k] = h0 - __mul64hi(m0, p);
+    c1[k] = n1;
+    uint64_t x = (uint64_t)t[k] + (uint64_t)d1[k];
+    t[k] = (int64_t)min(x, x - up);
+    if (CUBES) {
+      x = (uint64_t)d1[k] + (uint64_t)d2[k];
+      d1[k] = (int64_t)min(x, x - up);
+      x = (uint64_t)d2[k] + 6u;
+      d2[k] = (int64_t)min(x, x - up);
+    } else {
+      d1[k] += 2;
+    }
+  };
+#pragma unroll 1
+  for (uint64_t it = 0; it < len; ++it) {
+#pragma unroll
+    for (int k = 0; k < ILP; ++k) step(k);
+  }
+#pragma unroll
+  for (int k = 0; k < ILP; ++k)
+    if ((uint32_t)(k * 32 + lane) < rem) step(k);
+
+  int64_t a0 = m64_canon(c0[0], p), a1 = m64_canon(c1[0], p);
+#pragma unroll
+  for (int k = 1; k < ILP; ++k) M.combine(a0, a1, m64_canon(c0[k], p), m64_canon(c1[k], p));
+  warp_merge(M, a0, a1);
+  r0 = a0;
+  r1 = a1;
+}
+
+// ---- grouped accumulation for 2^30 <= p < 2^37 ------------------------------
+// Montgomery with R = 2^64 done as two 32-bit rounds on unsigned words:
+// p = p0 + p1 2^32 (p1 < 32), q = -p^-1 mod 2^32.  A product T = c g is held
+// as a low word T0 and a 64-bit rest TY (T = T0 + TY 2^32); each round adds
+// m p with m = (low word) q, which clears the low word exactly.  For
+// c < p + 2^31 and g < 2^57 every intermediate fits its word and the result
+// is below p + 2^31 (one conditional subtraction makes it canonical).
+//
+// The grouped scheme of the 32-bit path is used with larger groups here: the
+// group polynomials G0, G1 are stepped with plain 64-bit additions and no
+// reduction, and every BLK groups the tables are brought back below 10 p by
+// an approximate Barrett step (quotient from the high word times
+// floor(2^62 / p)).  Starting below 10 p, entry j of a degree-D table grows
+// over B steps to at most 10 p sum_{i <= D-j} C(B, i) <= 10 p 2^B, so with
+// BLK = 16 every entry stays below 10 p 2^16 < 2^57 (p < 2^37), whatever D.
+//
+// The scheme is parametrised by the group sizes (KB terms per group for the
+// cubes of the Bernoulli sums, KE for the squares of the Euler sums), the
+// shrink interval BLK and two ablation flags:
+//   1  difference-table additions written as three-input adds with a runtime
+//      zero, which keeps them on the integer ALU (off the multiply pipe);
+//   2  REDC rounds without zero-extended addends: the carry out of the
+//      cleared low word is (low word != 0), added to a high product.
+// A group costs the same 41 multiply-pipe slots whatever K, so larger groups
+// cut the products per term; the tables cost 2 (D_A + D_B) additions per
+// group and registers, which bound K.
+
+struct M64K {
+  uint32_t p0, p1, q, mhi;  // mhi = floor(2^62 / p)
+  uint64_t p;
+};
+
+__device__ __forceinline__ uint64_t umul_wide(uint32_t a, uint32_t b) {
+  uint64_t d;
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(d) : "r"(a), "r"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t umad_wide(uint32_t a, uint32_t b, uint64_t c) {
+  uint64_t d;
+  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ uint32_t ulo(uint64_t v) {
+  uint32_t lo;
+  asm("{\n\t.reg .b32 t;\n\tmov.b64 {%0, t}, %1;\n\t}" : "=r"(lo) : "l"(v));
+  return lo;
+}
+__device__ __forceinline__ uint32_t uhi(uint64_t v) {
+  uint32_t hi;
+  asm("{\n\t.reg .b32 t;\n\tmov.b64 {t, %0}, %1;\n\t}" : "=r"(hi) : "l"(v));
+  return hi;
+}
+__device__ __forceinline__ uint64_t upack(uint32_t lo, uint32_t hi) {
+  uint64_t v;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(v) : "r"(lo), "r"(hi));
+  return v;
+}
+
+// (T0 + TY 2^32) 2^-64 mod p for T < 2^96, result below p + 2^32
+__device__ __forceinline__ uint64_t m64_redc2(uint32_t T0, uint64_t TY, const M64K &K) {
+  const uint32_t m0 = T0 * K.q;
+  const uint64_t A = umad_wide(m0, K.p0, (uint64_t)T0);       // low word is 0
+  const uint64_t U = umad_wide(m0, K.p1, TY) + uhi(A);        // (T + m0 p) / 2^32
+  const uint32_t m1 = ulo(U) * K.q;
+  const uint64_t B = umad_wide(m1, K.p0, (uint64_t)ulo(U));   // low word is 0
+  return umad_wide(m1, K.p1, (uint64_t)uhi(U)) + uhi(B);      // (U + m1 p) / 2^32
+}
+// the same without zero-extended addends: T0 + lo(m0 p0) is 0 or 2^32, so its
+// carry is (T0 != 0) and only hi(m0 p0) enters the next word
+__device__ __forceinline__ uint64_t m64_redc2_nz(uint32_t T0, uint64_t TY, const M64K &K) {
+  const uint32_t m0 = T0 * K.q;
+  const uint64_t U = umad_wide(m0, K.p1, TY) + (uint64_t)(__umulhi(m0, K.p0) + (T0 != 0u));
+  const uint32_t u0 = ulo(U), u1 = uhi(U);
+  const uint32_t m1 = u0 * K.q;
+  return umul_wide(m1, K.p1) + (uint64_t)u1 + (uint64_t)(__umulhi(m1, K.p0) + (u0 != 0u));
+}
+// T = c g as (T0, TY); c < p + 2^31, g < 2^57
+__device__ __forceinline__ void m64_prod(uint64_t c, uint64_t g, uint32_t &T0, uint64_t &TY) {
+  const uint32_t c0 = ulo(c), c1 = uhi(c), g0 = ulo(g), g1 = uhi(g);
+  const uint64_t X = umul_wide(c0, g0);
+  T0 = ulo(X);
+  uint64_t Y = umad_wide(c0, g1, (uint64_t)uhi(X));
+  Y = umad_wide(c1, g0, Y);
+  TY = upack(ulo(Y), uhi(Y) + c1 * g1);
+}
+// T = ca ga + cb gb as (T0, TY)
+__device__ __forceinline__ void m64_prod2(uint64_t ca, uint64_t ga, uint64_t cb, uint64_t gb,
+                                          uint32_t &T0, uint64_t &TY) {
+  const uint32_t a0 = ulo(ca), a1 = uhi(ca), x0 = ulo(ga), x1 = uhi(ga);
+  const uint32_t b0 = ulo(cb), b1 = uhi(cb), y0 = ulo(gb), y1 = uhi(gb);
+  const uint64_t Xa = umul_wide(a0, x0);
+  const uint64_t Xb = umad_wide(b0, y0, (uint64_t)ulo(Xa));
+  T0 = ulo(Xb);
+  uint64_t Y = umad_wide(a0, x1, (uint64_t)uhi(Xa));
+  Y = umad_wide(a1, x0, Y);
+  Y = umad_wide(b0, y1, Y);
+  Y = umad_wide(b1, y0, Y) + uhi(Xb);
+  TY = upack(ulo(Y), uhi(Y) + a1 * x1 + b1 * y1);
+}
+// v < 2^64  ->  v' = v (mod p) with v' < 10 p
+__device__ __forceinline__ uint64_t m64_shrink(uint64_t v, const M64K &K) {
+  const uint64_t qq = umul_wide(uhi(v), K.mhi) >> 30;  // <= floor(v / p), short by < 10
+  const uint32_t q0 = ulo(qq), q1 = uhi(qq);
+  const uint64_t qp = umul_wide(q0, K.p0) + ((uint64_t)(q0 * K.p1 + q1 * K.p0) << 32);
+  return v - qp;
+}
+
+// group sizes, shrink interval and flags of each 64-bit formulation (arith)
+template <int AR> struct M64Form {  // 9: the default
+  static constexpr int KB = 8, KE = 10, BLK = 16, V = 0;
+};
+template <> struct M64Form<10> { static constexpr int KB = 2, KE = 3, BLK = 8, V = 1; };
+template <> struct M64Form<11> { static constexpr int KB = 2, KE = 3, BLK = 8, V = 2; };
+template <> struct M64Form<12> { static constexpr int KB = 2, KE = 3, BLK = 8, V = 0; };
+template <> struct M64Form<13> { static constexpr int KB = 3, KE = 4, BLK = 16, V = 0; };
+template <> struct M64Form<14> { static constexpr int KB = 4, KE = 5, BLK = 16, V = 0; };
+template <> struct M64Form<15> { static constexpr int KB = 5, KE = 6, BLK = 16, V = 0; };
+template <> struct M64Form<16> { static constexpr int KB = 6, KE = 8, BLK = 16, V = 0; };
+template <> struct M64Form<17> { static constexpr int KB = 7, KE = 9, BLK = 16, V = 0; };
+
+// a b 2^-64 mod p, below p + 2^12 for a, b < 2^38
+__device__ __forceinline__ uint64_t m64_mm(uint64_t a, uint64_t b, const M64K &K) {
+  uint32_t T0;
+  uint64_t TY;
+  m64_prod(a, b, T0, TY);
+  return m64_redc2(T0, TY, K);
+}
+// v < 2p -> [0, p); canonical modular add and subtract
+__device__ __forceinline__ uint64_t m64_once(uint64_t v, uint64_t p) { return v >= p ? v - p : v; }
+__device__ __forceinline__ uint64_t m64_addm(uint64_t a, uint64_t b, uint64_t p) {
+  return m64_once(a + b, p);
+}
+__device__ __forceinline__ uint64_t m64_subm(uint64_t a, uint64_t b, uint64_t p) {
+  return a >= b ? a - b : a + p - b;
+}
+
+template <int ILP, bool CUBES, int AR>
+__device__ __forceinline__ void tile_m64_grouped(const PrimeCtx &ctx, uint64_t start, uint64_t n,
+                                                 int64_t &r0, int64_t &r1) {
+  using F = M64Form<AR>;
+  constexpr int V = F::V;
+  constexpr int K = CUBES ? F::KB : F::KE;
+  constexpr uint32_t BLK = F::BLK;
+  constexpr int EX = CUBES ? 3 : 2;
+  constexpr int DA = K * EX;
+  constexpr int DB = (K - 1) * EX;
+  const int lane = threadIdx.x & 31;
+  const Mont M(ctx);
+  M64K KK;
+  KK.p = ctx.p;
+  KK.p0 = (uint32_t)ctx.p;
+  KK.p1 = (uint32_t)(ctx.p >> 32);
+  KK.q = 0u - (uint32_t)ctx.q;  // -p^-1 mod 2^32
+  KK.mhi = (uint32_t)((1ull << 62) / ctx.p);
+  const uint64_t z64 = (V & 1) ? (uint64_t)(ctx.flags >> 16) : 0ull;  // runtime zero
+  const uint64_t nch = 32 * ILP;
+  const uint64_t len = n / nch;
+  const uint32_t rem = (uint32_t)(n - len * nch);
+  const uint64_t G = len / K;
+  uint64_t c0[ILP], c1[ILP], ga[ILP][DA + 1], gb[ILP][DB + 1];
+  uint64_t s_tail[ILP];
+  uint32_t n_tail[ILP];
+#pragma unroll
+  for (int k = 0; k < ILP; ++k) {
+    const uint32_t ch = k * 32 + lane;
+    const uint64_t s = start + ch * len + (ch < rem ? ch : rem);
+    const uint64_t L = len + (ch < rem ? 1 : 0);
+    s_tail[k] = s + G * K;
+    n_tail[k] = (uint32_t)(L - G * K);
+    // Difference tables of the group polynomials at s, s + K, ..., s + DA K.
+    // Each point's pair is built from the plain powers t = x^e of its K
+    // consecutive x by the running recurrence P <- P t, Q <- Q t + P (start
+    // P = t, Q = R) in the two-round REDC above, which gives
+    // G0 = R^-(K-1) prod t_i and G1 = R^-(K-2) sum_i prod_{j != i} t_j: the
+    // same factor R^-(K-1) on G0 and on R G1, so c1 / c0 is unchanged.  The
+    // points are visited from the top down (x^e by backward differences) and
+    // folded into the tables' diagonal as they come: e_j <- (-1)^j D^j.
+    const uint64_t p = ctx.p;
+    {
+      uint64_t xr = s + (uint64_t)(K * (DA + 1) - 1);
+      xr = xr >= p ? xr % p : xr;
+      const uint64_t sq = (uint64_t)M.mulmod((int64_t)xr, (int64_t)xr);
+      uint64_t t, d1, d2;
+      if (EX == 3) {  // x^3, 3x^2 - 3x + 1, 6x - 6, 6
+        t = (uint64_t)M.mulmod((int64_t)sq, (int64_t)xr);
+        d1 = ((3 * sq + 1) % p + p - (3 * xr) % p) % p;
+        d2 = (6 * xr + 6 * p - 6) % p;
+      } else {        // x^2, 2x - 1, 2
+        t = sq;
+        d1 = (2 * xr + p - 1) % p;
+        d2 = 2;
+      }
+#pragma unroll
+      for (int m = DA; m >= 0; --m) {
+        uint64_t P = 0, Q = ctx.one;
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+          if (i == 0) {
+            P = t;
+          } else {
+            Q = m64_once(m64_mm(Q, t, KK) + P, p);
+            P = m64_mm(P, t, KK);
+          }
+          t = m64_subm(t, d1, p);
+          d1 = m64_subm(d1, d2, p);
+          if (EX == 3) d2 = m64_subm(d2, 6, p);
+        }
+        // fold the new point into the diagonals (point DA - m of the sequence)
+        uint64_t nv = m64_once(P, p);
+#pragma unroll
+        for (int j = 0; j <= DA - m; ++j) {
+          const uint64_t old = ga[k][j];
+          ga[k][j] = nv;
+          if (j < DA - m) nv = m64_subm(nv, old, p);
+        }
+        if (m <= DB) {
+          nv = m64_once(Q, p);
+#pragma unroll
+          for (int j = 0; j <= DB - m; ++j) {
+            const uint64_t old = gb[k][j];
+            gb[k][j] = nv;
+            if (j < DB - m) nv = m64_subm(nv, old, p);
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 1; j <= DA; j += 2) ga[k][j] = ga[k][j] ? p - ga[k][j] : 0;
+#pragma unroll
+      for (int j = 1; j <= DB; j += 2) gb[k][j] = gb[k][j] ? p - gb[k][j] : 0;
+    }
+    c0[k] = ctx.one;
+    c1[k] = 0;
+  }
+  for (uint64_t g = 0; g < G;) {
+    const uint32_t nb = (G - g < BLK) ? (uint32_t)(G - g) : BLK;
+#pragma unroll 1
+    for (uint32_t r = 0; r < nb; ++r) {
+#pragma unroll
+      for (int k = 0; k < ILP; ++k) {
+        uint32_t T0;
+        uint64_t TY;
+        m64_prod(c0[k], ga[k][0], T0, TY);
+        const uint64_t n0 = (V & 2) ? m64_redc2_nz(T0, TY, KK) : m64_redc2(T0, TY, KK);
+        m64_prod2(c1[k], ga[k][0], c0[k], gb[k][0], T0, TY);
+        c1[k] = (V & 2) ? m64_redc2_nz(T0, TY, KK) : m64_redc2(T0, TY, KK);
+        c0[k] = n0;
+#pragma unroll
+        for (int j = 0; j < DA; ++j) ga[k][j] = ga[k][j] + ga[k][j + 1] + z64;
+#pragma unroll
+        for (int j = 0; j < DB; ++j) gb[k][j] = gb[k][j] + gb[k][j + 1] + z64;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < ILP; ++k) {
+#pragma unroll
+      for (int j = 0; j < DA; ++j) ga[k][j] = m64_shrink(ga[k][j], KK);
+#pragma unroll
+      for (int j = 0; j < DB; ++j) gb[k][j] = m64_shrink(gb[k][j], KK);
+    }
+    g += nb;
+  }
+  // canonical accumulators, then the last (at most K) terms one at a time
+  int64_t a0 = 0, a1 = 0;
+#pragma unroll
+  for (int k = 0; k < ILP; ++k) {
+    int64_t x0 = (int64_t)(c0[k] >= ctx.p ? c0[k] - ctx.p : c0[k]);
+    int64_t x1 = (int64_t)(c1[k] >= ctx.p ? c1[k] - ctx.p : c1[k]);
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      if ((uint32_t)i < n_tail[k]) {
+        const int64_t b = M.to_mont((int64_t)(s_tail[k] + i));
+        int64_t tm = M.mul(b, b);
+        if (EX == 3) tm = M.mul(tm, b);
+        const int64_t t = M.from_mont(tm);
+        x1 = M.add(M.mul(x1, t), x0);  // REDC(c1 t) + c0, as in eqn 3.12's single step
+        x0 = M.mul(x0, t);
+      }
+    }
+    if (k == 0) {
+      a0 = x0;
+      a1 = x1;
+    } else {
+      M.combine(a0, a1, x0, x1);
+    }
+  }
+  warp_merge(M, a0, a1);
+  r0 = a0;
+  r1 = a1;
+}
+
+// ------------------------------------------------------------------ accumulate
+// One warp tile g of plan P: find its (prime, row) segment, sum its range of
+// terms, merge the lanes, and store the tile's (c0, c1) pair.
+template <bool WIDE, int ILP, int AR>
+__device__ __forceinline__ void process_tile(const Plan &P, uint32_t g) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t nsegs = P.n * P.rows_pp;
+  // segment owning tile g: the last s with seg_first[s] <= g
+  uint32_t lo = 0, hi = nsegs;
+  while (hi - lo > 1) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (__ldg(&P.seg_first[mid]) <= g) lo = mid; else hi = mid;
+  }
+  const uint32_t s = lo;
+  const uint32_t slot = s / P.rows_pp, j = s - slot * P.rows_pp;
+  const PrimeCtx ctx = P.ctx[slot];
+  const uint32_t k = g - P.seg_first[s], T = P.seg_tiles[s];
+  const uint64_t cnt = P.seg_cnt[s];
+  const uint64_t b0 = cnt * k / T, b1 = cnt * (k + 1) / T;
+  const uint64_t start = P.seg_lo[s] + b0, n = b1 - b0;
+  int64_t r0, r1;
+  // single-term form used beside the grouped one
+  constexpr int AS = (AR == 5 || AR >= 8) ? 4 : AR;
+  const bool grp_ok = n >= 32ull * ILP * kGroupMinChain;
+  if (!WIDE && AR == 5 && grp_ok) {
+    if (j < P.rows_b) tile_m31_grouped<ILP, true, 5>(ctx, start, n, r0, r1);
+    else tile_m31_grouped<ILP, false, 5>(ctx, start, n, r0, r1);
+  } else if (!WIDE && AR >= 7 && grp_ok && j >= P.rows_b) {
+    tile_m31_grouped<ILP, false, 7>(ctx, start, n, r0, r1);
+  } else if (!WIDE && AR >= 9 && grp_ok) {
+    tile_m31_grouped<ILP, true, 7>(ctx, start, n, r0, r1);
+  } else if (!WIDE) {
+    if (j < P.rows_b) tile_m31<ILP, true, AS>(ctx, start, n, r0, r1);
+    else tile_m31<ILP, false, AS>(ctx, start, n, r0, r1);
+  } else if (AR >= 9 && grp_ok) {
+    if (j < P.rows_b) tile_m64_grouped<ILP, true, AR>(ctx, start, n, r0, r1);
+    else tile_m64_grouped<ILP, false, AR>(ctx, start, n, r0, r1);
+  } else {
+    if (j < P.rows_b) tile_m64<ILP, true>(ctx, start, n, r0, r1);
+    else tile_m64<ILP, false>(ctx, start, n, r0, r1);
+  }
+  if (lane == 0) P.partials[g] = make_ulonglong2((unsigned long long)r0, (unsigned long long)r1);
+}
+
+template <bool WIDE, int ILP, int AR>
+__global__ void __launch_bounds__(kAccThreads) k_accumulate(Plan P) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t total = *P.total_tiles, split = *P.split_tile;
+  const uint32_t t_begin = WIDE ? split : 0u, t_end = WIDE ? total : split;
+  const uint32_t ntiles = t_end - t_begin;
+  uint32_t *counter = P.counters + (WIDE ? 1 : 0);
+  for (;;) {
+    uint32_t g = 0;
+    if (lane == 0) g = atomicAdd(counter, 1u);
+    g = __shfl_sync(0xffffffffu, g, 0);
+    if (g >= ntiles) break;
+    process_tile<WIDE, ILP, AR>(P, t_end - 1 - g);  // largest primes first
+  }
+}
+
+// Epoch form: tiles of several plans (one per request of a serving loop),
+// given as items {plan, first tile, count, prefix}; the items' tiles are
+// taken from one counter, each item from its top tile down.
+template <bool WIDE, int ILP, int AR>
+__global__ void __launch_bounds__(kAccThreads)
+    k_epoch(const EpochItem *items, uint32_t n_items, uint32_t total, const Plan *plans,
+            uint32_t *counter) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    uint32_t g = 0;
+    if (lane == 0) g = atomicAdd(counter, 1u);
+    g = __shfl_sync(0xffffffffu, g, 0);
+    if (g >= total) break;
+    uint32_t lo = 0, hi = n_items;
+    while (hi - lo > 1) {
+      uint32_t mid = (lo + hi) >> 1;
+      if (__ldg(&items[mid].prefix) <= g) lo = mid; else hi = mid;
+    }
+    const EpochItem it = items[lo];
+    process_tile<WIDE, ILP, AR>(plans[it.plan], it.first + it.count - 1 - (g - it.prefix));
+  }
+}
+
+// Epoch form with both arithmetic paths in one launch: items with bit 31 of
+// `plan` set are 64-bit-path tiles.  One launch (and one tail) per epoch.
+template <int I31, int I64>
+__global__ void __launch_bounds__(kAccThreads)
+    k_epoch_mixed(const EpochItem *items, uint32_t n_items, uint32_t total, const Plan *plans,
+                  uint32_t *counter) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    uint32_t g = 0;
+    if (lane == 0) g = atomicAdd(counter, 1u);
+    g = __shfl_sync(0xffffffffu, g, 0);
+    if (g >= total) break;
+    uint32_t lo = 0, hi = n_items;
+    while (hi - lo > 1) {
+      uint32_t mid = (lo + hi) >> 1;
+      if (__ldg(&items[mid].prefix) <= g) lo = mid; else hi = mid;
+    }
+    const EpochItem it = items[lo];
+    const uint32_t tile = it.first + it.count - 1 - (g - it.prefix);
+    if (it.plan >> 31) process_tile<true, I64, 9>(plans[it.plan & 0x7fffffffu], tile);
+    else process_tile<false, I31, 9>(plans[it.plan], tile);
+  }
+}
+
+// ------------------------------------------------------------------ getters
+using AccKernel = void (*)(Plan);
+using EpochKernel = void (*)(const EpochItem *, uint32_t, uint32_t, const Plan *, uint32_t *);
+// 32-bit path: formulation 1..9, ILP 1, 2 (any formulation) or 4 (formulation 9)
+AccKernel acc_kernel_m31(int arith, int ilp);
+// 64-bit path: formulation 1 (single terms, ILP 1, 2 or 4) or 9 (grouped
+// default, one chain per thread)
+AccKernel acc_kernel_m64(int arith, int ilp);
+// 64-bit path formulations kept for ablation (arith 10..17), one chain per thread
+AccKernel acc_kernel_m64x(int arith, int ilp);
+// serving-loop epoch kernels (formulation 9; one chain per thread on the 64-bit path)
+EpochKernel epoch_kernel(bool wide, int ilp);
+EpochKernel epoch_mixed_kernel(int ilp31, int ilp64);
+
+}  // namespace wv

@@ -95,11 +95,13 @@ struct ResidueConfig {
   int cong_b = 6;        // BB30; -2 = skip
   int cong_e = 12;       // EE33; -2 = skip
   int block = 256;
-  int ilp = 2;
+  int ilp = 2;            // chains per thread, p < 2^30
+  int ilp64 = 1;          // chains per thread, 2^30 <= p < 2^37
   int tile_terms = 1 << 20;
   int max_tiles = 8;
+  bool tiles_auto = true; // few primes: more, shorter tiles (see tile_shape)
   int blocks_per_sm = 0;  // 0 = occupancy
-  int arith = 9;          // p < 2^30 hot-loop formulation (see wv_residue.cu)
+  int arith = 9;          // hot-loop formulation (see wv_accum.cuh)
   size_t chunk = 0;       // primes per launch sequence (0: library default 16384)
 };
 wv_status resolve_config(const wv_options *opt, bool want_b, bool want_e, ResidueConfig *cfg);

@@ -283,9 +283,10 @@ wv_status resolve_config(const wv_options *opt, bool want_b, bool want_e, Residu
     if (want_b && opt->cong_b >= 0) c.cong_b = opt->cong_b;
     if (want_e && opt->cong_e >= 0) c.cong_e = opt->cong_e;
     if (opt->block > 0) c.block = opt->block;
-    if (opt->ilp > 0) c.ilp = opt->ilp;
+    if (opt->ilp > 0) c.ilp = c.ilp64 = opt->ilp;
     if (opt->tile_terms > 0) c.tile_terms = opt->tile_terms;
     if (opt->max_tiles > 0) c.max_tiles = opt->max_tiles;
+    if (opt->tile_terms > 0 || opt->max_tiles > 0) c.tiles_auto = false;
     if (opt->blocks_per_sm > 0) c.blocks_per_sm = opt->blocks_per_sm;
     if (opt->arith > 0) c.arith = opt->arith;
   }
@@ -293,11 +294,14 @@ wv_status resolve_config(const wv_options *opt, bool want_b, bool want_e, Residu
     return set_error(WV_EINVAL, "cong_b=%d is not a Bernoulli congruence", c.cong_b);
   if (c.cong_e >= 0 && (c.cong_e >= kWvNumCongruences || kWvCongruences[c.cong_e].kind != 1))
     return set_error(WV_EINVAL, "cong_e=%d is not an Euler congruence", c.cong_e);
-  if (c.block < 32 || c.block > 1024 || c.block % 32)
-    return set_error(WV_EINVAL, "block=%d must be a multiple of 32 in [32,1024]", c.block);
+  if (c.block < 32 || c.block > 256 || c.block % 32)
+    return set_error(WV_EINVAL, "block=%d must be a multiple of 32 in [32,256]", c.block);
   if (c.ilp != 1 && c.ilp != 2 && c.ilp != 4)
     return set_error(WV_EINVAL, "ilp=%d must be 1, 2 or 4", c.ilp);
-  if (c.arith < 1 || c.arith > 9) return set_error(WV_EINVAL, "arith=%d must be in 1..9", c.arith);
+  if (c.arith < 1 || c.arith > 17) return set_error(WV_EINVAL, "arith=%d must be in 1..17", c.arith);
+  if (c.ilp == 4 && c.arith < 9)
+    return set_error(WV_EINVAL, "ilp=4 is built for formulations >= 9 only (arith=%d)", c.arith);
+  if (c.arith >= 9) c.ilp64 = 1;  // the grouped 64-bit forms run one chain per thread
   if (c.max_tiles > 4096) return set_error(WV_EINVAL, "max_tiles=%d > 4096", c.max_tiles);
   *cfg = c;
   return WV_OK;

@@ -172,14 +172,18 @@ def test_edge_cases(orc):
 
 
 def test_launch_shapes_agree():
-    """Ragged tiles, many tiles per sum, ILP 1/2/4 and the single-kind entry
-    points all give the identical residues."""
-    ps = np.concatenate([u64(api.sieve(10**6, 10**6 + 3000)), u64(api.sieve(2**31, 2**31 + 400))])
+    """Ragged tiles, many tiles per sum, ILP 1/2/4, block sizes, every
+    formulation of both arithmetic paths and the single-kind entry points all
+    give the identical residues."""
+    ps = np.concatenate([u64(api.sieve(10**6, 10**6 + 3000)), u64(api.sieve(2**31, 2**31 + 400)),
+                         u64(api.sieve(2**36 - 300, 2**36))])
     ref_b, ref_e = gpu_residues(ps)
     for opt in ({"ilp": 1}, {"ilp": 4}, {"tile_terms": 97, "max_tiles": 4096},
                 {"tile_terms": 1 << 20, "max_tiles": 1}, {"blocks_per_sm": 1},
                 {"arith": 1}, {"arith": 2}, {"arith": 4}, {"arith": 9, "ilp": 1},
-                {"arith": 9, "tile_terms": 5000, "max_tiles": 64}):
+                {"arith": 9, "tile_terms": 5000, "max_tiles": 64},
+                {"block": 32}, {"block": 96, "ilp": 1}, {"block": 128},
+                *({"arith": a} for a in range(10, 18))):
         gb, ge = gpu_residues(ps, opt)
         assert np.array_equal(gb, ref_b), opt
         assert np.array_equal(ge, ref_e), opt
