@@ -38,6 +38,12 @@ SM_MAX_MHZ_FALLBACK = 2070.0
 # capture of the 492-prime head of the window (1.21984 MB read, 0 written), scaled by primes to the
 # 4907-prime launch.  Must be re-taken (or set to None) whenever that kernel changes.
 ACC_TRAFFIC_BYTES = 1.21984e6 * 4907 / 492
+# --workload top: the 391 primes of [1e11 - 1e4, 1e11) on the 64-bit path.  One 64-bit
+# Montgomery product for p < 2^37 (R = 2^64 in two 32-bit REDC rounds) costs 17 IMAD slots:
+# c g as three mul.wide and one mul.lo (7), each REDC round one mul.lo and two mul.wide (10).
+TOP_LO, TOP_WIDTH = 10**11 - 10**4, 10**4
+IMAD_SLOTS_PER_MODMUL64 = 17
+ACC64_TRAFFIC_BYTES = None
 
 
 def dist_env():
@@ -190,8 +196,13 @@ def gpu_arm(args):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    width = args.width
-    lo = LO + rank * WIDTH
+    top = args.workload == "top"
+    if top:  # rank r takes the r-th 1e4-wide window below 1e11
+        width = min(args.width, TOP_WIDTH)
+        lo = TOP_LO - rank * TOP_WIDTH
+    else:
+        width = args.width
+        lo = LO + rank * WIDTH
     hi = lo + width
     stream = torch.cuda.current_stream()
     props = torch.cuda.get_device_properties(local)
@@ -272,7 +283,7 @@ def gpu_arm(args):
 
     # CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
-    if ws == 1 and rank == 0 and not args.no_cpu:
+    if ws == 1 and rank == 0 and not args.no_cpu and not top:
         sample = oracle_sample(2, seed=7)
         dt, res = run_oracle_step(sample, threads=4)
         cpu = {"value": len(sample) / dt, "unit": "primes/s", "cores": 4, "kind": "oracle",
@@ -283,13 +294,15 @@ def gpu_arm(args):
         gb, ge = api.to_u64(d_rb)[idx], api.to_u64(d_re)[idx]
         cpu["agrees_with_gpu"] = bool(np.array_equal(gb, res["b"]) and np.array_equal(ge, res["e"]))
 
-    # roofline of the dominant kernel (the p < 2^30 accumulation)
-    acc_launches, acc_ms = prof.get("accumulate_m31", (0, 0.0))
+    # roofline of the dominant kernel (the p < 2^30 accumulation; the 64-bit one for top)
+    kname = "accumulate_m64" if top else "accumulate_m31"
+    slots = IMAD_SLOTS_PER_MODMUL64 if top else IMAD_SLOTS_PER_MODMUL
+    acc_launches, acc_ms = prof.get(kname, (0, 0.0))
     acc_avg_ms = acc_ms / max(1, acc_launches)
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz") or SM_MAX_MHZ_FALLBACK)
     imad_peak = sms * IMAD_PER_SM_CLK * sm_max * 1e6            # IMAD results / s
-    peak_gmodmul = imad_peak / IMAD_SLOTS_PER_MODMUL / 1e9
+    peak_gmodmul = imad_peak / slots / 1e9
     achieved_gmodmul = (modmuls_per_step / (acc_avg_ms / 1000.0)) / 1e9 if acc_avg_ms else 0.0
     total_primes = n_primes * ws
     value = total_primes / (ms / 1000.0)
@@ -299,18 +312,20 @@ def gpu_arm(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic: every prime of the window, sieved on the device (no dataset)",
         "config": {"workload": f"sieve + B_{{p-3}} (BB30, eqn 3.7) + E_{{p-3}} (EE33, eqn 5.6) mod p "
-                               f"+ zero/near flags for all primes in [{lo}, {hi}) per GPU",
+                               f"+ zero/near flags for all primes in [{lo}, {hi}) per GPU"
+                               + (" (64-bit path, 2^30 <= p < 2^37)" if top else ""),
                    "primes_per_gpu": int(n_primes), "congruences": "BB30+EE33",
                    "terms_per_step": int(tb + te), "parallelism": f"range-sharded x{ws}",
                    "l2": "flushed between steps (256 MB write)"},
         "modmul_per_s": modmuls_per_step * ws / (ms / 1000.0),
         "roofline": {"bound": "alu", "achieved": achieved_gmodmul, "peak": peak_gmodmul,
                      "unit": "Gmodmul/s", "frac": achieved_gmodmul / peak_gmodmul if peak_gmodmul else None,
-                     "traffic": ACC_TRAFFIC_BYTES if width == WIDTH else None,
+                     "traffic": (ACC64_TRAFFIC_BYTES if top else ACC_TRAFFIC_BYTES)
+                     if width == (TOP_WIDTH if top else WIDTH) else None,
                      "peak_basis": f"{sms} SMs x {IMAD_PER_SM_CLK} IMAD lanes/clk x {sm_max:.0f} MHz / "
-                                   f"{IMAD_SLOTS_PER_MODMUL} IMAD slots per 32-bit Montgomery product "
+                                   f"{slots} IMAD slots per {'64' if top else '32'}-bit Montgomery product "
                                    "(slot costs measured by wv_diag_throughput)",
-                     "kernel": "accumulate_m31", "kernel_ms": acc_avg_ms},
+                     "kernel": kname, "kernel_ms": acc_avg_ms},
         "e2e": {"value": total_primes / (e2e_step / 1000.0), "unit": "primes/s",
                 "h2d_bytes_per_step": int(n_primes * 8), "d2h_bytes_per_step": int(n_primes * 16),
                 "path": "host prime list (pinned) -> wv_residues_pm3 -> host residues"},
@@ -321,6 +336,14 @@ def gpu_arm(args):
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if top:
+        line["cpu_baseline"] = None
+        line["cpu_baseline_note"] = ("not timed: the oracle needs about 20 core-minutes per prime "
+                                     "near 1e11 (eqn 2.4 / eqn 4.1 single sums)")
+        line["note"] = ("achieved counts 2 modmuls per summed term (eqn 3.12); the grouped "
+                        "formulation (8 cubes / 10 squares per eqn 3.14 step) issues far fewer "
+                        "multiply-pipe slots per term than two 17-slot products, so frac can "
+                        "exceed 1; the ncu pipe counters in profiles/ give the pipe utilisation")
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -405,7 +428,8 @@ def serve_arm(args):
             if q["kind"] == "range":
                 q["hi"] = min(q["hi"], q["lo"] + args.max_range)
     # served
-    srv = wv.wv_server_create(epoch_terms=args.epoch_terms)
+    srv = wv.wv_server_create(epoch_terms=args.epoch_terms, epoch_form=args.epoch_form,
+                              epoch_block=args.epoch_block)
     t0 = time.perf_counter()
     ids = []
     for q in stream:
@@ -420,6 +444,8 @@ def serve_arm(args):
     served_res = [wv.wv_server_result(srv, i) for i in ids]
     wv.wv_server_destroy(srv)
     lat = [i["t_done"] - i["t_submit"] for i in infos]
+    wait_admit = [i["t_admit"] - i["t_submit"] for i in infos]
+    service = [i["t_done"] - i["t_admit"] for i in infos]
     n_primes = sum(i["n_primes"] for i in infos)
     # plain: one query at a time, in arrival order
     t0 = time.perf_counter()
@@ -429,15 +455,16 @@ def serve_arm(args):
         dt = q["t"] - (time.perf_counter() - t0)
         if dt > 0:
             time.sleep(dt)
+        popt = {"block": args.plain_block} if args.plain_block else None
         if q["kind"] == "range":
             lo = max(q["lo"], 5)
             if q["hi"] > lo:
-                _, pr, rb, re = api.search(lo, q["hi"], with_residues=True)
+                _, pr, rb, re = api.search(lo, q["hi"], with_residues=True, options=popt)
             else:
                 pr = rb = re = torch.empty(0, dtype=torch.int64, device="cuda")
         else:
             pr = torch.tensor([q["p"]], dtype=torch.int64, device="cuda")
-            rb, re = api.residues(pr)
+            rb, re = api.residues(pr, options=popt)
         torch.cuda.synchronize()
         lat_p.append(time.perf_counter() - t0 - q["t"])
         same = same and np.array_equal(api.to_u64(rb), res[1]) and np.array_equal(api.to_u64(re), res[2])
@@ -454,9 +481,13 @@ def serve_arm(args):
             "value": n_primes / makespan, "unit": "primes/s", "plain_value": n_primes / makespan_p,
             "makespan_s": makespan, "plain_makespan_s": makespan_p,
             "latency": stats(lat), "plain_latency": stats(lat_p), "identical_results": bool(same),
+            "admission_wait": stats(wait_admit), "service_time": stats(service),
             "server": st, "config": {"queries": len(stream), "rate_per_s": args.rate, "seed": 11,
                                      "range_len_cap": args.max_range or None,
-                                     "epoch_terms": args.epoch_terms, "primes": int(n_primes)}}
+                                     "epoch_terms": args.epoch_terms, "primes": int(n_primes),
+                                     "plain_block": args.plain_block or None,
+                                     "epoch_form": args.epoch_form,
+                                     "epoch_block": args.epoch_block or 32}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -469,13 +500,18 @@ def main():
     ap.add_argument("--impl", default="wv", choices=["wv", "reference"])
     ap.add_argument("--width", type=int, default=WIDTH, help="window width (smaller for profiling)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--workload", default="window", choices=["window", "batch", "serve"])
+    ap.add_argument("--workload", default="window", choices=["window", "top", "batch", "serve"])
     ap.add_argument("--requests", type=int, default=64, help="batch: number of requests")
     ap.add_argument("--max-len", type=int, default=4096, help="batch: longest request")
     ap.add_argument("--queries", type=int, default=256, help="serve: queries in the stream")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrivals per second")
     ap.add_argument("--max-range", type=int, default=0, help="serve: cap on range length (0: none)")
     ap.add_argument("--epoch-terms", type=float, default=4e10, help="serve: terms per epoch")
+    ap.add_argument("--epoch-form", type=int, default=0,
+                    help="serve: 0 persistent per path, 1 persistent over both paths, 2 one warp per tile")
+    ap.add_argument("--epoch-block", type=int, default=0, help="serve: epoch block size (0: 32)")
+    ap.add_argument("--plain-block", type=int, default=0,
+                    help="serve: accumulation block size of the one-query-at-a-time form (0: default)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)

@@ -153,13 +153,13 @@ typedef struct {
                        call with few primes gets more and shorter tiles (up to 64 per
                        sum) so that one launch still holds ~1e5 tiles */
   int blocks_per_sm;/* persistent grid = SMs x this */
-  int arith;        /* hot-loop formulation, 1..17 (default 9: grouped terms, REDC folded
+  int arith;        /* hot-loop formulation, 1..22 (default 9: grouped terms, REDC folded
                        into wide multiply-adds, on both paths).  1..8 select the single-
                        term and intermediate forms of the 32-bit path for ablation, and
-                       any value below 9 the single-term 64-bit path; 10..17 select other
+                       any value below 9 the single-term 64-bit path; 10..22 select other
                        grouped 64-bit forms (group sizes, shrink interval, instruction
-                       choices; one chain per thread) for ablation, with formulation 9
-                       on the 32-bit path */
+                       choices, register budget; one chain per thread) for ablation,
+                       with formulation 9 on the 32-bit path */
   int reserved[8];
 } wv_options;
 
@@ -204,6 +204,22 @@ wv_status wv_search_ex(uint64_t lo, uint64_t hi, uint64_t near, wv_hit *d_hits,
                        size_t cap, size_t *n_hits, uint64_t *d_primes,
                        uint64_t *d_res_b, uint64_t *d_res_e, size_t cap_primes,
                        size_t *n_primes, const wv_options *opt, wv_stream stream);
+
+/*
+ * Histogram mode (Sec. 3 "Results": the histogram of <B_{p-3}>_p / p over
+ * 2000 equal bins, where <r>_p is the representative of r mod p in
+ * (-p/2, p/2]).  For every prime p of [lo, hi) (5 <= p), with
+ * u = <r>_p / p + 1/2 in (0, 1), ADDS 1 to hist[floor(u * bins)]: bin b holds
+ * u in [b / bins, (b + 1) / bins) (only r = 0 lies on an edge, u = 1/2).
+ * d_hist_b receives the counts of r = B_{p-3} mod p, d_hist_e those of
+ * r = E_{p-3} mod p (either may be NULL, not both); each is a caller-owned
+ * device array of `bins` uint64 counters, 1 <= bins <= 2^20, which the call
+ * adds to (zero it first; disjoint ranges may be accumulated over calls).
+ * *n_primes (may be NULL) receives the number of primes counted.
+ * SYNCHRONOUS: the counts are complete on return.
+ */
+wv_status wv_histogram(uint64_t lo, uint64_t hi, uint32_t bins, unsigned long long *d_hist_b,
+                       unsigned long long *d_hist_e, size_t *n_primes, wv_stream stream);
 
 /* ---------------------------------------------------------------------- */
 /* host-side inspection of the congruence tables (no GPU needed)           */

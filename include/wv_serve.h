@@ -27,11 +27,15 @@ extern "C" {
 typedef struct wv_server_s *wv_server;
 
 typedef struct {
-  size_t mem_budget;     /* device bytes for admitted queries (0: 4 GiB)            */
+  size_t mem_budget;     /* device bytes for admitted queries (0: 16 GiB)           */
   uint32_t max_active;   /* queries admitted at once (0: 256)                        */
   double epoch_terms;    /* summed terms per epoch, bounds its duration (0: 4e10)    */
   int device;            /* CUDA device (-1: current device at creation)              */
-  int reserved[7];
+  int epoch_form;        /* epoch launch: 0 one persistent launch per arithmetic path
+                            (default), 1 one persistent launch over both paths,
+                            2 one warp per tile (non-persistent, both paths)          */
+  int epoch_block;       /* threads per block of an epoch launch, 32..256 (0: 32)     */
+  int reserved[5];
 } wv_server_config;
 
 typedef struct {
@@ -39,7 +43,7 @@ typedef struct {
   int kind;              /* 0 = range, 1 = single prime                              */
   int state;             /* 0 pending, 1 active, 2 done, 3 failed, 4 cancelled       */
   wv_status status;      /* final status once done/failed                            */
-  uint64_t n_primes;     /* primes in the query                                       */
+  uint64_t n_primes;     /* primes in the query (an upper bound until it is admitted) */
   uint64_t n_hits;       /* primes with a zero residue                                */
   double t_submit, t_admit, t_done; /* seconds since the server was created            */
 } wv_query_info;

@@ -22,6 +22,7 @@ Levels (see ``wv_oracle.c`` for the passage each one follows):
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -224,3 +225,16 @@ def symmetric(r: int, p: int) -> int:
     """The representative of r mod p in (-p/2, p/2] (Sec. 3, near-miss tables)."""
     r %= p
     return r - p if r > p // 2 else r
+
+
+def histogram(primes, residues, bins: int = 2000) -> np.ndarray:
+    """Counts of <r>_p / p over `bins` equal bins of (-1/2, 1/2] (Sec. 3
+    "Results": the 2000-bin histogram of <B_{p-3}>_p / p).  Bin b holds the
+    primes with u = <r>_p / p + 1/2 in [b / bins, (b + 1) / bins), computed
+    with exact rationals."""
+    out = np.zeros(bins, dtype=np.int64)
+    for p, r in zip(primes, residues):
+        p, r = int(p), int(r)
+        u = Fraction(symmetric(r, p), p) + Fraction(1, 2)
+        out[math.floor(u * bins)] += 1
+    return out

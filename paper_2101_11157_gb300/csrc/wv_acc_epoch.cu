@@ -14,4 +14,8 @@ EpochKernel epoch_mixed_kernel(int ilp31, int) {
   return ilp31 == 1 ? k_epoch_mixed<1, 1> : k_epoch_mixed<2, 1>;
 }
 
+EpochTilesKernel epoch_tiles_kernel(int ilp31) {
+  return ilp31 == 1 ? k_epoch_tiles<1, 1> : k_epoch_tiles<2, 1>;
+}
+
 }  // namespace wv

@@ -5,7 +5,7 @@
 namespace wv {
 
 AccKernel acc_kernel_m64(int arith, int ilp) {
-  if (arith == 9) return k_accumulate<true, 1, 9>;
+  if (arith == 9) return k_accumulate_m64cap<9, kM64MaxReg>;
   return ilp == 1 ? k_accumulate<true, 1, 1> : ilp == 2 ? k_accumulate<true, 2, 1>
                                                         : k_accumulate<true, 4, 1>;
 }

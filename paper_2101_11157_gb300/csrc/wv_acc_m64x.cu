@@ -1,6 +1,7 @@
 // wv_acc_m64x.cu -- the 64-bit-path formulations kept for ablation
-// (wv_options.arith 10..17: other group sizes, shrink intervals and the two
-// flags of M64Form), one chain per thread.  The code is in wv_accum.cuh.
+// (wv_options.arith 10..22: other group sizes, shrink intervals, the two
+// flags and the register budgets of M64Form), one chain per thread.  The
+// code is in wv_accum.cuh.
 #include "wv_accum.cuh"
 
 namespace wv {
@@ -15,7 +16,12 @@ AccKernel acc_kernel_m64x(int arith, int) {
     case 14: return k_accumulate<true, I, 14>;
     case 15: return k_accumulate<true, I, 15>;
     case 16: return k_accumulate<true, I, 16>;
-    default: return k_accumulate<true, I, 17>;
+    case 17: return k_accumulate<true, I, 17>;
+    case 18: return k_accumulate<true, I, 18>;
+    case 19: return k_accumulate_m64cap<19, 96>;
+    case 20: return k_accumulate_m64cap<20, 168>;
+    case 21: return k_accumulate_m64cap<21, kM64MaxReg>;
+    default: return k_accumulate_m64cap<22, kM64MaxReg>;
   }
 }
 

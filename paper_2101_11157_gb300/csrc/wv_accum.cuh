@@ -495,6 +495,16 @@ template <> struct M64Form<14> { static constexpr int KB = 4, KE = 5, BLK = 16, 
 template <> struct M64Form<15> { static constexpr int KB = 5, KE = 6, BLK = 16, V = 0; };
 template <> struct M64Form<16> { static constexpr int KB = 6, KE = 8, BLK = 16, V = 0; };
 template <> struct M64Form<17> { static constexpr int KB = 7, KE = 9, BLK = 16, V = 0; };
+// 18..22: the register budget.  Form 9 runs under a cap of kM64MaxReg
+// registers per thread (16 resident warps per SM, a few bytes of spill in
+// the setup); 18 is form 9 without the cap (8 warps), 19 and 20 caps of 96
+// and 168, 21 and 22 other group sizes under the cap of 128.
+constexpr int kM64MaxReg = 128;
+template <> struct M64Form<18> : M64Form<9> {};
+template <> struct M64Form<19> : M64Form<9> {};
+template <> struct M64Form<20> : M64Form<9> {};
+template <> struct M64Form<21> { static constexpr int KB = 9, KE = 11, BLK = 16, V = 0; };
+template <> struct M64Form<22> : M64Form<17> {};
 
 // a b 2^-64 mod p, below p + 2^12 for a, b < 2^38
 __device__ __forceinline__ uint64_t m64_mm(uint64_t a, uint64_t b, const M64K &K) {
@@ -711,7 +721,7 @@ __device__ __forceinline__ void process_tile(const Plan &P, uint32_t g) {
 }
 
 template <bool WIDE, int ILP, int AR>
-__global__ void __launch_bounds__(kAccThreads) k_accumulate(Plan P) {
+__device__ __forceinline__ void accumulate_loop(const Plan &P) {
   const int lane = threadIdx.x & 31;
   const uint32_t total = *P.total_tiles, split = *P.split_tile;
   const uint32_t t_begin = WIDE ? split : 0u, t_end = WIDE ? total : split;
@@ -726,11 +736,23 @@ __global__ void __launch_bounds__(kAccThreads) k_accumulate(Plan P) {
   }
 }
 
+template <bool WIDE, int ILP, int AR>
+__global__ void __launch_bounds__(kAccThreads) k_accumulate(Plan P) {
+  accumulate_loop<WIDE, ILP, AR>(P);
+}
+
+// The 64-bit path with a register cap (any block size): fewer registers per
+// thread, more resident warps.
+template <int AR, int MAXREG>
+__global__ void __maxnreg__(MAXREG) k_accumulate_m64cap(Plan P) {
+  accumulate_loop<true, 1, AR>(P);
+}
+
 // Epoch form: tiles of several plans (one per request of a serving loop),
 // given as items {plan, first tile, count, prefix}; the items' tiles are
 // taken from one counter, each item from its top tile down.
 template <bool WIDE, int ILP, int AR>
-__global__ void __launch_bounds__(kAccThreads)
+__global__ void __maxnreg__(kM64MaxReg)
     k_epoch(const EpochItem *items, uint32_t n_items, uint32_t total, const Plan *plans,
             uint32_t *counter) {
   const int lane = threadIdx.x & 31;
@@ -752,7 +774,7 @@ __global__ void __launch_bounds__(kAccThreads)
 // Epoch form with both arithmetic paths in one launch: items with bit 31 of
 // `plan` set are 64-bit-path tiles.  One launch (and one tail) per epoch.
 template <int I31, int I64>
-__global__ void __launch_bounds__(kAccThreads)
+__global__ void __maxnreg__(kM64MaxReg)
     k_epoch_mixed(const EpochItem *items, uint32_t n_items, uint32_t total, const Plan *plans,
                   uint32_t *counter) {
   const int lane = threadIdx.x & 31;
@@ -773,6 +795,26 @@ __global__ void __launch_bounds__(kAccThreads)
   }
 }
 
+// Non-persistent epoch form: one warp per tile (grid = the epoch's tiles in
+// one-warp blocks), so warps retire tile by tile and the block scheduler
+// hands their slots to whatever is pending -- the next epoch, or admission
+// kernels on a higher-priority stream -- without a persistent grid's tail.
+template <int I31, int I64>
+__global__ void __maxnreg__(kM64MaxReg)
+    k_epoch_tiles(const EpochItem *items, uint32_t n_items, uint32_t total, const Plan *plans) {
+  const uint32_t g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (g >= total) return;
+  uint32_t lo = 0, hi = n_items;
+  while (hi - lo > 1) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (__ldg(&items[mid].prefix) <= g) lo = mid; else hi = mid;
+  }
+  const EpochItem it = items[lo];
+  const uint32_t tile = it.first + it.count - 1 - (g - it.prefix);
+  if (it.plan >> 31) process_tile<true, I64, 9>(plans[it.plan & 0x7fffffffu], tile);
+  else process_tile<false, I31, 9>(plans[it.plan], tile);
+}
+
 // ------------------------------------------------------------------ getters
 using AccKernel = void (*)(Plan);
 using EpochKernel = void (*)(const EpochItem *, uint32_t, uint32_t, const Plan *, uint32_t *);
@@ -781,10 +823,12 @@ AccKernel acc_kernel_m31(int arith, int ilp);
 // 64-bit path: formulation 1 (single terms, ILP 1, 2 or 4) or 9 (grouped
 // default, one chain per thread)
 AccKernel acc_kernel_m64(int arith, int ilp);
-// 64-bit path formulations kept for ablation (arith 10..17), one chain per thread
+// 64-bit path formulations kept for ablation (arith 10..22), one chain per thread
 AccKernel acc_kernel_m64x(int arith, int ilp);
 // serving-loop epoch kernels (formulation 9; one chain per thread on the 64-bit path)
 EpochKernel epoch_kernel(bool wide, int ilp);
 EpochKernel epoch_mixed_kernel(int ilp31, int ilp64);
+using EpochTilesKernel = void (*)(const EpochItem *, uint32_t, uint32_t, const Plan *);
+EpochTilesKernel epoch_tiles_kernel(int ilp31);
 
 }  // namespace wv

@@ -138,12 +138,16 @@ size_t plan_struct_bytes();
 // Epoch launch over items (device array) of plans (device array).
 wv_status epoch_launch(bool wide, const EpochItem *d_items, uint32_t n_items, uint32_t total,
                        const Plan *d_plans, uint32_t *d_counter, const ResidueConfig &cfg,
-                       int sms, cudaStream_t s);
+                       int sms,
+                       int reserve_blocks, cudaStream_t s);
 // One launch for items of both paths (bit 31 of EpochItem::plan marks 64-bit items).
 // `reserve_blocks` leaves room on the SMs for concurrent kernels of other streams.
 wv_status epoch_launch_mixed(const EpochItem *d_items, uint32_t n_items, uint32_t total,
                              const Plan *d_plans, uint32_t *d_counter, const ResidueConfig &cfg,
                              int sms, int reserve_blocks, cudaStream_t s);
+// Non-persistent form: one warp per tile (grid = total tiles), no counter.
+wv_status epoch_launch_tiles(const EpochItem *d_items, uint32_t n_items, uint32_t total,
+                             const Plan *d_plans, const ResidueConfig &cfg, cudaStream_t s);
 // Finalise every prime of the plan into d_out_b / d_out_e (asynchronous).
 wv_status plan_finalize(PlanState *ps, uint64_t *d_out_b, uint64_t *d_out_e, cudaStream_t s);
 void plan_free(PlanState *ps, cudaStream_t s);

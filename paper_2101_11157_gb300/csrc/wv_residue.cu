@@ -427,14 +427,17 @@ wv_status plan_upload(const PlanState *ps, Plan *d_plan, cudaStream_t s) {
 
 wv_status epoch_launch(bool wide, const EpochItem *d_items, uint32_t n_items, uint32_t total,
                        const Plan *d_plans, uint32_t *d_counter, const ResidueConfig &cfg, int sms,
-                       cudaStream_t s) {
+                       int reserve_blocks, cudaStream_t s) {
   if (total == 0) return WV_OK;
   EpochKernel kern = epoch_kernel(wide, wide ? cfg.ilp64 : cfg.ilp);
   int occ = 0;
   WV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, cfg.block, 0));
   if (occ < 1) occ = 1;
   WV_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(uint32_t), s));
-  WV_LAUNCH(wide ? "epoch_m64" : "epoch_m31", kern, (unsigned)(sms * occ), cfg.block, 0, s,
+  // reserve_blocks is counted in 256-thread blocks
+  int grid = sms * occ - reserve_blocks * (kAccThreads / cfg.block);
+  if (grid < 1) grid = 1;
+  WV_LAUNCH(wide ? "epoch_m64" : "epoch_m31", kern, (unsigned)grid, cfg.block, 0, s,
             d_items, n_items, total, d_plans, d_counter);
   return WV_OK;
 }
@@ -453,6 +456,15 @@ wv_status epoch_launch_mixed(const EpochItem *d_items, uint32_t n_items, uint32_
   if (grid < 1) grid = 1;
   WV_LAUNCH("epoch", kern, (unsigned)grid, cfg.block, 0, s, d_items, n_items, total, d_plans,
             d_counter);
+  return WV_OK;
+}
+
+wv_status epoch_launch_tiles(const EpochItem *d_items, uint32_t n_items, uint32_t total,
+                             const Plan *d_plans, const ResidueConfig &cfg, cudaStream_t s) {
+  if (total == 0) return WV_OK;
+  const uint32_t wpb = (uint32_t)(cfg.block / 32);
+  WV_LAUNCH("epoch", epoch_tiles_kernel(cfg.ilp), (total + wpb - 1) / wpb, cfg.block, 0, s, d_items,
+            n_items, total, d_plans);
   return WV_OK;
 }
 

@@ -5,7 +5,9 @@
 //
 // The range is processed in windows: sieve the window on the device, compute
 // both residues for its primes, flag, and compact the flagged primes in
-// ascending order (exclusive scan of the flags, then scatter).
+// ascending order (exclusive scan of the flags, then scatter).  The histogram
+// mode (Sec. 3 "Results", the 2000-bin histogram of <B_{p-3}>_p / p) replaces
+// the flag/compact epilogue by a binning kernel over the same windows.
 #include "wv_internal.h"
 
 namespace wv {
@@ -55,10 +57,42 @@ __global__ void k_copy_u64(const uint64_t *src, uint64_t *dst, size_t n, uint64_
   if (i < n && base + i < cap) dst[base + i] = src[i];
 }
 
+// Bin of <r>_p / p: with u = <r>_p / p + 1/2 = (2<r>_p + p) / (2p) in (0, 1),
+// bin = floor(u bins), i.e. bins [b / bins, (b + 1) / bins) of u.  Per-block
+// counts in shared memory (bins <= kHistShared), then one atomic per bin.
+constexpr uint32_t kHistShared = 8192;
+
+__global__ void k_hist(const uint64_t *primes, const uint64_t *res, size_t n, uint32_t bins,
+                       unsigned long long *hist) {
+  extern __shared__ uint32_t sh[];
+  const bool local = bins <= kHistShared;
+  if (local)
+    for (uint32_t b = threadIdx.x; b < bins; b += blockDim.x) sh[b] = 0;
+  __syncthreads();
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const uint64_t p = primes[i], r = res[i];
+    if (p < 5 || r >= p) continue;  // invalid slots carry WV_RESIDUE_INVALID
+    const uint64_t num = (r > p / 2) ? 2 * r - p : 2 * r + p;  // 2 <r>_p + p, in [1, 2p)
+    const uint32_t b = (uint32_t)(num * bins / (2 * p));
+    if (local) atomicAdd(&sh[b], 1u);
+    else atomicAdd(&hist[b], 1ull);
+  }
+  if (!local) return;
+  __syncthreads();
+  for (uint32_t b = threadIdx.x; b < bins; b += blockDim.x)
+    if (sh[b]) atomicAdd(&hist[b], (unsigned long long)sh[b]);
+}
+
+struct HistOut {
+  uint32_t bins = 0;
+  unsigned long long *b = nullptr, *e = nullptr;
+};
+
 static wv_status search_impl(uint64_t lo, uint64_t hi, uint64_t near, wv_hit *d_hits, size_t cap,
                              size_t *n_hits, uint64_t *d_primes_out, uint64_t *d_rb_out,
                              uint64_t *d_re_out, size_t cap_primes, size_t *n_primes,
-                             const wv_options *opt, cudaStream_t s) {
+                             const wv_options *opt, cudaStream_t s, const HistOut *hist = nullptr) {
   if (!n_hits) return set_error(WV_EINVAL, "n_hits is NULL");
   if (cap && !d_hits) return set_error(WV_EINVAL, "d_hits is NULL with cap > 0");
   if (hi > WV_P_MAX || lo > hi) return set_error(WV_EINVAL, "range [%llu, %llu) invalid",
@@ -88,6 +122,14 @@ static wv_status search_impl(uint64_t lo, uint64_t hi, uint64_t near, wv_hit *d_
       if (np == 0) continue;
       WV_CHECK(residues_device(pr, np, rb, re, cfg, s));
       const unsigned g = (unsigned)((np + 255) / 256);
+      if (hist) {
+        const unsigned hg = g < 1024 ? g : 1024;
+        const size_t shb = hist->bins <= kHistShared ? hist->bins * sizeof(uint32_t) : 0;
+        if (hist->b) WV_LAUNCH("hist", k_hist, hg, 256, shb, s, pr, rb, (size_t)np, hist->bins, hist->b);
+        if (hist->e) WV_LAUNCH("hist", k_hist, hg, 256, shb, s, pr, re, (size_t)np, hist->bins, hist->e);
+        primes_total += np;
+        continue;
+      }
       WV_LAUNCH("search_flag", k_flag, g, 256, 0, s, pr, rb, re, (size_t)np, near, kind, flag);
       WV_CHECK(scan_exclusive_u32(flag, off, np, tot, tmp, s));
       WV_LAUNCH("search_scatter", k_scatter_hits, g, 256, 0, s, pr, kind, off, (size_t)np,
@@ -131,6 +173,23 @@ wv_status wv_search(uint64_t lo, uint64_t hi, wv_hit *d_hits, size_t cap, size_t
   clear_error();
   return search_impl(lo, hi, 0, d_hits, cap, n_hits, nullptr, nullptr, nullptr, 0, nullptr,
                      nullptr, (cudaStream_t)stream);
+}
+
+wv_status wv_histogram(uint64_t lo, uint64_t hi, uint32_t bins, unsigned long long *d_hist_b,
+                       unsigned long long *d_hist_e, size_t *n_primes, wv_stream stream) {
+  clear_error();
+  if (bins < 1 || bins > (1u << 20)) return set_error(WV_EINVAL, "bins=%u not in [1, 2^20]", bins);
+  if (!d_hist_b && !d_hist_e) return set_error(WV_EINVAL, "no histogram output");
+  HistOut h;
+  h.bins = bins;
+  h.b = d_hist_b;
+  h.e = d_hist_e;
+  size_t nh = 0, np = 0;
+  WV_CHECK(search_impl(lo, hi, 0, nullptr, 0, &nh, nullptr, nullptr, nullptr, 0, &np, nullptr,
+                       (cudaStream_t)stream, &h));
+  WV_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  if (n_primes) *n_primes = np;
+  return WV_OK;
 }
 
 wv_status wv_search_ex(uint64_t lo, uint64_t hi, uint64_t near, wv_hit *d_hits, size_t cap,

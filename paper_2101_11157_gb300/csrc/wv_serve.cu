@@ -1,21 +1,23 @@
 // wv_serve.cu -- step a9: a continuous-batching serving loop (see include/wv_serve.h).
 //
-// One worker thread per server owns a CUDA stream and loops:
-//   1. admit pending queries while active slots, plan slots and the device
-//      memory budget allow (a range query is sieved on the device first);
-//      each admitted query gets its prime list, residue buffers and one plan
-//      per <= 65536 primes, all resident;
-//   2. run one epoch: the active queries, ordered by remaining work
-//      (smallest first), contribute ranges of their not-yet-run tiles until
-//      the epoch's term budget is filled; one persistent launch per
-//      arithmetic path runs all of them (k_epoch);
-//   3. finalise every plan whose tiles are all done; a query whose plans are
-//      all finalised is copied to the host, marked done and its device memory
-//      released.
-// Queries arriving meanwhile are admitted at the next iteration, so their
-// tiles share epochs with long-running ones.
+// Two threads per server:
+//   * the admitter takes pending queries in arrival order and, as active
+//     slots, plan slots and the device memory budget allow, gives each its
+//     prime list (a range query is sieved on the device), residue buffers
+//     and one plan per <= 65536 primes, all resident; it works on its own
+//     high-priority stream, beside the running epochs;
+//   * the worker runs epochs: the active queries, ordered by remaining work
+//     (smallest first), contribute ranges of their not-yet-run tiles until
+//     the epoch's term budget is filled, and one persistent launch runs all
+//     of them (both arithmetic paths); two epochs are kept in flight on two
+//     streams.  When an epoch retires, every plan whose tiles have all run is
+//     finalised, and a query whose plans are all finalised is copied to the
+//     host, marked done and its device memory released.
+// A query admitted while others run joins the next epoch, so its tiles share
+// launches with long-running ones.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <deque>
 #include <mutex>
@@ -33,13 +35,15 @@ namespace wv {
 constexpr uint32_t kPlanPrimes = 65536;  // primes per plan
 constexpr uint32_t kMaxPlans = 2048;     // plan slots per server
 constexpr double kWideWeight = 3.0;      // cost of a 64-bit-path term relative to a 32-bit one
-constexpr size_t kAdmitPerIter = 8;      // queries admitted per loop turn (epochs keep running meanwhile)
 constexpr double kMinEpochTerms = 5e9;   // shortest epoch
-// Epoch grids leave this many blocks' room so that admission work (sieve,
-// planner: a few small kernels) runs beside a running epoch instead of after it.
+constexpr size_t kAdmitScan = 4096;      // pending queries looked at per admission decision
+constexpr double kAdmitAge = 5.0;        // seconds pending after which a query goes first
+// Persistent epoch grids leave this many 256-thread blocks' room so that
+// admission work (sieve, planner: small kernels) runs beside a running epoch.
 constexpr int kReserveBlocks = 4;
+constexpr int kEpochBlock = 32;          // default threads per block of an epoch launch
 
-struct SChunk {
+struct SChunk {  // one plan of a query; its tile state is the worker's
   PlanState plan;
   uint32_t off = 0, n = 0;
   uint32_t slot = 0;       // index in the device plan array
@@ -64,6 +68,9 @@ struct SQuery {
   std::vector<uint64_t> h_primes, h_rb, h_re;
   uint64_t n_hits = 0;
   double remaining = 0;
+  bool counted = false;          // bound on n and bytes known (admission)
+  uint64_t n_cap = 0;            // capacity of d_primes (the admission bound)
+  wv_status count_status = WV_OK;
 };
 
 static uint64_t row_terms_host(const WvRow &r, uint64_t p) {
@@ -92,6 +99,18 @@ static void terms_host(const uint64_t *ps, size_t n, const ResidueConfig &cfg, d
   *t64 = b;
 }
 
+// Upper bound on the number of primes in [lo, hi), for admission before the
+// range is sieved: pi(x + y) - pi(x) <= 2y / log y for y > 1 (the
+// Brun-Titchmarsh inequality in the form of Montgomery and Vaughan), and at
+// most the odd numbers of a short range.
+static uint64_t prime_count_bound(uint64_t lo, uint64_t hi) {
+  const uint64_t y = hi > lo ? hi - lo : 0;
+  const uint64_t odd = y / 2 + 2;
+  if (y < 64) return odd;
+  const uint64_t bt = (uint64_t)(2.0 * (double)y / std::log((double)y)) + 2;
+  return bt < odd ? bt : odd;
+}
+
 }  // namespace wv
 
 using namespace wv;
@@ -99,18 +118,19 @@ using namespace wv;
 struct wv_server_s {
   wv_server_config cfg{};
   int device = 0, sms = 0;
-  cudaStream_t st = nullptr;       // admission, finalisation, copies
+  cudaStream_t sa = nullptr;       // admission: sieve, planning (high priority)
+  cudaStream_t st = nullptr;       // finalisation, result copies (high priority)
   cudaStream_t se[2] = {};         // epochs alternate between two streams
   cudaEvent_t ev[2] = {};          // epoch completion
-  std::thread worker;
-  std::mutex mu;
-  std::condition_variable cv_work, cv_done;
-  std::deque<SQuery *> pending;
-  std::vector<SQuery *> active;
+  std::thread worker, admitter;
+  std::mutex mu;                   // guards everything below that both threads touch
+  std::condition_variable cv_work, cv_admit, cv_done;
+  std::deque<SQuery *> pending;    // submitted, not yet admitted (admitter pops)
+  std::vector<SQuery *> active;    // admitted; tile state owned by the worker
   std::unordered_map<uint64_t, SQuery *> queries;
   bool stop = false;
   uint64_t next_id = 1;
-  size_t bytes_in_use = 0;
+  size_t bytes_in_use = 0;         // device bytes reserved by admitted queries
   Plan *d_plans = nullptr;
   std::vector<uint32_t> free_slots;
   EpochItem *d_items = nullptr, *h_items = nullptr;  // two halves, one per epoch stream
@@ -127,96 +147,67 @@ struct wv_server_s {
 
 namespace {
 
-void release_device(wv_server_s *S, SQuery *q) {
+// Free a query's device memory (stream-ordered on s) and return its plan slots.
+void release_device(wv_server_s *S, SQuery *q, cudaStream_t s) {
+  std::vector<uint32_t> slots;
   for (auto &c : q->chunks) {
-    if (c.plan.host) {
-      plan_free(&c.plan, S->st);
-      S->free_slots.push_back(c.slot);
-    }
+    if (c.plan.host) plan_free(&c.plan, s);
+    slots.push_back(c.slot);
   }
   q->chunks.clear();
-  scratch_free(q->d_primes, S->st);
-  scratch_free(q->d_rb, S->st);
-  scratch_free(q->d_re, S->st);
+  scratch_free(q->d_primes, s);
+  scratch_free(q->d_rb, s);
+  scratch_free(q->d_re, s);
   q->d_primes = q->d_rb = q->d_re = nullptr;
+  std::lock_guard<std::mutex> lk(S->mu);
+  for (uint32_t v : slots) S->free_slots.push_back(v);
 }
 
-// Admit one query: sieve / copy its primes, allocate, plan.  Called by the
-// worker without the lock.  Returns false if it must wait (memory or slots).
-bool admit(wv_server_s *S, SQuery *q, size_t bytes_now, size_t free_slots, bool alone) {
-  wv_status st = WV_OK;
-  uint64_t n = 0;
-  if (q->kind == 0) {
-    st = sieve_device(q->lo, q->hi, nullptr, 0, &n, S->st);
-  } else {
-    n = 1;
-  }
-  if (st != WV_OK) {
-    q->state = 3;
-    q->status = st;
-    q->err = wv_last_error();
-    return true;
-  }
-  const size_t nplans = (size_t)((n + kPlanPrimes - 1) / kPlanPrimes);
+// Device bytes a query of n primes holds while active.
+size_t query_bytes(const wv_server_s *S, uint64_t n) {
   size_t need = n * 24;
-  for (size_t i = 0; i < nplans; ++i) {
-    const uint32_t m = (uint32_t)std::min<uint64_t>(kPlanPrimes, n - i * kPlanPrimes);
-    need += plan_bytes(m, S->rcfg);
-  }
-  if (!alone && (bytes_now + need > S->cfg.mem_budget || nplans > free_slots)) return false;
-  if (nplans > free_slots) {  // cannot fit even alone
-    q->state = 3;
-    q->status = WV_ENOMEM;
-    q->err = "query needs more plan slots than the server has";
-    return true;
+  for (uint64_t off = 0; off < n; off += kPlanPrimes)
+    need += plan_bytes((uint32_t)std::min<uint64_t>(kPlanPrimes, n - off), S->rcfg);
+  return need;
+}
+
+// Build an admitted query's device state on the admission stream: its
+// primes (a range is sieved into a buffer sized by the bound used at
+// admission), residue buffers, and one plan per kPlanPrimes primes in the
+// reserved slots.  Sets q->n to the exact count.
+wv_status build_query(wv_server_s *S, SQuery *q, const std::vector<uint32_t> &slots) {
+  const uint64_t cap = q->n;  // the admission bound
+  q->n_cap = cap;
+  WV_CHECK(scratch_alloc((void **)&q->d_primes, cap * 8, S->sa));
+  uint64_t n = cap;
+  if (q->kind == 0) {
+    WV_CHECK(sieve_device(q->lo, q->hi, q->d_primes, cap, &n, S->sa));
+  } else {
+    q->h_primes.assign(1, q->lo);
+    WV_CUDA(cudaMemcpyAsync(q->d_primes, q->h_primes.data(), 8, cudaMemcpyHostToDevice, S->sa));
   }
   q->n = n;
-  q->bytes = need;
-  q->t_admit = S->now();
-  if (n == 0) {
-    q->state = 2;
-    q->t_done = q->t_admit;
-    return true;
-  }
-  auto fail = [&](wv_status s2) {
-    q->state = 3;
-    q->status = s2;
-    q->err = wv_last_error();
-    release_device(S, q);
-    return true;
-  };
-  if ((st = scratch_alloc((void **)&q->d_primes, n * 8, S->st)) != WV_OK) return fail(st);
-  if ((st = scratch_alloc((void **)&q->d_rb, n * 8, S->st)) != WV_OK) return fail(st);
-  if ((st = scratch_alloc((void **)&q->d_re, n * 8, S->st)) != WV_OK) return fail(st);
-  q->h_primes.resize(n);
+  if (n == 0) return WV_OK;
+  WV_CHECK(scratch_alloc((void **)&q->d_rb, n * 8, S->sa));
+  WV_CHECK(scratch_alloc((void **)&q->d_re, n * 8, S->sa));
   if (q->kind == 0) {
-    uint64_t n2 = 0;
-    if ((st = sieve_device(q->lo, q->hi, q->d_primes, n, &n2, S->st)) != WV_OK) return fail(st);
-    if (cudaMemcpyAsync(q->h_primes.data(), q->d_primes, n * 8, cudaMemcpyDeviceToHost, S->st) !=
-        cudaSuccess)
-      return fail(cuda_fail(cudaGetLastError(), "serve: copy primes"));
-  } else {
-    q->h_primes[0] = q->lo;
-    if (cudaMemcpyAsync(q->d_primes, q->h_primes.data(), 8, cudaMemcpyHostToDevice, S->st) !=
-        cudaSuccess)
-      return fail(cuda_fail(cudaGetLastError(), "serve: copy prime"));
+    q->h_primes.resize(n);
+    WV_CUDA(cudaMemcpyAsync(q->h_primes.data(), q->d_primes, n * 8, cudaMemcpyDeviceToHost, S->sa));
   }
-  if (cudaStreamSynchronize(S->st) != cudaSuccess)
-    return fail(cuda_fail(cudaGetLastError(), "serve: admit"));
+  WV_CUDA(cudaStreamSynchronize(S->sa));
   q->remaining = 0;
+  const size_t nplans = (size_t)((n + kPlanPrimes - 1) / kPlanPrimes);
   for (size_t i = 0; i < nplans; ++i) {
     SChunk c;
     c.off = (uint32_t)(i * kPlanPrimes);
     c.n = (uint32_t)std::min<uint64_t>(kPlanPrimes, n - c.off);
-    c.slot = S->free_slots.back();
-    S->free_slots.pop_back();
+    c.slot = slots[i];
     q->chunks.push_back(c);
     SChunk &cc = q->chunks.back();
-    if ((st = plan_build(q->d_primes + cc.off, cc.n, S->rcfg, &cc.plan, S->st)) != WV_OK)
-      return fail(st);
-    if ((st = plan_totals(&cc.plan, S->st)) != WV_OK) return fail(st);
+    WV_CHECK(plan_build(q->d_primes + cc.off, cc.n, S->rcfg, &cc.plan, S->sa));
+    WV_CHECK(plan_totals(&cc.plan, S->sa));
     Plan *dst = (Plan *)((char *)S->d_plans + (size_t)cc.slot * plan_struct_bytes());
-    if ((st = plan_upload(&cc.plan, dst, S->st)) != WV_OK) return fail(st);
+    WV_CHECK(plan_upload(&cc.plan, dst, S->sa));
     cc.hi31 = cc.plan.split;
     cc.hi64 = cc.plan.total;
     double t31 = 0, t64 = 0;
@@ -225,10 +216,130 @@ bool admit(wv_server_s *S, SQuery *q, size_t bytes_now, size_t free_slots, bool 
     cc.tpt64 = (cc.plan.total > cc.plan.split) ? t64 / (cc.plan.total - cc.plan.split) : 1.0;
     q->remaining += t31 + kWideWeight * t64;
   }
-  q->state = 1;
-  return true;
+  WV_CUDA(cudaStreamSynchronize(S->sa));  // plans visible before the worker sees the query
+  return WV_OK;
 }
 
+void fail_query(wv_server_s *S, SQuery *q, wv_status st) {
+  q->state = 3;
+  q->status = st;
+  q->err = wv_last_error();
+  q->t_done = S->now();
+}
+
+// Admission thread.  Among the pending queries (the oldest kAdmitScan), the
+// one needing the least device memory that fits the budget, the active-query
+// limit and the plan slots goes first (shortest job first: a single prime is
+// not held up behind the planning of large ranges); a query pending for more
+// than kAdmitAge seconds goes before any other, and while it does not fit
+// nothing else is admitted, so large queries cannot starve.  A query is
+// always admitted when nothing is active.
+void admitter_main(wv_server_s *S) {
+  cudaSetDevice(S->device);
+  for (;;) {
+    std::vector<SQuery *> cand;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv_admit.wait(lk, [&] { return S->stop || !S->pending.empty(); });
+      if (S->stop) return;
+      const size_t m = std::min(S->pending.size(), kAdmitScan);
+      cand.assign(S->pending.begin(), S->pending.begin() + m);
+    }
+    // device needs from an upper bound on the prime count (no device work)
+    for (SQuery *q : cand) {
+      if (q->counted) continue;
+      const uint64_t n = q->kind == 0 ? prime_count_bound(q->lo, q->hi) : 1;
+      q->count_status = WV_OK;
+      if ((n + kPlanPrimes - 1) / kPlanPrimes > kMaxPlans) {
+        q->count_status = WV_ENOMEM;
+        q->err = "query needs more plan slots than the server has";
+      }
+      q->n = n;
+      q->bytes = query_bytes(S, n);
+      q->counted = true;
+    }
+    SQuery *q = nullptr;
+    std::vector<uint32_t> slots;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      if (S->stop) return;
+      auto fits = [&](const SQuery *c) {
+        const size_t nplans = (size_t)((c->n + kPlanPrimes - 1) / kPlanPrimes);
+        const bool alone = S->active.empty();
+        return (alone || (S->bytes_in_use + c->bytes <= S->cfg.mem_budget &&
+                          S->active.size() < S->cfg.max_active)) &&
+               nplans <= S->free_slots.size();
+      };
+      const double t = S->now();
+      for (SQuery *c : cand)
+        if (c->count_status != WV_OK) {
+          q = c;
+          break;
+        }
+      if (!q && t - cand.front()->t_submit > kAdmitAge) {
+        if (fits(cand.front())) q = cand.front();  // the aged head, or nothing
+      } else if (!q) {
+        for (SQuery *c : cand)
+          if ((!q || c->bytes < q->bytes) && fits(c)) q = c;
+      }
+      if (!q) {
+        // a query finished or arrived; re-check the age of the head now and then
+        S->cv_admit.wait_for(lk, std::chrono::milliseconds(20));
+        continue;
+      }
+      S->pending.erase(std::find(S->pending.begin(), S->pending.end(), q));
+      if (q->count_status != WV_OK) {
+        q->status = q->count_status;
+        q->state = 3;
+        q->t_done = S->now();
+        S->cv_done.notify_all();
+        continue;
+      }
+      q->t_admit = S->now();
+      S->bytes_in_use += q->bytes;
+      const size_t nplans = (size_t)((q->n + kPlanPrimes - 1) / kPlanPrimes);
+      for (size_t i = 0; i < nplans; ++i) {
+        slots.push_back(S->free_slots.back());
+        S->free_slots.pop_back();
+      }
+    }
+    clear_error();
+    wv_status st = build_query(S, q, slots);
+    if (st != WV_OK) {
+      fail_query(S, q, st);
+      const size_t used = q->chunks.size();  // slots of built chunks go back with them
+      release_device(S, q, S->sa);
+      std::lock_guard<std::mutex> lk(S->mu);
+      for (size_t i = used; i < slots.size(); ++i) S->free_slots.push_back(slots[i]);
+      S->bytes_in_use -= std::min(S->bytes_in_use, q->bytes);
+      S->cv_done.notify_all();
+      continue;
+    }
+    // exact needs now that the range is sieved: give back the rest (the
+    // prime buffer keeps its bound-sized allocation)
+    if (q->n == 0) release_device(S, q, S->sa);
+    const size_t exact = q->n ? query_bytes(S, q->n) + (q->n_cap - q->n) * 8 : 0;
+    std::lock_guard<std::mutex> lk(S->mu);
+    for (size_t i = q->chunks.size(); i < slots.size(); ++i) S->free_slots.push_back(slots[i]);
+    if (exact < q->bytes) {
+      S->bytes_in_use -= std::min(S->bytes_in_use, q->bytes - exact);
+      q->bytes = exact;
+      S->cv_admit.notify_all();
+    }
+    if (q->n == 0) {
+      q->state = 2;
+      q->t_done = S->now();
+      S->cv_done.notify_all();
+      continue;
+    }
+    q->state = 1;
+    S->active.push_back(q);
+    S->peak_active = std::max<uint32_t>(S->peak_active, (uint32_t)S->active.size());
+    S->cv_work.notify_one();
+  }
+}
+
+// Copy a finished query's residues to the host and release its device memory.
 void finish_query(wv_server_s *S, SQuery *q) {
   q->h_rb.resize(q->n);
   q->h_re.resize(q->n);
@@ -236,134 +347,136 @@ void finish_query(wv_server_s *S, SQuery *q) {
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(q->h_re.data(), q->d_re, q->n * 8, cudaMemcpyDeviceToHost, S->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(S->st);
-  release_device(S, q);
+  release_device(S, q, S->st);
   if (e != cudaSuccess) {
-    q->state = 3;
-    q->status = cuda_fail(e, "serve: results");
-    q->err = wv_last_error();
-  } else {
-    uint64_t h = 0;
-    for (size_t i = 0; i < q->n; ++i) h += (q->h_rb[i] == 0 || q->h_re[i] == 0) ? 1 : 0;
-    q->n_hits = h;
-    q->state = 2;
+    fail_query(S, q, cuda_fail(e, "serve: results"));
+    return;
   }
+  uint64_t h = 0;
+  for (size_t i = 0; i < q->n; ++i) h += (q->h_rb[i] == 0 || q->h_re[i] == 0) ? 1 : 0;
+  q->n_hits = h;
   q->t_done = S->now();
+  q->state = 2;
 }
 
+// One epoch's launches on stream es (items already copied to d / h).
+wv_status launch_epoch(wv_server_s *S, int b, const std::vector<EpochItem> &items, EpochItem *h,
+                       EpochItem *d, uint32_t tot, cudaStream_t es) {
+  const int form = S->cfg.epoch_form;
+  if (form == 2) return epoch_launch_tiles(d, (uint32_t)items.size(), tot, S->d_plans, S->rcfg, es);
+  if (form == 1)
+    return epoch_launch_mixed(d, (uint32_t)items.size(), tot, S->d_plans, S->d_counter + 2 * b,
+                              S->rcfg, S->sms, kReserveBlocks, es);
+  // form 0: the items of each path as their own list (h is pinned host memory
+  // of 2 kMaxPlans items; the 32-bit items first, then the 64-bit ones)
+  uint32_t n31 = 0, t31 = 0, t64 = 0;
+  for (const EpochItem &it : items)
+    if (!(it.plan >> 31)) {
+      h[n31] = it;
+      h[n31].prefix = t31;
+      t31 += it.count;
+      ++n31;
+    }
+  uint32_t n64 = 0;
+  for (const EpochItem &it : items)
+    if (it.plan >> 31) {
+      EpochItem x = it;
+      x.plan &= 0x7fffffffu;
+      x.prefix = t64;
+      t64 += it.count;
+      h[n31 + n64++] = x;
+    }
+  WV_CUDA(cudaMemcpyAsync(d, h, items.size() * sizeof(EpochItem), cudaMemcpyHostToDevice, es));
+  if (n31)
+    WV_CHECK(epoch_launch(false, d, n31, t31, S->d_plans, S->d_counter + 2 * b, S->rcfg, S->sms,
+                          kReserveBlocks, es));
+  if (n64)
+    WV_CHECK(epoch_launch(true, d + n31, n64, t64, S->d_plans, S->d_counter + 2 * b + 1, S->rcfg,
+                          S->sms, kReserveBlocks, es));
+  return WV_OK;
+}
+
+// Worker thread: epochs, retirement, finalisation.
 void worker_main(wv_server_s *S) {
   cudaSetDevice(S->device);
   int64_t epoch_k = 0, completed = -1;
   std::deque<int64_t> inflight;
   for (;;) {
-    std::vector<SQuery *> cand;
-    size_t bytes_now;
-    bool none_active;
+    std::vector<SQuery *> act;
     {
       std::unique_lock<std::mutex> lk(S->mu);
-      S->cv_work.wait(lk, [&] { return S->stop || !S->pending.empty() || !S->active.empty(); });
+      S->cv_work.wait(lk, [&] { return S->stop || !S->active.empty() || !inflight.empty(); });
       if (S->stop) {
         lk.unlock();
         for (int b = 0; b < 2; ++b) cudaStreamSynchronize(S->se[b]);
         return;
       }
-      while (!S->pending.empty() && S->active.size() + cand.size() < S->cfg.max_active &&
-             cand.size() < kAdmitPerIter) {
-        cand.push_back(S->pending.front());
-        S->pending.pop_front();
-      }
-      bytes_now = S->bytes_in_use;
-      none_active = S->active.empty();
-    }
-    // ---- launch one epoch over the active queries, smallest remaining work first
-    std::vector<SQuery *> act;
-    {
-      std::lock_guard<std::mutex> lk(S->mu);
       act = S->active;
     }
+    clear_error();
+    // ---- launch one epoch (at most two in flight), smallest remaining work first
     std::sort(act.begin(), act.end(),
               [](const SQuery *a, const SQuery *b) { return a->remaining < b->remaining; });
-    // epoch size: short while a small query waits (its latency is at least one
-    // epoch), up to the configured size when only large work remains
-    double budget = S->cfg.epoch_terms;
-    if (!act.empty()) {
-      const double smallest = std::max(act.front()->remaining, 0.0);
-      budget = std::min(budget, std::max(kMinEpochTerms, 2.0 * smallest));
-    }
-    std::vector<EpochItem> items;
-    uint32_t tot = 0;
-    const int64_t k = epoch_k;
-    for (SQuery *q : act) {
-      for (SChunk &c : q->chunks) {
-        if (budget <= 0 || items.size() + 2 > 2 * kMaxPlans) break;
-        if (c.hi31 > 0) {
-          uint32_t kk = (uint32_t)std::min<double>(c.hi31, std::max(1.0, budget / c.tpt31));
-          items.push_back({c.slot, c.hi31 - kk, kk, tot});
-          tot += kk;
-          c.hi31 -= kk;
-          budget -= kk * c.tpt31;
-          q->remaining -= kk * c.tpt31;
-          c.last_epoch = k;
-        }
-        if (budget > 0 && c.hi64 > c.plan.split) {
-          const uint32_t avail = c.hi64 - c.plan.split;
-          uint32_t kk = (uint32_t)std::min<double>(avail, std::max(1.0, budget / (kWideWeight * c.tpt64)));
-          items.push_back({c.slot | 0x80000000u, c.hi64 - kk, kk, tot});
-          tot += kk;
-          c.hi64 -= kk;
-          budget -= kWideWeight * kk * c.tpt64;
-          q->remaining -= kWideWeight * kk * c.tpt64;
-          c.last_epoch = k;
-        }
-      }
-      if (budget <= 0) break;
-    }
     wv_status st = WV_OK;
-    const bool launched = !items.empty();
-    if (launched) {
-      const int b = (int)(k & 1);
-      cudaStream_t es = S->se[b];
-      // this half of the item buffers was used by epoch k-2, which has completed
-      EpochItem *h = S->h_items + (size_t)b * 2 * kMaxPlans;
-      EpochItem *d = S->d_items + (size_t)b * 2 * kMaxPlans;
-      std::copy(items.begin(), items.end(), h);
-      cudaError_t e = cudaMemcpyAsync(d, h, items.size() * sizeof(EpochItem), cudaMemcpyHostToDevice, es);
-      if (e != cudaSuccess) st = cuda_fail(e, "serve: items");
-      if (st == WV_OK)
-        st = epoch_launch_mixed(d, (uint32_t)items.size(), tot, S->d_plans, S->d_counter + 2 * b,
-                                S->rcfg, S->sms, kReserveBlocks, es);
-      if (st == WV_OK && (e = cudaEventRecord(S->ev[b], es)) != cudaSuccess) st = cuda_fail(e, "serve: event");
-      inflight.push_back(k);
-      epoch_k++;
-      S->epochs++;
-      S->tiles += tot;
-    }
-    // ---- admission, in arrival order
-    std::vector<SQuery *> admitted, finished, deferred;
-    for (size_t i = 0; i < cand.size(); ++i) {
-      SQuery *q = cand[i];
-      const bool alone = none_active && admitted.empty();
-      if (!deferred.empty() || !admit(S, q, bytes_now, S->free_slots.size(), alone)) {
-        deferred.push_back(q);
-        continue;
+    bool launched = false;
+    if (inflight.size() < 2) {
+      // epoch size: short while a small query waits (its latency is at least
+      // one epoch), up to the configured size when only large work remains
+      double budget = S->cfg.epoch_terms;
+      for (SQuery *q : act)
+        if (q->remaining > 0) {
+          budget = std::min(budget, std::max(kMinEpochTerms, 2.0 * q->remaining));
+          break;
+        }
+      std::vector<EpochItem> items;
+      uint32_t tot = 0;
+      const int64_t k = epoch_k;
+      for (SQuery *q : act) {
+        for (SChunk &c : q->chunks) {
+          if (budget <= 0 || items.size() + 2 > 2 * kMaxPlans) break;
+          if (c.hi31 > 0) {
+            uint32_t kk = (uint32_t)std::min<double>(c.hi31, std::max(1.0, budget / c.tpt31));
+            items.push_back({c.slot, c.hi31 - kk, kk, tot});
+            tot += kk;
+            c.hi31 -= kk;
+            budget -= kk * c.tpt31;
+            q->remaining -= kk * c.tpt31;
+            c.last_epoch = k;
+          }
+          if (budget > 0 && c.hi64 > c.plan.split) {
+            const uint32_t avail = c.hi64 - c.plan.split;
+            uint32_t kk = (uint32_t)std::min<double>(avail, std::max(1.0, budget / (kWideWeight * c.tpt64)));
+            items.push_back({c.slot | 0x80000000u, c.hi64 - kk, kk, tot});
+            tot += kk;
+            c.hi64 -= kk;
+            budget -= kWideWeight * kk * c.tpt64;
+            q->remaining -= kWideWeight * kk * c.tpt64;
+            c.last_epoch = k;
+          }
+        }
+        if (budget <= 0) break;
       }
-      if (q->state == 1) {
-        admitted.push_back(q);
-        bytes_now += q->bytes;
-      } else {
-        finished.push_back(q);
+      if (!items.empty()) {
+        const int b = (int)(k & 1);
+        cudaStream_t es = S->se[b];
+        // this half of the item buffers was used by epoch k-2, which has retired
+        EpochItem *h = S->h_items + (size_t)b * 2 * kMaxPlans;
+        EpochItem *d = S->d_items + (size_t)b * 2 * kMaxPlans;
+        std::copy(items.begin(), items.end(), h);
+        cudaError_t e = cudaMemcpyAsync(d, h, items.size() * sizeof(EpochItem), cudaMemcpyHostToDevice, es);
+        if (e != cudaSuccess) st = cuda_fail(e, "serve: items");
+        if (st == WV_OK) st = launch_epoch(S, b, items, h, d, tot, es);
+        if (st == WV_OK && (e = cudaEventRecord(S->ev[b], es)) != cudaSuccess)
+          st = cuda_fail(e, "serve: event");
+        inflight.push_back(k);
+        epoch_k++;
+        launched = true;
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->epochs++;
+        S->tiles += tot;
       }
     }
-    {
-      std::lock_guard<std::mutex> lk(S->mu);
-      for (auto it = deferred.rbegin(); it != deferred.rend(); ++it) S->pending.push_front(*it);
-      for (SQuery *q : admitted) {
-        S->active.push_back(q);
-        S->bytes_in_use += q->bytes;
-      }
-      S->peak_active = std::max<uint32_t>(S->peak_active, (uint32_t)S->active.size());
-      if (!finished.empty()) S->cv_done.notify_all();
-    }
-    // ---- retire the oldest epoch once two are in flight (or when nothing new could start)
+    // ---- retire the oldest epoch once two are in flight (or nothing new started)
     if (st == WV_OK && !inflight.empty() && (inflight.size() >= 2 || !launched)) {
       const int64_t done_k = inflight.front();
       inflight.pop_front();
@@ -372,15 +485,12 @@ void worker_main(wv_server_s *S) {
       else completed = done_k;
     }
     // ---- finalise plans whose tiles have all run; finish complete queries
-    finished.clear();
+    std::vector<SQuery *> finished;
     for (SQuery *q : act) {
       if (st != WV_OK) {
-        q->state = 3;
-        q->status = st;
-        q->err = wv_last_error();
         for (int b = 0; b < 2; ++b) cudaStreamSynchronize(S->se[b]);
-        release_device(S, q);
-        q->t_done = S->now();
+        release_device(S, q, S->st);
+        fail_query(S, q, st);
         finished.push_back(q);
         continue;
       }
@@ -405,6 +515,7 @@ void worker_main(wv_server_s *S) {
         S->bytes_in_use -= std::min(S->bytes_in_use, q->bytes);
       }
       S->cv_done.notify_all();
+      S->cv_admit.notify_all();
     }
   }
 }
@@ -431,7 +542,7 @@ wv_status wv_server_create(const wv_server_config *cfg, wv_server *out) {
   *out = nullptr;
   wv_server_s *S = new wv_server_s();
   if (cfg) S->cfg = *cfg;
-  if (S->cfg.mem_budget == 0) S->cfg.mem_budget = (size_t)4 << 30;
+  if (S->cfg.mem_budget == 0) S->cfg.mem_budget = (size_t)16 << 30;
   if (S->cfg.max_active == 0) S->cfg.max_active = 256;
   if (S->cfg.epoch_terms <= 0) S->cfg.epoch_terms = 4e10;
   int dev = S->cfg.device;
@@ -449,10 +560,16 @@ wv_status wv_server_create(const wv_server_config *cfg, wv_server *out) {
   if (st == WV_OK) {
     S->sms = ds->sms;
     WV_CHECK(resolve_config(nullptr, true, true, &S->rcfg));
+    // small epoch blocks (one warp by default): a warp that runs out of tiles
+    // frees its registers at once for the next epoch, not after its block
+    S->rcfg.block = S->cfg.epoch_block > 0 ? S->cfg.epoch_block : kEpochBlock;
+    if (S->rcfg.block % 32 || S->rcfg.block > 256) st = set_error(WV_EINVAL, "epoch_block must be 32..256, a multiple of 32");
+    if (S->cfg.epoch_form < 0 || S->cfg.epoch_form > 2) st = set_error(WV_EINVAL, "epoch_form must be 0, 1 or 2");
     int lo_prio = 0, hi_prio = 0;
     cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
     // admission and finalisation go first whenever SMs free up
     e = cudaStreamCreateWithPriority(&S->st, cudaStreamNonBlocking, hi_prio);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&S->sa, cudaStreamNonBlocking, hi_prio);
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
       e = cudaStreamCreateWithFlags(&S->se[b], cudaStreamNonBlocking);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev[b], cudaEventDisableTiming);
@@ -465,6 +582,7 @@ wv_status wv_server_create(const wv_server_config *cfg, wv_server *out) {
   }
   if (st != WV_OK) {
     if (S->st) cudaStreamDestroy(S->st);
+    if (S->sa) cudaStreamDestroy(S->sa);
     for (int b = 0; b < 2; ++b) {
       if (S->se[b]) cudaStreamDestroy(S->se[b]);
       if (S->ev[b]) cudaEventDestroy(S->ev[b]);
@@ -479,6 +597,7 @@ wv_status wv_server_create(const wv_server_config *cfg, wv_server *out) {
   for (uint32_t i = 0; i < kMaxPlans; ++i) S->free_slots.push_back(kMaxPlans - 1 - i);
   S->t0 = std::chrono::steady_clock::now();
   S->worker = std::thread(worker_main, S);
+  S->admitter = std::thread(admitter_main, S);
   *out = S;
   return WV_OK;
 }
@@ -500,7 +619,7 @@ static wv_status submit(wv_server s, int kind, uint64_t lo, uint64_t hi, uint64_
   s->queries[q->id] = q;
   s->pending.push_back(q);
   *id = q->id;
-  s->cv_work.notify_one();
+  s->cv_admit.notify_all();
   return WV_OK;
 }
 
@@ -600,14 +719,17 @@ wv_status wv_server_destroy(wv_server s) {
     std::lock_guard<std::mutex> lk(s->mu);
     s->stop = true;
     s->cv_work.notify_all();
+    s->cv_admit.notify_all();
   }
   if (s->worker.joinable()) s->worker.join();
+  if (s->admitter.joinable()) s->admitter.join();
   cudaSetDevice(s->device);
   for (int b = 0; b < 2; ++b) cudaStreamSynchronize(s->se[b]);
+  cudaStreamSynchronize(s->sa);
   for (auto &kv : s->queries) {
     SQuery *q = kv.second;
     if (q->state < 2) {
-      release_device(s, q);
+      release_device(s, q, s->st);
       q->state = 4;
     }
   }
@@ -623,6 +745,7 @@ wv_status wv_server_destroy(wv_server s) {
   cudaFreeHost(s->h_items);
   cudaFree(s->d_counter);
   cudaStreamDestroy(s->st);
+  cudaStreamDestroy(s->sa);
   for (int b = 0; b < 2; ++b) {
     cudaStreamDestroy(s->se[b]);
     cudaEventDestroy(s->ev[b]);

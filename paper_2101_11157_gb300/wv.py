@@ -44,7 +44,8 @@ class wv_request(ctypes.Structure):
 class wv_server_config(ctypes.Structure):
     _fields_ = [("mem_budget", ctypes.c_size_t), ("max_active", ctypes.c_uint32),
                 ("epoch_terms", ctypes.c_double), ("device", ctypes.c_int),
-                ("reserved", ctypes.c_int * 7)]
+                ("epoch_form", ctypes.c_int), ("epoch_block", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
 
 
 class wv_query_info(ctypes.Structure):
@@ -76,6 +77,7 @@ _SIGS = {
     "wv_residues_ex": ([_vp, _sz, _vp, _vp, ctypes.POINTER(wv_options), _vp], _i32),
     "wv_residues_pm3_noalloc": ([_vp, _sz, _vp, _vp, _vp], _i32),
     "wv_search": ([_u64, _u64, _vp, _sz, _psz, _vp], _i32),
+    "wv_histogram": ([_u64, _u64, ctypes.c_uint32, _vp, _vp, _psz, _vp], _i32),
     "wv_search_ex": ([_u64, _u64, _u64, _vp, _sz, _psz, _vp, _vp, _vp, _sz, _psz,
                       ctypes.POINTER(wv_options), _vp], _i32),
     "wv_congruence_count": ([], _i32),
@@ -243,6 +245,20 @@ def wv_search_ex(lo: int, hi: int, near: int, d_hits, d_primes=None, d_res_b=Non
     return nh.value, npr.value
 
 
+def wv_histogram(lo: int, hi: int, d_hist_b=None, d_hist_e=None, stream=None) -> int:
+    """Adds the bin counts of <B_{p-3}>_p / p and <E_{p-3}>_p / p for the primes
+    of [lo, hi) to the given int64 device tensors (bins = their length);
+    returns the number of primes."""
+    ts = [t for t in (d_hist_b, d_hist_e) if t is not None]
+    bins = ts[0].numel() if ts else 0
+    if any(t.numel() != bins for t in ts):
+        raise ValueError("histogram tensors differ in length")
+    npr = ctypes.c_size_t(0)
+    _check(load().wv_histogram(lo, hi, bins, _ptr(d_hist_b), _ptr(d_hist_e), ctypes.byref(npr),
+                               _stream(stream)))
+    return npr.value
+
+
 def wv_congruence_count() -> int:
     return load().wv_congruence_count()
 
@@ -374,9 +390,10 @@ def _info(i: wv_query_info) -> dict:
 
 
 def wv_server_create(mem_budget: int = 0, max_active: int = 0, epoch_terms: float = 0.0,
-                     device: int = -1):
+                     device: int = -1, epoch_form: int = 0, epoch_block: int = 0):
     cfg = wv_server_config()
     cfg.mem_budget, cfg.max_active, cfg.epoch_terms, cfg.device = mem_budget, max_active, epoch_terms, device
+    cfg.epoch_form, cfg.epoch_block = epoch_form, epoch_block
     h = ctypes.c_void_p()
     _check(load().wv_server_create(ctypes.byref(cfg), ctypes.byref(h)))
     return h

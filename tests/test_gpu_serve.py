@@ -87,6 +87,27 @@ def test_serving_under_a_tight_memory_budget():
         wv.wv_server_destroy(s)
 
 
+def test_small_query_backfills_past_a_blocked_large_one():
+    # the budget holds one of the two large ranges at a time; the single prime
+    # submitted behind the second one is admitted (and done) before it
+    s = wv.wv_server_create(mem_budget=20 << 20, epoch_terms=2e10)
+    try:
+        a = wv.wv_server_submit_range(s, 2 * 10**9, 2 * 10**9 + 30000)
+        time.sleep(0.05)
+        b = wv.wv_server_submit_range(s, 2 * 10**9 + 30000, 2 * 10**9 + 60000)
+        c = wv.wv_server_submit_prime(s, 1062232319)
+        ia, ib, ic = (wv.wv_server_wait(s, q, 300.0) for q in (a, b, c))
+        assert ic["t_admit"] < ib["t_admit"] and ic["t_done"] < ib["t_admit"]
+        assert ib["t_admit"] >= ia["t_done"] - 1e-3
+        for q, (lo, hi) in ((a, (2 * 10**9, 2 * 10**9 + 30000)), (b, (2 * 10**9 + 30000, 2 * 10**9 + 60000))):
+            pr, rb, re = wv.wv_server_result(s, q)
+            ref = _alone_range(lo, hi)
+            assert np.array_equal(pr, ref[0]) and np.array_equal(rb, ref[1]) and np.array_equal(re, ref[2])
+        assert wv.wv_server_result(s, c)[2][0] == 0
+    finally:
+        wv.wv_server_destroy(s)
+
+
 def test_serving_rejects_bad_queries():
     s = wv.wv_server_create()
     try:
