@@ -43,7 +43,10 @@ ACC_TRAFFIC_BYTES = 1.21984e6 * 4907 / 492
 # c g as three mul.wide and one mul.lo (7), each REDC round one mul.lo and two mul.wide (10).
 TOP_LO, TOP_WIDTH = 10**11 - 10**4, 10**4
 IMAD_SLOTS_PER_MODMUL64 = 17
-ACC64_TRAFFIC_BYTES = None
+# DRAM bytes per launch of the 64-bit accumulation kernel (k_accumulate_m64cap<9,128>), from one ncu
+# capture of the 17-prime head of the window below 1e11 (707,328 B read, 0 written), scaled by primes
+# to the 391-prime launch.  Must be re-taken (or set to None) whenever that kernel changes.
+ACC64_TRAFFIC_BYTES = 707328 * 391 / 17
 
 
 def dist_env():
@@ -375,7 +378,12 @@ def batch_arm(args):
         x, y = wv.wv_count_terms(a)
         tb, te = tb + x, te + y
     stream = torch.cuda.current_stream()
-    b = wv.wv_batch_create(reqs)
+    # launch shape chosen by the autotuner (timed on this batch, outside the timed region)
+    opt, table = None, []
+    if not args.no_autotune:
+        from paper_2101_11157_gb300 import tune
+        opt, table = tune.tune_batch(reqs, key=f"requests{len(reqs_np)}-seed7-max{args.max_len}")
+    b = wv.wv_batch_create(reqs, opt or None)
     _, _, nodes = wv.wv_batch_info(b)
 
     def timed(fn, k):
@@ -406,6 +414,7 @@ def batch_arm(args):
             "speedup_vs_plain": mp / mb, "ms_per_step": mb, "plain_ms_per_step": mp,
             "modmul_per_s": 2 * (tb + te) / (mb / 1e3), "steps": args.steps, "warmup": args.warmup,
             "identical_results": bool(same), "graph_nodes": nodes,
+            "options": opt or {}, "autotune": table,
             "config": {"requests": len(reqs_np), "primes": int(n), "terms": int(tb + te),
                        "lengths": "floor(2^U(0,12)) clamped to [1, %d]" % args.max_len,
                        "primes_from": "next_prime(10^U(5,10)), seed 7"}}
@@ -503,6 +512,7 @@ def main():
     ap.add_argument("--workload", default="window", choices=["window", "top", "batch", "serve"])
     ap.add_argument("--requests", type=int, default=64, help="batch: number of requests")
     ap.add_argument("--max-len", type=int, default=4096, help="batch: longest request")
+    ap.add_argument("--no-autotune", action="store_true", help="batch: library default launch shape")
     ap.add_argument("--queries", type=int, default=256, help="serve: queries in the stream")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrivals per second")
     ap.add_argument("--max-range", type=int, default=0, help="serve: cap on range length (0: none)")

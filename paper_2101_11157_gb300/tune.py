@@ -3,8 +3,9 @@
 Times the accumulation kernels (CUDA events on the launching stream, through
 the library's profiler) for a grid of ``wv_options`` on a given set of primes,
 checks that every shape returns bit-identical residues, and records the
-fastest shape per GPU and p-bucket (floor(log2 p_max)) in a JSON cache.  The
-batch and serving front ends read that cache.
+fastest shape per GPU and p-bucket (floor(log2 p_max)) in a JSON cache.
+``tune_batch`` does the same for a whole batch (the graph-captured launch
+sequence of ``wv_batch_create``) and caches its choice per GPU and workload.
 
     python -m paper_2101_11157_gb300.tune --lo 1062200000 --hi 1062300000 --grid arith
     python -m paper_2101_11157_gb300.tune --lo 1062200000 --hi 1062300000 --grid shape --save
@@ -71,6 +72,62 @@ def sweep(primes, grid, reps: int = 2):
         tpc = (tb + te) / (ms / 1e3) / props.multi_processor_count / clk if ms else 0.0
         yield {"options": opt, "acc_ms": round(ms, 3), "terms_per_clk_sm": round(tpc, 3),
                "identical": same}
+
+
+# launch shapes tried for a batch (one graph-captured launch sequence over many requests)
+BATCH_GRID = [{}, {"block": 32}, {"tile_terms": 1 << 19, "max_tiles": 32},
+              {"block": 32, "tile_terms": 1 << 19, "max_tiles": 32},
+              {"tile_terms": 1 << 21, "max_tiles": 8}, {"ilp": 1}]
+
+
+def tune_batch(reqs, grid=None, reps: int = 1, key: str | None = None, path: str = CACHE):
+    """Choose the launch shape of a batch by timing it.
+
+    reqs: list of (d_primes, d_out_b, d_out_e) device tensors, as for
+    wv.wv_batch_create.  Each option set in `grid` is captured into its own
+    batch, replayed once untimed and `reps` times under CUDA events; every
+    shape must give bit-identical residues.  Returns (best options, table).
+    With `key`, the choice is cached per GPU under that key and reused."""
+    import torch
+    name = torch.cuda.get_device_name()
+    if key:
+        hit = load_cache(path).get(name, {}).get("batch:" + key)
+        if hit is not None:
+            return hit, []
+    grid = BATCH_GRID if grid is None else grid
+    stream = torch.cuda.current_stream()
+    table, ref = [], None
+    for opt in grid:
+        b = wv.wv_batch_create(reqs, opt or None)
+        try:
+            wv.wv_batch_run(b, stream)
+            torch.cuda.synchronize()
+            ms = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                wv.wv_batch_run(b, stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+        finally:
+            wv.wv_batch_destroy(b)
+        out = [(rb.clone(), re.clone()) for _, rb, re in reqs]
+        if ref is None:
+            ref = out
+        same = all(torch.equal(a, c) and torch.equal(b_, d) for (a, b_), (c, d) in zip(out, ref))
+        table.append({"options": opt, "ms": min(ms), "identical": bool(same)})
+    bad = [r for r in table if not r["identical"]]
+    if bad:
+        raise RuntimeError(f"batch shapes disagree: {bad}")
+    best = min(table, key=lambda r: r["ms"])["options"]
+    if key:
+        cache = load_cache(path)
+        cache.setdefault(name, {})["batch:" + key] = best
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        with open(path, "w") as f:
+            json.dump(cache, f, indent=1)
+    return best, table
 
 
 def bucket(p_max: int) -> int:

@@ -70,3 +70,24 @@ def test_batch_seeded_requests():
         torch.cuda.synchronize()
         assert torch.equal(ob, rb) and torch.equal(oe, re)
     wv.wv_batch_destroy(b)
+
+
+def test_autotuner_picks_a_shape_with_identical_results():
+    from paper_2101_11157_gb300 import tune
+    reqs_np = W.batch_requests(seed=7, k=6, max_len=64)
+    reqs = []
+    for a in reqs_np:
+        d = torch.from_numpy(a.view(np.int64)).cuda()
+        reqs.append((d, torch.empty_like(d), torch.empty_like(d)))
+    best, table = tune.tune_batch(reqs, grid=[{}, {"block": 32}, {"ilp": 1}], reps=1)
+    assert len(table) == 3 and all(r["identical"] for r in table)
+    assert best in [r["options"] for r in table]
+    b = wv.wv_batch_create(reqs, best or None)
+    try:
+        wv.wv_batch_run(b)
+        torch.cuda.synchronize()
+    finally:
+        wv.wv_batch_destroy(b)
+    for (d, rb, re), a in zip(reqs, reqs_np):
+        gb, ge = api.residues(d)
+        assert torch.equal(rb, gb) and torch.equal(re, ge)
