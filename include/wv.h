@@ -153,13 +153,15 @@ typedef struct {
                        call with few primes gets more and shorter tiles (up to 64 per
                        sum) so that one launch still holds ~1e5 tiles */
   int blocks_per_sm;/* persistent grid = SMs x this */
-  int arith;        /* hot-loop formulation, 1..22 (default 9: grouped terms, REDC folded
+  int arith;        /* hot-loop formulation, 1..23 (default 9: grouped terms, REDC folded
                        into wide multiply-adds, on both paths).  1..8 select the single-
                        term and intermediate forms of the 32-bit path for ablation, and
                        any value below 9 the single-term 64-bit path; 10..22 select other
                        grouped 64-bit forms (group sizes, shrink interval, instruction
                        choices, register budget; one chain per thread) for ablation,
-                       with formulation 9 on the 32-bit path */
+                       with formulation 9 on the 32-bit path; 23 selects the paper's own
+                       arithmetic on both paths (plain residues, eqn 3.15 split products,
+                       remainders from a double-precision quotient, single terms) */
   int reserved[8];
 } wv_options;
 

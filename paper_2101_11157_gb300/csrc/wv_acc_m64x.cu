@@ -21,6 +21,7 @@ AccKernel acc_kernel_m64x(int arith, int) {
     case 19: return k_accumulate_m64cap<19, 96>;
     case 20: return k_accumulate_m64cap<20, 168>;
     case 21: return k_accumulate_m64cap<21, kM64MaxReg>;
+    case 23: return k_accumulate<true, 1, 23>;  // the paper's arithmetic (ablation)
     default: return k_accumulate_m64cap<22, kM64MaxReg>;
   }
 }

@@ -679,6 +679,87 @@ __device__ __forceinline__ void tile_m64_grouped(const PrimeCtx &ctx, uint64_t s
 // ------------------------------------------------------------------ accumulate
 // One warp tile g of plan P: find its (prime, row) segment, sum its range of
 // terms, merge the lanes, and store the tile's (c0, c1) pair.
+// ---- the paper's own arithmetic, kept as an ablation (arith 23) -------------
+// Sec. 3 ("Method for primes p < 6e10" and its improvements 1-2): plain
+// residues; a product mod p of a = a0 + a1 2^32 and b = b0 + b1 2^32 by
+// eqn 3.15, ab = a0 b0 + a1 b0 2^32 + b1 (a0 2^32 + a1 2^64), each piece a
+// native 64-bit product reduced by a remainder whose quotient comes from a
+// double-precision product with 1/p (exact after at most two corrections
+// each way, as every reduced value is below 2^64 and p >= 2^11); for p < 2^32
+// one native product and one such remainder.  Terms s^e by forward
+// differences (improvement 1), single eqn 3.12 steps.
+__device__ __forceinline__ uint64_t rem_fp64(uint64_t x, uint64_t p, double pinv) {
+  const uint64_t q = (uint64_t)((double)x * pinv);
+  int64_t r = (int64_t)(x - q * p);
+  const int64_t sp = (int64_t)p;
+  if (r < 0) r += sp;
+  if (r < 0) r += sp;
+  if (r >= sp) r -= sp;
+  if (r >= sp) r -= sp;
+  return (uint64_t)r;
+}
+
+__device__ __forceinline__ uint64_t mulmod_split(uint64_t a, uint64_t b, uint64_t p, double pinv,
+                                                 uint64_t r64) {
+  if (p < (1ull << 32)) return rem_fp64(a * b, p, pinv);
+  const uint64_t a0 = a & 0xffffffffull, a1 = a >> 32, b0 = b & 0xffffffffull, b1 = b >> 32;
+  const uint64_t t0 = rem_fp64(a0 * b0, p, pinv);
+  // a1 b0 2^32: a1 b0 < 2^37, reduced, then the shift in two steps of 27 and 5 bits
+  uint64_t t1 = rem_fp64(a1 * b0, p, pinv);
+  t1 = rem_fp64(rem_fp64(t1 << 27, p, pinv) << 5, p, pinv);
+  // b1 (a0 2^32 + a1 2^64): both inside the bracket reduced, 2^64 mod p precomputed
+  const uint64_t u = rem_fp64(a0 << 32, p, pinv) + a1 * r64;
+  const uint64_t t2 = rem_fp64(b1 * u, p, pinv);
+  return rem_fp64(t0 + t1 + t2, p, pinv);
+}
+
+template <bool CUBES>
+__device__ __forceinline__ void tile_paper(const PrimeCtx &ctx, uint64_t start, uint64_t n,
+                                           int64_t &r0, int64_t &r1) {
+  const int lane = threadIdx.x & 31;
+  const Mont M(ctx);
+  const uint64_t p = ctx.p;
+  const double pinv = 1.0 / (double)p;
+  // 2^64 mod p, needed for p >= 2^32 only, where R = 2^64 and ctx.one = R mod p
+  const uint64_t r64 = (ctx.flags & 1u) ? ctx.one : 0;
+  const uint64_t len = n / 32, rem = n - len * 32;
+  const uint64_t s = start + lane * len + (lane < rem ? lane : rem);
+  const uint64_t L = len + (lane < rem ? 1 : 0);
+  // s^e and its forward differences, canonical in [0, p)
+  const uint64_t sq = mulmod_split(s, s, p, pinv, r64);
+  uint64_t t, d1, d2;
+  if (CUBES) {
+    t = mulmod_split(sq, s, p, pinv, r64);
+    d1 = rem_fp64(3 * sq + 3 * s + 1, p, pinv);
+    d2 = rem_fp64(6 * s + 6, p, pinv);
+  } else {
+    t = sq;
+    d1 = rem_fp64(2 * s + 1, p, pinv);
+    d2 = 2;
+  }
+  const uint64_t d3 = CUBES ? 6 : 0;
+  uint64_t c0 = 1, c1 = 0;
+  for (uint64_t i = 0; i < L; ++i) {
+    c1 = mulmod_split(c1, t, p, pinv, r64) + c0;  // eqn 3.12
+    c1 = c1 >= p ? c1 - p : c1;
+    c0 = mulmod_split(c0, t, p, pinv, r64);
+    t += d1;
+    t = t >= p ? t - p : t;
+    d1 += d2;
+    d1 = d1 >= p ? d1 - p : d1;
+    if (CUBES) {
+      d2 += d3;
+      d2 = d2 >= p ? d2 - p : d2;
+    }
+  }
+  // c1 / c0 = S; the merge and the finaliser expect R S: scale c1 by R mod p
+  c1 = mulmod_split(c1, ctx.one, p, pinv, r64);
+  int64_t a0 = (int64_t)c0, a1 = (int64_t)c1;
+  warp_merge(M, a0, a1);
+  r0 = a0;
+  r1 = a1;
+}
+
 template <bool WIDE, int ILP, int AR>
 __device__ __forceinline__ void process_tile(const Plan &P, uint32_t g) {
   const int lane = threadIdx.x & 31;
@@ -700,7 +781,10 @@ __device__ __forceinline__ void process_tile(const Plan &P, uint32_t g) {
   // single-term form used beside the grouped one
   constexpr int AS = (AR == 5 || AR >= 8) ? 4 : AR;
   const bool grp_ok = n >= 32ull * ILP * kGroupMinChain;
-  if (!WIDE && AR == 5 && grp_ok) {
+  if (AR == 23) {
+    if (j < P.rows_b) tile_paper<true>(ctx, start, n, r0, r1);
+    else tile_paper<false>(ctx, start, n, r0, r1);
+  } else if (!WIDE && AR == 5 && grp_ok) {
     if (j < P.rows_b) tile_m31_grouped<ILP, true, 5>(ctx, start, n, r0, r1);
     else tile_m31_grouped<ILP, false, 5>(ctx, start, n, r0, r1);
   } else if (!WIDE && AR >= 7 && grp_ok && j >= P.rows_b) {

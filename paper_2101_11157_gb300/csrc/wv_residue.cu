@@ -212,6 +212,7 @@ static void tile_shape(const ResidueConfig &cfg, size_t n, size_t rows, uint32_t
 }
 
 AccKernel acc_kernel_m31(int ar, int ilp) {
+  if (ar == 23) return k_accumulate<false, 1, 23>;  // the paper's arithmetic (ablation)
 #define WV_PICK(I)                                                            \
   (ar == 1 ? k_accumulate<false, I, 1> : ar == 2 ? k_accumulate<false, I, 2> \
    : ar == 3 ? k_accumulate<false, I, 3> : ar == 4 ? k_accumulate<false, I, 4> \
@@ -232,7 +233,7 @@ static wv_status launch_accumulate(const Plan &P, const ResidueConfig &cfg, int 
     kern = cfg.arith > 9 ? acc_kernel_m64x(cfg.arith, cfg.ilp64)
                          : acc_kernel_m64(cfg.arith == 9 ? 9 : 1, cfg.ilp64);
   } else {
-    kern = acc_kernel_m31(cfg.arith > 9 ? 9 : cfg.arith, cfg.ilp);
+    kern = acc_kernel_m31(cfg.arith == 23 ? 23 : cfg.arith > 9 ? 9 : cfg.arith, cfg.ilp);
   }
   int occ = cfg.blocks_per_sm;
   if (occ <= 0) {

@@ -32,7 +32,9 @@ GRIDS = {
     "shape": [{"ilp": i, "tile_terms": t, "max_tiles": m}
               for i, (t, m) in itertools.product((1, 2), ((1 << 18, 16), (1 << 20, 8), (1 << 22, 4)))],
     # the grouped 64-bit forms (2^30 <= p < 2^37): group sizes and shrink interval
-    "m64": [{"arith": a} for a in (9, *range(12, 23))],
+    "m64": [{"arith": a} for a in (9, *range(12, 24))],
+    # the paper's own arithmetic (eqn 3.15, double-precision quotients) against the default
+    "paper": [{"arith": 9}, {"arith": 23}],
     "block": [{"block": b} for b in (32, 64, 128, 256)],
     "default": [{}],
 }
