@@ -136,6 +136,24 @@ wv_status wv_residues_pm3(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,
 wv_status wv_residues_pm3_noalloc(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,
                                   uint64_t *d_out_e, wv_stream stream);
 
+/*
+ * General index near the top (Sec. 2 and Sec. 4 with t = 2k - 1, resp.
+ * t = p - 1 - 2k, and p - 1 - t small): for every prime p of d_primes,
+ *   d_out_b[i] = B_{p-e_b} mod p   (e_b odd, 3 <= e_b <= 15; 0 skips B),
+ *   d_out_e[i] = E_{p-1-e_e} mod p (e_e even, 2 <= e_e <= 16; 0 skips E),
+ * canonical in [0, p).  Every sum is then S_t = sum s^-e: B by Vandiver's
+ * congruence (eqn 2.5, cost p/10) and E by the three-sum congruence of
+ * eqn 4.2 (cost 3p/16), with their coefficients d^t and left-hand constants
+ * evaluated per prime; the sums by eqn 3.12 with terms s^e from difference
+ * tables of degree e.  e_b = 3, e_e = 2 reproduce wv_residues_pm3.
+ * A slot is WV_RESIDUE_INVALID where p < 11, p < e + 3, p is not a valid
+ * prime, or the left-hand constant vanishes mod p (C_k(2,5,6) for B).
+ * Device arrays of n uint64, caller-owned; asynchronous on `stream`.
+ * Errors: WV_EINVAL for an exponent outside the ranges above.
+ */
+wv_status wv_residues_general(const uint64_t *d_primes, size_t n, uint32_t e_b, uint32_t e_e,
+                              uint64_t *d_out_b, uint64_t *d_out_e, wv_stream stream);
+
 /* Options for the *_ex entry points.  Zero-initialise, then set fields;
  * a zero / negative field means "library default". */
 typedef struct {
@@ -238,6 +256,15 @@ wv_status wv_congruence_info(int id, int *kind, int *n_rows, int64_t *lhs,
 /* Row `row` of congruence `id`: coef * S(xn/xd, yn/yd). */
 wv_status wv_congruence_row(int id, int row, int64_t *coef, uint32_t *xn,
                             uint32_t *xd, uint32_t *yn, uint32_t *yd);
+
+/* The general-index forms used by wv_residues_general (host only):
+ * kind 0 = B (Vandiver, eqn 2.5), kind 1 = E (eqn 4.2).  Row `row` is
+ * (sum_i c[i] d[i]^t) * S_t(xn/xd, yn/yd) with t = p - 1 - e; lhs = (a, b, c)
+ * of C_k(a, b, c) for kind 0 (unused for kind 1).  wv_general_rows(kind)
+ * returns the number of rows (0 for an unknown kind). */
+int wv_general_rows(int kind);
+wv_status wv_general_row(int kind, int row, uint32_t *xn, uint32_t *xd, uint32_t *yn,
+                         uint32_t *yd, int32_t c[3], uint32_t d[3], uint32_t lhs[3]);
 
 /* ---------------------------------------------------------------------- */
 /* profiling: per-kernel CUDA-event timing on the launching stream         */

@@ -238,3 +238,25 @@ def histogram(primes, residues, bins: int = 2000) -> np.ndarray:
         u = Fraction(symmetric(r, p), p) + Fraction(1, 2)
         out[math.floor(u * bins)] += 1
     return out
+
+
+def bernoulli_general(p: int, e: int) -> int:
+    """B_{p-e} mod p for odd e >= 3 and p >= e + 3 (-1 where the congruence's
+    constant vanishes mod p), by the Stafford-Vandiver congruence (Sec. 2,
+    eqn 2.4) in its general form: C_k(3,4,6) B_{2k} = S_{2k-1}(1/6, 1/4) with
+    2k = p - e and C_k(a,b,c) = (a^{p-2k} + b^{p-2k} - c^{p-2k} - 1) / (4k).
+    The sum has exponent 2k - 1 = p - 1 - e, i.e. the inverse powers s^-e."""
+    two_k = p - e
+    c = (pow(3, e, p) + pow(4, e, p) - pow(6, e, p) - 1) * pow(2 * two_k, -1, p) % p
+    if c == 0:
+        return -1
+    return interval_sum(p, Fraction(1, 6), Fraction(1, 4), e) * pow(c, -1, p) % p
+
+
+def euler_general(p: int, e: int) -> int:
+    """E_{p-1-e} mod p for even e >= 2 and p >= e + 3, by Glaisher's congruence
+    (Sec. 4, eqn 4.1, with the sign (-1)^k): (-1)^k 4^{2k-1} E_{p-1-2k} =
+    S_{p-1-2k}(0, 1/4) with 2k = e, the sum of the inverse powers s^-e."""
+    k = e // 2
+    lhs = (-1) ** k * pow(4, 2 * k - 1, p) % p
+    return interval_sum(p, Fraction(0), Fraction(1, 4), e) * pow(lhs, -1, p) % p

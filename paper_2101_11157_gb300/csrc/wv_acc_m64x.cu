@@ -22,6 +22,7 @@ AccKernel acc_kernel_m64x(int arith, int) {
     case 20: return k_accumulate_m64cap<20, 168>;
     case 21: return k_accumulate_m64cap<21, kM64MaxReg>;
     case 23: return k_accumulate<true, 1, 23>;  // the paper's arithmetic (ablation)
+    case 24: return k_accumulate<true, 1, 24>;  // general index (wv_residues_general)
     default: return k_accumulate_m64cap<22, kM64MaxReg>;
   }
 }

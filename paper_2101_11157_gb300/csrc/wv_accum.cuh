@@ -16,7 +16,8 @@
 namespace wv {
 
 constexpr int kAccThreads = 256;
-constexpr int kMaxRowsPP = 66;  // B rows + E rows for one prime (30 + 33 for BB30 + EE33)
+constexpr int kMaxRowsPP = 66;
+constexpr int kMaxGenRows = 6;  // rows of the general-index forms, both kinds  // B rows + E rows for one prime (30 + 33 for BB30 + EE33)
 constexpr uint32_t kChunkPrimes = 16384;  // primes per internal launch sequence
 constexpr uint64_t kGroupMinChain = 48;   // grouped path only for chains of >= 48 terms
 
@@ -38,6 +39,12 @@ struct Plan {
   uint32_t xn[kMaxRowsPP], xd[kMaxRowsPP], yn[kMaxRowsPP], yd[kMaxRowsPP];
   int64_t coef[kMaxRowsPP];
   int64_t lhs_b, lhs_e;
+  // general index (0: the B_{p-3} / E_{p-3} forms): exponents e of the
+  // inverse-power sums, row coefficients sum_i gc_i gd_i^-e, C_k(a,b,c) of B
+  uint32_t gen_e_b, gen_e_e;
+  int32_t gc[kMaxGenRows][3];
+  uint32_t gd[kMaxGenRows][3];
+  uint32_t glhs[3];
 };
 
 // ------------------------------------------------------------------ tiles
@@ -760,6 +767,47 @@ __device__ __forceinline__ void tile_paper(const PrimeCtx &ctx, uint64_t start, 
   r1 = a1;
 }
 
+// ---- general index (arith 24): sums of s^-e for any 2 <= e <= 16 ----------
+// Single eqn 3.12 steps on canonical Montgomery values (the generic Mont
+// arithmetic of either path), terms s^e from a forward-difference table of
+// degree e.
+constexpr int kGenEMax = 16;
+__device__ __forceinline__ void tile_general(const PrimeCtx &ctx, uint64_t start, uint64_t n,
+                                             uint32_t e, int64_t &r0, int64_t &r1) {
+  const int lane = threadIdx.x & 31;
+  const Mont M(ctx);
+  const uint64_t len = n / 32, rem = n - len * 32;
+  const uint64_t s = start + lane * len + (lane < rem ? lane : rem);
+  const uint64_t L = len + (lane < rem ? 1 : 0);
+  int64_t d[kGenEMax + 1];
+#pragma unroll
+  for (int i = 0; i <= kGenEMax; ++i) {
+    d[i] = 0;
+    if ((uint32_t)i <= e) {
+      uint64_t x = s + (uint64_t)i;
+      if (x >= ctx.p) x -= ctx.p;
+      d[i] = M.from_mont(M.pow(M.to_mont((int64_t)x), e));  // x^e mod p, plain
+    }
+  }
+#pragma unroll
+  for (int j = 1; j <= kGenEMax; ++j)
+#pragma unroll
+    for (int i = kGenEMax; i >= j; --i)
+      if ((uint32_t)i <= e) d[i] = M.sub(d[i], d[i - 1]);
+  int64_t c0 = M.one, c1 = 0;
+  for (uint64_t it = 0; it < L; ++it) {
+    const int64_t t = d[0];
+    c1 = M.add(M.mul(c1, t), c0);  // REDC(c1 t) + c0: c1 / c0 grows by R / t
+    c0 = M.mul(c0, t);
+#pragma unroll
+    for (int j = 0; j < kGenEMax; ++j)
+      if ((uint32_t)j < e) d[j] = M.add(d[j], d[j + 1]);
+  }
+  warp_merge(M, c0, c1);
+  r0 = c0;
+  r1 = c1;
+}
+
 template <bool WIDE, int ILP, int AR>
 __device__ __forceinline__ void process_tile(const Plan &P, uint32_t g) {
   const int lane = threadIdx.x & 31;
@@ -781,7 +829,9 @@ __device__ __forceinline__ void process_tile(const Plan &P, uint32_t g) {
   // single-term form used beside the grouped one
   constexpr int AS = (AR == 5 || AR >= 8) ? 4 : AR;
   const bool grp_ok = n >= 32ull * ILP * kGroupMinChain;
-  if (AR == 23) {
+  if (AR == 24) {
+    tile_general(ctx, start, n, j < P.rows_b ? P.gen_e_b : P.gen_e_e, r0, r1);
+  } else if (AR == 23) {
     if (j < P.rows_b) tile_paper<true>(ctx, start, n, r0, r1);
     else tile_paper<false>(ctx, start, n, r0, r1);
   } else if (!WIDE && AR == 5 && grp_ok) {

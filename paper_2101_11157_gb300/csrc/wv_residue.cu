@@ -143,12 +143,17 @@ __global__ void k_finalize(Plan P) {
   uint64_t *out = isB ? P.out_b : P.out_e;
   if (!out) return;
   const PrimeCtx ctx = P.ctx[slot];
+  const uint32_t ge = isB ? P.gen_e_b : P.gen_e_e;  // general index: exponent e, else 0
   if (ctx.flags & 2u) {
-    if (lane == 0) out[ctx.orig] = special_value(ctx.p, isB);
+    if (lane == 0) out[ctx.orig] = ge ? WV_RESIDUE_INVALID : special_value(ctx.p, isB);
     return;
   }
   const Mont M(ctx);
   const int64_t p = (int64_t)ctx.p;
+  if (ge && ctx.p < (uint64_t)ge + 3) {  // the general forms need 2 <= 2k <= p - 3
+    if (lane == 0) out[ctx.orig] = WV_RESIDUE_INVALID;
+    return;
+  }
   const uint32_t nrows = isB ? P.rows_b : P.rows_e;
   const uint32_t r0 = isB ? 0u : P.rows_b;
   const uint32_t seg0 = slot * P.rows_pp + r0;
@@ -161,7 +166,17 @@ __global__ void k_finalize(Plan P) {
       const ulonglong2 v = P.partials[g];
       M.combine(C0, C1, (int64_t)v.x, (int64_t)v.y);
     }
-    const int64_t aM = M.to_mont(smod64(P.coef[r0 + j], p));
+    int64_t aM;
+    if (ge) {  // sum_i c_i d_i^t with t = p - 1 - e
+      aM = 0;
+      for (int i = 0; i < 3; ++i) {
+        if (!P.gc[r0 + j][i]) continue;
+        const int64_t dt = M.pow(M.to_mont((int64_t)P.gd[r0 + j][i]), (uint64_t)(p - 1 - (int64_t)ge));
+        aM = M.add(aM, M.mul(M.to_mont(smod64(P.gc[r0 + j][i], p)), dt));
+      }
+    } else {
+      aM = M.to_mont(smod64(P.coef[r0 + j], p));
+    }
     const int64_t X = M.mul(aM, C1);  // coef * C1 at C1's scale
     N = M.add(M.mul(N, C0), M.mul(X, D));
     D = M.mul(D, C0);
@@ -174,7 +189,24 @@ __global__ void k_finalize(Plan P) {
     D = M.mul(D, D2);
   }
   if (lane == 0) {
-    const int64_t L = smod64(isB ? P.lhs_b : P.lhs_e, p);
+    int64_t L;  // the constant on the left, plain
+    if (ge && isB) {
+      // C_k(a,b,c) = (a^e + b^e - c^e - 1) / (4k) with 4k = 2(p - e) = -2e (mod p):
+      // the numerator stays in L, the denominator moves into N
+      int64_t num = M.sub(0, M.one);
+      for (int i = 0; i < 3; ++i) {
+        const int64_t pw = M.pow(M.to_mont((int64_t)P.glhs[i]), ge);
+        num = (i < 2) ? M.add(num, pw) : M.sub(num, pw);
+      }
+      L = M.from_mont(num);
+      N = M.mul(N, M.to_mont(smod64(-2 * (int64_t)ge, p)));
+    } else if (ge) {
+      // (-1)^k 4^{2k-1} with 2k = e
+      const int64_t f = M.from_mont(M.pow(M.to_mont(4), ge - 1));
+      L = ((ge / 2) & 1) ? (f ? p - f : 0) : f;
+    } else {
+      L = smod64(isB ? P.lhs_b : P.lhs_e, p);
+    }
     if (L == 0 || D == 0) {
       out[ctx.orig] = WV_RESIDUE_INVALID;
       return;
@@ -213,6 +245,7 @@ static void tile_shape(const ResidueConfig &cfg, size_t n, size_t rows, uint32_t
 
 AccKernel acc_kernel_m31(int ar, int ilp) {
   if (ar == 23) return k_accumulate<false, 1, 23>;  // the paper's arithmetic (ablation)
+  if (ar == 24) return k_accumulate<false, 1, 24>;  // general index (wv_residues_general)
 #define WV_PICK(I)                                                            \
   (ar == 1 ? k_accumulate<false, I, 1> : ar == 2 ? k_accumulate<false, I, 2> \
    : ar == 3 ? k_accumulate<false, I, 3> : ar == 4 ? k_accumulate<false, I, 4> \
@@ -233,7 +266,7 @@ static wv_status launch_accumulate(const Plan &P, const ResidueConfig &cfg, int 
     kern = cfg.arith > 9 ? acc_kernel_m64x(cfg.arith, cfg.ilp64)
                          : acc_kernel_m64(cfg.arith == 9 ? 9 : 1, cfg.ilp64);
   } else {
-    kern = acc_kernel_m31(cfg.arith == 23 ? 23 : cfg.arith > 9 ? 9 : cfg.arith, cfg.ilp);
+    kern = acc_kernel_m31(cfg.arith >= 23 ? cfg.arith : cfg.arith > 9 ? 9 : cfg.arith, cfg.ilp);
   }
   int occ = cfg.blocks_per_sm;
   if (occ <= 0) {
@@ -244,6 +277,8 @@ static wv_status launch_accumulate(const Plan &P, const ResidueConfig &cfg, int 
   return WV_OK;
 }
 
+static void fill_rows(Plan &P, const ResidueConfig &cfg);
+
 wv_status residues_device(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,
                           uint64_t *d_out_e, const ResidueConfig &cfg, cudaStream_t s) {
   if (n == 0) return WV_OK;
@@ -252,29 +287,13 @@ wv_status residues_device(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,
   WV_CHECK(device_state(&dev));
   Plan P;
   memset(&P, 0, sizeof P);
-  const bool do_b = cfg.cong_b >= 0 && d_out_b;
-  const bool do_e = cfg.cong_e >= 0 && d_out_e;
+  const bool do_b = (cfg.gen_e_b ? true : cfg.cong_b >= 0) && d_out_b;
+  const bool do_e = (cfg.gen_e_e ? true : cfg.cong_e >= 0) && d_out_e;
   if (!do_b && !do_e) return WV_OK;
-  uint32_t r = 0;
-  if (do_b) {
-    const WvCongruence &c = kWvCongruences[cfg.cong_b];
-    for (int j = 0; j < c.nrows; ++j, ++r) {
-      const WvRow &w = kWvRows[c.row_offset + j];
-      P.xn[r] = w.xn; P.xd[r] = w.xd; P.yn[r] = w.yn; P.yd[r] = w.yd; P.coef[r] = w.coef;
-    }
-    P.rows_b = c.nrows;
-    P.lhs_b = c.lhs;
-  }
-  if (do_e) {
-    const WvCongruence &c = kWvCongruences[cfg.cong_e];
-    for (int j = 0; j < c.nrows; ++j, ++r) {
-      const WvRow &w = kWvRows[c.row_offset + j];
-      P.xn[r] = w.xn; P.xd[r] = w.xd; P.yn[r] = w.yn; P.yd[r] = w.yd; P.coef[r] = w.coef;
-    }
-    P.rows_e = c.nrows;
-    P.lhs_e = c.lhs;
-  }
-  P.rows_pp = r;
+  ResidueConfig c2 = cfg;
+  if (!do_b) c2.cong_b = -2, c2.gen_e_b = 0;
+  if (!do_e) c2.cong_e = -2, c2.gen_e_e = 0;
+  fill_rows(P, c2);
 
   const size_t cap = cfg.chunk > 0 ? (size_t)cfg.chunk : kChunkPrimes;
   const uint32_t chunk = (uint32_t)(n < cap ? n : cap);
@@ -329,7 +348,23 @@ wv_status residues_device(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,
 
 static void fill_rows(Plan &P, const ResidueConfig &cfg) {
   uint32_t r = 0;
-  if (cfg.cong_b >= 0) {
+  // a general-index form: its rows with their coefficient descriptors
+  auto general = [&](const WvGenCongruence &c) {
+    for (int j = 0; j < c.nrows; ++j, ++r) {
+      const WvGenRow &w = c.rows[j];
+      P.xn[r] = w.xn; P.xd[r] = w.xd; P.yn[r] = w.yn; P.yd[r] = w.yd; P.coef[r] = 0;
+      for (int i = 0; i < 3; ++i) {
+        P.gc[r][i] = w.c[i];
+        P.gd[r][i] = w.d[i];
+      }
+    }
+    return (uint32_t)c.nrows;
+  };
+  if (cfg.gen_e_b) {
+    P.rows_b = general(kWvGeneral[0]);
+    P.gen_e_b = cfg.gen_e_b;
+    for (int i = 0; i < 3; ++i) P.glhs[i] = kWvGeneral[0].lhs[i];
+  } else if (cfg.cong_b >= 0) {
     const WvCongruence &c = kWvCongruences[cfg.cong_b];
     for (int j = 0; j < c.nrows; ++j, ++r) {
       const WvRow &w = kWvRows[c.row_offset + j];
@@ -338,7 +373,10 @@ static void fill_rows(Plan &P, const ResidueConfig &cfg) {
     P.rows_b = c.nrows;
     P.lhs_b = c.lhs;
   }
-  if (cfg.cong_e >= 0) {
+  if (cfg.gen_e_e) {
+    P.rows_e = general(kWvGeneral[1]);
+    P.gen_e_e = cfg.gen_e_e;
+  } else if (cfg.cong_e >= 0) {
     const WvCongruence &c = kWvCongruences[cfg.cong_e];
     for (int j = 0; j < c.nrows; ++j, ++r) {
       const WvRow &w = kWvRows[c.row_offset + j];
@@ -352,8 +390,10 @@ static void fill_rows(Plan &P, const ResidueConfig &cfg) {
 
 static size_t rows_of(const ResidueConfig &cfg) {
   size_t r = 0;
-  if (cfg.cong_b >= 0) r += kWvCongruences[cfg.cong_b].nrows;
-  if (cfg.cong_e >= 0) r += kWvCongruences[cfg.cong_e].nrows;
+  if (cfg.gen_e_b) r += kWvGeneral[0].nrows;
+  else if (cfg.cong_b >= 0) r += kWvCongruences[cfg.cong_b].nrows;
+  if (cfg.gen_e_e) r += kWvGeneral[1].nrows;
+  else if (cfg.cong_e >= 0) r += kWvCongruences[cfg.cong_e].nrows;
   return r;
 }
 
@@ -645,6 +685,24 @@ wv_status wv_residues_pm3_noalloc(const uint64_t *d_primes, size_t n, uint64_t *
                                   uint64_t *d_out_e, wv_stream stream) {
   clear_error();
   return residues_noalloc(d_primes, n, d_out_b, d_out_e, (cudaStream_t)stream);
+}
+
+wv_status wv_residues_general(const uint64_t *d_primes, size_t n, uint32_t e_b, uint32_t e_e,
+                              uint64_t *d_out_b, uint64_t *d_out_e, wv_stream stream) {
+  clear_error();
+  if (e_b && (e_b < 3 || e_b > kWvGeneralMaxE || !(e_b & 1)))
+    return set_error(WV_EINVAL, "e_b=%u must be odd, 3 <= e_b <= %u (or 0)", e_b, kWvGeneralMaxE);
+  if (e_e && (e_e < 2 || e_e > kWvGeneralMaxE || (e_e & 1)))
+    return set_error(WV_EINVAL, "e_e=%u must be even, 2 <= e_e <= %u (or 0)", e_e, kWvGeneralMaxE);
+  if (n && !d_primes) return set_error(WV_EINVAL, "d_primes is NULL");
+  ResidueConfig cfg;
+  WV_CHECK(resolve_config(nullptr, true, true, &cfg));
+  cfg.arith = 24;
+  cfg.ilp = cfg.ilp64 = 1;
+  cfg.gen_e_b = e_b;
+  cfg.gen_e_e = e_e;
+  return residues_device(d_primes, n, e_b ? d_out_b : nullptr, e_e ? d_out_e : nullptr, cfg,
+                         (cudaStream_t)stream);
 }
 
 wv_status wv_euler_pm3(const uint64_t *d_primes, size_t n, uint64_t *d_out, wv_stream stream) {

@@ -343,6 +343,26 @@ wv_status wv_congruence_row(int id, int row, int64_t *coef, uint32_t *xn, uint32
   return WV_OK;
 }
 
+wv_status wv_general_row(int kind, int row, uint32_t *xn, uint32_t *xd, uint32_t *yn, uint32_t *yd,
+                         int32_t c[3], uint32_t d[3], uint32_t lhs[3]) {
+  if (kind < 0 || kind > 1) return set_error(WV_EINVAL, "kind %d", kind);
+  const WvGenCongruence &g = kWvGeneral[kind];
+  if (row < 0 || row >= g.nrows) return set_error(WV_EINVAL, "row %d of %s", row, g.name);
+  const WvGenRow &r = g.rows[row];
+  if (xn) *xn = r.xn;
+  if (xd) *xd = r.xd;
+  if (yn) *yn = r.yn;
+  if (yd) *yd = r.yd;
+  for (int i = 0; i < 3; ++i) {
+    if (c) c[i] = r.c[i];
+    if (d) d[i] = r.d[i];
+    if (lhs) lhs[i] = g.lhs[i];
+  }
+  return WV_OK;
+}
+
+int wv_general_rows(int kind) { return (kind == 0 || kind == 1) ? kWvGeneral[kind].nrows : 0; }
+
 static uint64_t row_terms(const WvRow &r, uint64_t p) {
   // s runs over floor(xn p/xd)+1 .. floor(yn p/yd) (no endpoint is an integer, p >= 7)
   uint64_t lo = (uint64_t)r.xn * p / r.xd + 1;

@@ -77,6 +77,11 @@ _SIGS = {
     "wv_residues_ex": ([_vp, _sz, _vp, _vp, ctypes.POINTER(wv_options), _vp], _i32),
     "wv_residues_pm3_noalloc": ([_vp, _sz, _vp, _vp, _vp], _i32),
     "wv_search": ([_u64, _u64, _vp, _sz, _psz, _vp], _i32),
+    "wv_residues_general": ([_vp, _sz, ctypes.c_uint32, ctypes.c_uint32, _vp, _vp, _vp], _i32),
+    "wv_general_rows": ([_i32], _i32),
+    "wv_general_row": ([_i32, _i32] + [ctypes.POINTER(ctypes.c_uint32)] * 4 +
+                       [ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_uint32),
+                        ctypes.POINTER(ctypes.c_uint32)], _i32),
     "wv_histogram": ([_u64, _u64, ctypes.c_uint32, _vp, _vp, _psz, _vp], _i32),
     "wv_search_ex": ([_u64, _u64, _u64, _vp, _sz, _psz, _vp, _vp, _vp, _sz, _psz,
                       ctypes.POINTER(wv_options), _vp], _i32),
@@ -243,6 +248,25 @@ def wv_search_ex(lo: int, hi: int, near: int, d_hits, d_primes=None, d_res_b=Non
                              ctypes.byref(npr), _options(options), _stream(stream))
     _check(st, nh.value)
     return nh.value, npr.value
+
+
+def wv_residues_general(d_primes, e_b: int, e_e: int, d_out_b=None, d_out_e=None, stream=None):
+    """B_{p-e_b} mod p and E_{p-1-e_e} mod p (an exponent 0 skips its kind)."""
+    n = d_primes.numel()
+    _check(load().wv_residues_general(_ptr(d_primes), n, e_b, e_e, _ptr(d_out_b), _ptr(d_out_e),
+                                      _stream(stream)))
+
+
+def wv_general_rows(kind: int) -> int:
+    return load().wv_general_rows(kind)
+
+
+def wv_general_row(kind: int, row: int):
+    """((xn, xd, yn, yd), [(c_i, d_i)...], lhs (a, b, c)) of a general-index row."""
+    v = [ctypes.c_uint32() for _ in range(4)]
+    c, d, l = (ctypes.c_int32 * 3)(), (ctypes.c_uint32 * 3)(), (ctypes.c_uint32 * 3)()
+    _check(load().wv_general_row(kind, row, *[ctypes.byref(x) for x in v], c, d, l))
+    return tuple(x.value for x in v), [(c[i], d[i]) for i in range(3) if c[i]], tuple(l)
 
 
 def wv_histogram(lo: int, hi: int, d_hist_b=None, d_hist_e=None, stream=None) -> int:
