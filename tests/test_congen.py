@@ -1,0 +1,73 @@
+"""The congruence generator (Prop. 2.1): derivations, searches, validity.
+
+* The paper's derivation sequences (Sec. 2 for B2 ... B30 from Vandiver's
+  congruence, Sec. 4 for E3 ... E24 from eqn 4.1) reproduce every one of the
+  library's transcribed tables exactly, at the costs the paper states.
+* The exhaustive search reproduces the paper's table of least costs r_m for
+  m = 2 ... 8 (Sec. 2, "Exhaustive searches").
+* Every generated congruence holds: evaluated with Python integers at
+  several k and p it equals the left side computed from the definitions.
+"""
+from fractions import Fraction as F
+
+import pytest
+
+from paper_2101_11157_gb300 import congen as C
+from paper_2101_11157_gb300 import workloads as W
+
+PAPER_COSTS = {"BB2": F(1, 15), "BB6": F(5, 96), "BB9": F(1, 20), "BB16": F(1, 24),
+               "BB22": F(3, 80), "BB30": F(227, 6480), "EE3": F(3, 16), "EE5": F(9, 64),
+               "EE9": F(43, 384), "EE16": F(205, 2304), "EE24": F(115, 1536)}
+
+
+@pytest.mark.parametrize("name", sorted(C.DERIVATIONS))
+def test_derivation_reproduces_library_table(name):
+    cg = C.derive(name)
+    lhs, rows = C.library_table(name)
+    assert C.matches_table(cg, lhs, rows)
+    assert cg.cost == PAPER_COSTS[name]
+    assert cg.m == int(name[2:])
+
+
+def test_exhaustive_search_reproduces_least_costs():
+    best = C.exhaustive(C.vandiver(), [2] * 7)
+    r = {m: 1 / best[m].cost for m in range(2, 9)}
+    assert r == {2: 15, 3: 15, 4: F(120, 7), 5: F(240, 13), 6: F(96, 5), 7: F(960, 49),
+                 8: F(1920, 97)}
+
+
+def _lhs_b(p, k, orc):
+    # C_k(2,5,6) B_{2k} with C_k(a,b,c) = (a^{p-2k} + b^{p-2k} - c^{p-2k} - 1) / (4k)
+    e = p - 2 * k
+    c = (pow(2, e, p) + pow(5, e, p) - pow(6, e, p) - 1) * pow(4 * k, -1, p) % p
+    return c * orc.bernoulli_def(2 * k, p) % p
+
+
+def _lhs_e(p, k, orc):
+    # (-1)^k 4^{2k-1} E_{p-1-2k}
+    return (-1) ** k * pow(4, 2 * k - 1, p) * orc.euler_def(p - 1 - 2 * k, p) % p
+
+
+def test_generated_congruences_hold_at_general_k(orc):
+    greedy = C.greedy(C.derive("BB2"), 6, D=6)
+    forms = [C.derive("BB9"), C.derive("BB30"), greedy[-1]]
+    primes = [p for p in range(11, 90) if W.is_prime(p)]
+    for cg in forms:
+        for p in primes:
+            for k in range(1, (p - 3) // 2 + 1):  # 2 <= 2k <= p - 3, so p - 1 does not divide 2k
+                assert C.evaluate(cg, p, 2 * k - 1) == _lhs_b(p, k, orc), (cg, p, k)
+    for cg in (C.derive("EE9"), C.derive("EE24")):
+        for p in primes:
+            for k in range(1, (p - 3) // 2 + 1):
+                assert C.evaluate(cg, p, p - 1 - 2 * k) == _lhs_e(p, k, orc), (cg, p, k)
+
+
+def test_greedy_cost_never_increases():
+    costs = [cg.cost for cg in C.greedy(C.vandiver(), 8, D=8)]
+    assert all(b <= a for a, b in zip(costs, costs[1:]))
+    assert costs[-1] < F(1, 20)
+
+
+def test_subdivision_of_a_missing_interval_is_rejected():
+    with pytest.raises(ValueError):
+        C.subdivide(C.vandiver(), F(1, 4), F(1, 3), 2)
