@@ -3,7 +3,8 @@
 [1062200000, 1062300000) near 1e9 (4907 primes, all < 2^30).
 
 One step = the whole path over the window: segmented sieve on the device,
-planning, the persistent accumulation of BB30 (eqn 3.7) and EE33 (eqn 5.6),
+planning, the persistent accumulation of the library's default congruences
+for B_{p-3} and E_{p-3} (generated from BB30, eqn 3.7, and EE33, eqn 5.6),
 per-prime finalisation, and flag/compaction of the zero residues
 (wv_search_ex).  The headline value is primes/s (each prime gets both
 residues); modmul/s counts two modular multiplications per summed term
@@ -34,19 +35,19 @@ WIDTH = HI - LO
 IMAD_PER_SM_CLK = 64          # 32-bit integer multiply-add results per SM per clock
 IMAD_SLOTS_PER_MODMUL = 5     # one 32-bit Montgomery product: mul.wide (2) + mul.lo (1) + mul.hi (2)
 SM_MAX_MHZ_FALLBACK = 2070.0
-# DRAM bytes per launch of the p < 2^30 accumulation kernel (k_accumulate<0,2,9>), from one ncu
-# capture of the 492-prime head of the window (1.21984 MB read, 0 written), scaled by primes to the
-# 4907-prime launch.  Must be re-taken (or set to None) whenever that kernel changes.
-ACC_TRAFFIC_BYTES = 1.21984e6 * 4907 / 492
+# DRAM bytes per launch of the p < 2^30 accumulation kernel (k_accumulate<0,2,9>, default congruences
+# BB249 + EE404), from one ncu capture of the 492-prime head of the window (9,297,152 B read, 0 written),
+# scaled by primes to the 4907-prime launch.  Must be re-taken (or set to None) whenever that kernel changes.
+ACC_TRAFFIC_BYTES = 9297152 * 4907 / 492
 # --workload top: the 391 primes of [1e11 - 1e4, 1e11) on the 64-bit path.  One 64-bit
 # Montgomery product for p < 2^37 (R = 2^64 in two 32-bit REDC rounds) costs 17 IMAD slots:
 # c g as three mul.wide and one mul.lo (7), each REDC round one mul.lo and two mul.wide (10).
 TOP_LO, TOP_WIDTH = 10**11 - 10**4, 10**4
 IMAD_SLOTS_PER_MODMUL64 = 17
 # DRAM bytes per launch of the 64-bit accumulation kernel (k_accumulate_m64cap<9,128>), from one ncu
-# capture of the 17-prime head of the window below 1e11 (707,328 B read, 0 written), scaled by primes
+# capture of the 17-prime head of the window below 1e11 (1,231,104 B read, 0 written), scaled by primes
 # to the 391-prime launch.  Must be re-taken (or set to None) whenever that kernel changes.
-ACC64_TRAFFIC_BYTES = 707328 * 391 / 17
+ACC64_TRAFFIC_BYTES = 1231104 * 391 / 17
 
 
 def dist_env():
@@ -309,15 +310,16 @@ def gpu_arm(args):
     achieved_gmodmul = (modmuls_per_step / (acc_avg_ms / 1000.0)) / 1e9 if acc_avg_ms else 0.0
     total_primes = n_primes * ws
     value = total_primes / (ms / 1000.0)
+    cong_names = [wv.wv_congruence_info(wv.wv_congruence_default(k))[0] for k in (0, 1)]
     line = {
         "metric": METRIC, "value": value, "unit": "primes/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic: every prime of the window, sieved on the device (no dataset)",
-        "config": {"workload": f"sieve + B_{{p-3}} (BB30, eqn 3.7) + E_{{p-3}} (EE33, eqn 5.6) mod p "
+        "config": {"workload": f"sieve + B_{{p-3}} ({cong_names[0]}) + E_{{p-3}} ({cong_names[1]}) mod p "
                                f"+ zero/near flags for all primes in [{lo}, {hi}) per GPU"
                                + (" (64-bit path, 2^30 <= p < 2^37)" if top else ""),
-                   "primes_per_gpu": int(n_primes), "congruences": "BB30+EE33",
+                   "primes_per_gpu": int(n_primes), "congruences": "+".join(cong_names),
                    "terms_per_step": int(tb + te), "parallelism": f"range-sharded x{ws}",
                    "l2": "flushed between steps (256 MB write)"},
         "modmul_per_s": modmuls_per_step * ws / (ms / 1000.0),

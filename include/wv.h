@@ -84,8 +84,10 @@ wv_status wv_sieve_count(uint64_t lo, uint64_t hi, uint64_t *count, wv_stream st
 
 /*
  * d_out[i] = B_{p_i - 3} mod p_i for the n primes d_primes[0..n).
- * Follows Sec. 3: B_{p-3} from eqn 3.7 (BB30) for p >= 11, each sum
- * S_{p-4}(x,y) = sum_{xp<s<yp} s^-3 evaluated as c1/c0 of
+ * Follows Sec. 3: B_{p-3} from a congruence of the form of eqn 3.7 for
+ * p >= 11 -- by default BB249, 249 sums of cost p/38.2 generated from BB30
+ * (eqn 3.7) by the greedy search over Prop. 2.1 (wv_congruence_default) --
+ * each sum S_{p-4}(x,y) = sum_{xp<s<yp} s^-3 evaluated as c1/c0 of
  * prod (z + s^3) (the polynomial trick and eqn 3.12), partial products
  * combined with eqn 3.14, one modular inverse per prime; p = 5, 7 from the
  * definition.  d_primes and d_out: device arrays of n uint64 (may alias
@@ -95,8 +97,9 @@ wv_status wv_bernoulli_pm3(const uint64_t *d_primes, size_t n, uint64_t *d_out,
                            wv_stream stream);
 
 /*
- * d_out[i] = E_{p_i - 3} mod p_i (sec convention).  Follows Sec. 5: eqn 5.6
- * (EE33) for p >= 11 with S_{p-3}(x,y) = sum s^-2 evaluated through
+ * d_out[i] = E_{p_i - 3} mod p_i (sec convention).  Follows Sec. 5: a
+ * congruence of the form of eqn 5.6 for p >= 11 -- by default EE404, 404 sums
+ * of cost p/29.8 generated from EE33 (eqn 5.6) -- with S_{p-3}(x,y) = sum s^-2 evaluated through
  * prod (z + s^2) (the remark after eqn 5.6).  Same layout and behaviour as
  * wv_bernoulli_pm3.  Asynchronous.
  */
@@ -120,7 +123,7 @@ wv_status wv_residues_pm3(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,
  *
  * It computes exactly what wv_residues_pm3 computes (default congruences and
  * launch shape) but allocates nothing: all scratch lives in one fixed device
- * array inside the library, about 10 MB, that every GPU which loads the
+ * array inside the library, about 12 MB, that every GPU which loads the
  * library keeps until the process exits.  Limits and behaviour:
  *  - n <= 1024 primes per call; larger n returns WV_ERANGE (split the list).
  *  - The first call on each device looks up the array's device address
@@ -157,8 +160,8 @@ wv_status wv_residues_general(const uint64_t *d_primes, size_t n, uint32_t e_b, 
 /* Options for the *_ex entry points.  Zero-initialise, then set fields;
  * a zero / negative field means "library default". */
 typedef struct {
-  int cong_b;       /* congruence id (wv_congruence_info) for B; <0: default BB30 */
-  int cong_e;       /* congruence id for E; <0: default EE33 */
+  int cong_b;       /* congruence id (wv_congruence_info) for B; <0: default (BB249) */
+  int cong_e;       /* congruence id for E; <0: default (EE404) */
   int block;        /* accumulation block size (threads): 32..256, multiple of 32;
                        default 256.  Smaller blocks release their registers warp by
                        warp at the end of a launch and round occupancy differently */
@@ -245,17 +248,32 @@ wv_status wv_histogram(uint64_t lo, uint64_t hi, uint32_t bins, unsigned long lo
 /* host-side inspection of the congruence tables (no GPU needed)           */
 /* ---------------------------------------------------------------------- */
 
-/* Number of congruences in the library (BB1..BB30, EE3..EE33). */
+/* Number of congruences in the library: ids 0..12 are the paper's (BB1..BB30,
+ * EE3..EE33, Sec. 3 and Sec. 5); the ids after them were generated from
+ * BB30 and EE33 by the greedy search over Prop. 2.1 (Sec. 2, "Heuristic
+ * searches"), named by their number of sums (BB249 ... EE967). */
 int wv_congruence_count(void);
+
+/* The id of the congruence the residue and search calls use by default for
+ * kind 0 (B_{p-3}) or 1 (E_{p-3}): the generated BB249 and EE404. */
+int wv_congruence_default(int kind);
 
 /* Congruence `id`: kind 0 = B_{p-3}, 1 = E_{p-3}; n_rows sums; lhs = the
  * constant on the left; name (static string).  Any out-pointer may be NULL. */
 wv_status wv_congruence_info(int id, int *kind, int *n_rows, int64_t *lhs,
                              const char **name);
 
-/* Row `row` of congruence `id`: coef * S(xn/xd, yn/yd). */
+/* Row `row` of congruence `id`: coef * S(xn/xd, yn/yd) for a row whose
+ * coefficient is a plain integer (every row of ids 0..12).  A row with a
+ * coefficient sum_k c_k d_k^t returns WV_ERANGE with *coef = 0 (the interval
+ * is still written): read it with wv_congruence_terms. */
 wv_status wv_congruence_row(int id, int row, int64_t *coef, uint32_t *xn,
                             uint32_t *xd, uint32_t *yn, uint32_t *yd);
+
+/* The coefficient of row `row` of congruence `id` as terms c[k] d[k]^t
+ * (t = p - 4 for B_{p-3}, p - 3 for E_{p-3}, so d^t = d^-3 resp. d^-2):
+ * writes up to `cap` terms, *n = their number; WV_ERANGE if n > cap. */
+wv_status wv_congruence_terms(int id, int row, int64_t *c, uint64_t *d, int cap, int *n);
 
 /* The general-index forms used by wv_residues_general (host only):
  * kind 0 = B (Vandiver, eqn 2.5), kind 1 = E (eqn 4.2).  Row `row` is

@@ -80,37 +80,40 @@ def _add(a: dict, b: dict, scale: int = 1) -> dict:
     return out
 
 
-def simplify(kind: str, raw) -> list:
-    """Reflect into [0, 1/2], sum on the common refinement, merge equal neighbours."""
+def _reflect_into_half(kind: str, raw):
     sign = -1 if kind == "B" else 1
-    parts = []
+    out = []
     for x, y, c in raw:
-        if x < HALF < y:  # separation at 1/2 (p/2 is never an integer)
-            parts += [(x, HALF, c), (HALF, y, c)]
-        else:
-            parts.append((x, y, c))
-    moved = []
-    for x, y, c in parts:
-        if x >= HALF:
-            moved.append((1 - y, 1 - x, {d: sign * v for d, v in c.items()}))
-        else:
-            moved.append((x, y, c))
-    cuts = sorted({v for x, y, _ in moved for v in (x, y)})
-    pieces = []
+        parts = [(x, HALF), (HALF, y)] if x < HALF < y else [(x, y)]  # separation at 1/2
+        for a, b in parts:
+            if a >= HALF:
+                out.append((1 - b, 1 - a, {d: sign * v for d, v in c.items()}))
+            else:
+                out.append((a, b, c))
+    return out
+
+
+def simplify(kind: str, raw) -> list:
+    """Reflect into [0, 1/2], sum on the common refinement, merge equal neighbours.
+
+    A sweep over the endpoints keeps the running coefficient of the covering
+    sums, so the cost is O(n log n) dictionary updates."""
+    moved = _reflect_into_half(kind, raw)
+    events = {}
+    for x, y, c in moved:
+        events.setdefault(x, []).append((1, c))
+        events.setdefault(y, []).append((-1, c))
+    cuts = sorted(events)
+    cur, pieces = {}, []
     for a, b in zip(cuts, cuts[1:]):
-        coef = {}
-        for x, y, c in moved:
-            if x <= a and b <= y:
-                coef = _add(coef, c)
-        if coef:
-            pieces.append([a, b, coef])
-    merged = []
-    for a, b, c in pieces:
-        if merged and merged[-1][1] == a and merged[-1][2] == c:
-            merged[-1][1] = b
-        else:
-            merged.append([a, b, c])
-    return [(a, b, c) for a, b, c in merged]
+        for sgn, c in events[a]:
+            cur = _add(cur, c, sgn)
+        if cur:
+            if pieces and pieces[-1][1] == a and pieces[-1][2] == cur:
+                pieces[-1][1] = b
+            else:
+                pieces.append([a, b, dict(cur)])
+    return [(a, b, c) for a, b, c in pieces]
 
 
 def subdivide(cg: Congruence, x: F, y: F, d: int) -> Congruence:
@@ -263,6 +266,72 @@ def exhaustive(start: Congruence, ds) -> dict:
     return best
 
 
+def _coef_at(sums, starts, v):
+    import bisect
+    i = bisect.bisect_right(starts, v) - 1
+    if i >= 0 and sums[i][0] <= v < sums[i][1]:
+        return sums[i][2]
+    return {}
+
+
+def cost_delta(cg: Congruence, j: int, d: int, starts=None) -> F:
+    """The change of cost when sum j of cg is subdivided with d, without
+    building the new congruence: the new coefficient is compared with the old
+    one on every piece the change touches."""
+    import bisect
+    if starts is None:
+        starts = [a for a, _, _ in cg.sums]
+    a, b, c = cg.sums[j]
+    scaled = {dd * d: v for dd, v in c.items()}
+    mods = [(a, b, {dd: -v for dd, v in c.items()})]
+    mods += _reflect_into_half(cg.kind, [((a + i) / d, (b + i) / d, scaled) for i in range(d)])
+    cuts = set()
+    for x, y, _ in mods:
+        cuts.add(x)
+        cuts.add(y)
+        i = max(bisect.bisect_right(starts, x) - 1, 0)
+        while i < len(cg.sums) and cg.sums[i][0] < y:
+            for v in (cg.sums[i][0], cg.sums[i][1]):
+                if x < v < y:
+                    cuts.add(v)
+            i += 1
+    cuts = sorted(cuts)
+    delta = F(0)
+    for u, v in zip(cuts, cuts[1:]):
+        inside = [m for m in mods if m[0] <= u and v <= m[1]]
+        if not inside:
+            continue
+        old = _coef_at(cg.sums, starts, u)
+        new = old
+        for _, _, dc in inside:
+            new = _add(new, dc)
+        delta += (v - u) * ((1 if new else 0) - (1 if old else 0))
+    return delta
+
+
+def greedy_fast(start: Congruence, rounds: int, D: int = 8, min_gain: F = F(0), log=None):
+    """The heuristic search with lambda = 1, choosing each round's subdivision
+    by its exact cost change (cost_delta) and applying only the best one."""
+    cg = start
+    out = [cg]
+    for r in range(rounds):
+        starts = [a for a, _, _ in cg.sums]
+        best = None
+        for j in range(cg.m):
+            for d in range(2, D + 1):
+                dl = cost_delta(cg, j, d, starts)
+                if best is None or dl < best[0]:
+                    best = (dl, j, d)
+        if best is None or best[0] >= -min_gain:
+            break
+        a, b, _ = cg.sums[best[1]]
+        cg = subdivide(cg, a, b, best[2])
+        out.append(cg)
+        if log:
+            log(r, cg)
+    return out
+
+
 def greedy(start: Congruence, rounds: int, D: int = 8, lam: int = 1):
     """The heuristic search: each round takes the cheapest congruence reachable
     with `lam` subdivisions of d <= D.  Returns the list of congruences."""
@@ -280,6 +349,86 @@ def greedy(start: Congruence, rounds: int, D: int = 8, lam: int = 1):
         cg = min(cands.values(), key=lambda c: (c.cost, c.m))
         out.append(cg)
     return out
+
+
+# ---------------------------------------------------------------- generated tables
+# Cheaper congruences for B_{p-3} and E_{p-3} from the greedy search (Sec. 2,
+# "Heuristic searches", with lambda = 1, D = 8): (name, start, rounds).
+# The Bernoulli ones start from B30 as derived here (formal coefficients,
+# left side C_k(2,5,6), which is 14 at 2k = p - 3); the Euler ones from the
+# library's E33 table (integer coefficients relative to its left side).
+GENERATED = [("BB249", "BB30", 40), ("BB476", "BB30", 80), ("BB1115", "BB30", 200),
+             ("EE200", "EE33", 40), ("EE404", "EE33", 80), ("EE967", "EE33", 200)]
+
+
+def generated(which=None):
+    """{name: (congruence, lhs as an integer)} for the GENERATED list."""
+    starts = {}
+    out = {}
+    for name, start, rounds in GENERATED:
+        if which and name not in which:
+            continue
+        if start not in starts:
+            if start == "EE33":
+                lhs, rows = library_table("EE33")
+                cg = Congruence("E", ("table", lhs), simplify("E", [(x, y, {1: c}) for c, x, y in rows]))
+            else:
+                cg, lhs = derive(start), 14
+            rounds_needed = max(r for n, s, r in GENERATED if s == start and (not which or n in which))
+            starts[start] = (greedy_fast(cg, rounds_needed), lhs)
+        traj, lhs = starts[start]
+        cg = traj[min(rounds, len(traj) - 1)]
+        assert f"{name[:2]}{cg.m}" == name, (name, cg.m)
+        out[name] = (cg, lhs)
+    return out
+
+
+def emit_header(path: str):
+    """Write the generated congruences as a C header for the library."""
+    gens = generated()
+    dist_all, rows_all, tc_all, td_all, entries = [], [], [], [], []
+    for name, _, _ in GENERATED:
+        cg, lhs = gens[name]
+        dist = sorted({d for _, _, c in cg.sums for d in c})
+        dpos = {d: i for i, d in enumerate(dist)}
+        entries.append((name, 0 if cg.kind == "B" else 1, cg.m, lhs, len(rows_all), len(dist_all),
+                        len(dist), cg.cost))
+        for x, y, c in cg.sums:
+            assert max(x.numerator, x.denominator, y.numerator, y.denominator) < 2**26
+            rows_all.append((x.numerator, x.denominator, y.numerator, y.denominator, len(tc_all), len(c)))
+            for d in sorted(c):
+                tc_all.append(c[d])
+                td_all.append(dpos[d])
+        dist_all += dist
+    L = ["// Generated by paper_2101_11157_gb300/congen.py (emit_header): congruences for",
+         "// B_{p-3} and E_{p-3} from the greedy search of Sec. 2 (\"Heuristic searches\")",
+         "// over Prop. 2.1.  Row j of a congruence is (sum_k c_k d_k^t) S_t(xn/xd, yn/yd),",
+         "// t = p - 4 (B) or p - 3 (E), so d^t = d^-3 resp. d^-2; the left side is `lhs`.",
+         "// Do not edit: regenerate with `python -m paper_2101_11157_gb300.congen --emit`.",
+         "#pragma once", "#include <stdint.h>", "",
+         "struct WvGenTable {", "  const char *name;", "  int kind;", "  int nrows;", "  int64_t lhs;",
+         "  uint32_t row0, dist0, ndist;", "  double cost;  // in units of p", "};", "",
+         "static const WvGenTable kWvGenTables[] = {"]
+    for name, kind, m, lhs, r0, d0, nd, cost in entries:
+        L.append(f'  {{"{name}", {kind}, {m}, {lhs}LL, {r0}u, {d0}u, {nd}u, {float(cost)!r}}},')
+    L += ["};", "static const int kWvNumGenTables = (int)(sizeof(kWvGenTables) / sizeof(kWvGenTables[0]));",
+          "", "// xn, xd, yn, yd, first term, number of terms",
+          "static const uint32_t kWvGenRows[][6] = {"]
+    L += ["  {%d, %d, %d, %d, %d, %d}," % r for r in rows_all]
+    L += ["};", "", "static const int64_t kWvGenTermC[] = {"]
+    for i in range(0, len(tc_all), 12):
+        L.append("  " + " ".join(f"{v}," for v in tc_all[i:i + 12]))
+    L += ["};", "", "// index of d_k in the congruence's list of distinct bases",
+          "static const uint16_t kWvGenTermD[] = {"]
+    for i in range(0, len(td_all), 16):
+        L.append("  " + " ".join(f"{v}," for v in td_all[i:i + 16]))
+    L += ["};", "", "static const uint64_t kWvGenDist[] = {"]
+    for i in range(0, len(dist_all), 12):
+        L.append("  " + " ".join(f"{v}ull," for v in dist_all[i:i + 12]))
+    L += ["};", ""]
+    with open(path, "w") as f:
+        f.write("\n".join(L))
+    return entries
 
 
 # ---------------------------------------------------------------- library tables
@@ -305,7 +454,14 @@ def main():
     ap.add_argument("--lam", type=int, default=1)
     ap.add_argument("--exhaustive", default="", help="comma-separated d_i, e.g. 3,3,2")
     ap.add_argument("--start", default="vandiver", choices=["vandiver", "sv", "e1", *DERIVATIONS])
+    ap.add_argument("--emit", action="store_true", help="write csrc/wv_tables_gen.h")
     args = ap.parse_args()
+    if args.emit:
+        import os
+        path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc", "wv_tables_gen.h")
+        for name, kind, m, lhs, r0, d0, nd, cost in emit_header(path):
+            print(f"{name}: m={m} cost=p/{float(1 / cost):.3f} distinct bases={nd}")
+        return
     start = stafford_vandiver() if args.start == "sv" else derive(args.start)
     if args.derive:
         for name in DERIVATIONS:

@@ -16,8 +16,8 @@
 namespace wv {
 
 constexpr int kAccThreads = 256;
-constexpr int kMaxRowsPP = 66;
-constexpr int kMaxGenRows = 6;  // rows of the general-index forms, both kinds  // B rows + E rows for one prime (30 + 33 for BB30 + EE33)
+constexpr int kMaxRowsPP = 66;  // B rows + E rows of BB30 + EE33 (the allocation-free path)
+constexpr int kMaxDist = 256;   // distinct coefficient bases d of one congruence
 constexpr uint32_t kChunkPrimes = 16384;  // primes per internal launch sequence
 constexpr uint64_t kGroupMinChain = 48;   // grouped path only for chains of >= 48 terms
 
@@ -32,18 +32,24 @@ struct Plan {
   uint32_t *bk;                 // 3 x 64 words: bucket counts, offsets, cursors
   uint64_t *seg_lo, *seg_cnt;   // per segment (slot * rows_pp + row)
   uint32_t *seg_tiles, *seg_first;
+  uint32_t *tile_seg;           // per tile: its segment (written by the planner)
   uint32_t *total_tiles, *split_tile;
   uint32_t *counters;           // [0] M31 accumulation, [1] M64 accumulation
   ulonglong2 *partials;         // per tile (c0, c1), canonical
-  // congruence rows: rows [0, rows_b) are B rows, [rows_b, rows_pp) E rows
-  uint32_t xn[kMaxRowsPP], xd[kMaxRowsPP], yn[kMaxRowsPP], yd[kMaxRowsPP];
-  int64_t coef[kMaxRowsPP];
+  // congruence rows: rows [0, rows_b) are B rows, [rows_b, rows_pp) E rows,
+  // taken from the registry (device copy): B row j is registry row rb0 + j,
+  // E row j is re0 + j; a row's coefficient is sum_k c_k d_k^-ex with the
+  // bases d of its congruence at cg_dist[db0 ..] (B) / [de0 ..] (E)
+  const uint32_t *cg_rows;
+  const int64_t *cg_tc;
+  const uint16_t *cg_td;
+  const uint64_t *cg_dist;
+  uint32_t rb0, re0, db0, dbn, de0, den;
+  uint32_t ex_b, ex_e;  // 3 / 2 for B_{p-3} / E_{p-3}; e at a general index
   int64_t lhs_b, lhs_e;
-  // general index (0: the B_{p-3} / E_{p-3} forms): exponents e of the
-  // inverse-power sums, row coefficients sum_i gc_i gd_i^-e, C_k(a,b,c) of B
+  // general index (0: the B_{p-3} / E_{p-3} forms): the exponent e of the
+  // inverse-power sums, and (a, b, c) of C_k(a,b,c) for B
   uint32_t gen_e_b, gen_e_e;
-  int32_t gc[kMaxGenRows][3];
-  uint32_t gd[kMaxGenRows][3];
   uint32_t glhs[3];
 };
 
@@ -170,35 +176,8 @@ __device__ __forceinline__ void tile_m31(const PrimeCtx &ctx, uint64_t start, ui
 // polynomials in s of degree K e and (K-1) e.  Both are stepped s -> s+K by
 // forward differences (additions only), and each group costs three products:
 //   c0 <- c0 G0,   c1 <- c1 G0 + c0 G1.
-// G1 is kept in Montgomery form so that, as in the single-term step, the
-// ratio c1/c0 accumulates R * sum t^-1 (see the bookkeeping note above).
-
-// G0(x) (plain) and G1(x) R (Montgomery) for the group x, x+1, ..., x+K-1.
-template <int K, int EX>
-__device__ __forceinline__ void group_poly(const Mont &M, uint64_t x, int64_t &g0, int64_t &g1m) {
-  int64_t tm[K];
-#pragma unroll
-  for (int i = 0; i < K; ++i) {
-    uint64_t v = x + i;
-    if (v >= (uint64_t)M.p) v -= (uint64_t)M.p;
-    const int64_t b = M.to_mont((int64_t)v);
-    int64_t t = M.mul(b, b);
-    if (EX == 3) t = M.mul(t, b);
-    tm[i] = t;  // (x+i)^e in Montgomery form
-  }
-  int64_t all = M.one, g1 = 0;
-#pragma unroll
-  for (int i = 0; i < K; ++i) {
-    int64_t others = M.one;
-#pragma unroll
-    for (int j = 0; j < K; ++j)
-      if (j != i) others = M.mul(others, tm[j]);
-    g1 = M.add(g1, others);
-    all = M.mul(all, tm[i]);
-  }
-  g0 = M.from_mont(all);
-  g1m = g1;
-}
+// The tables are built so that G0 and R G1 carry the same power of R; as in
+// the single-term step the ratio c1/c0 then accumulates R * sum t^-1.
 
 template <int ILP, bool CUBES, int AR>
 __device__ __forceinline__ void tile_m31_grouped(const PrimeCtx &ctx, uint64_t start, uint64_t n,
@@ -228,27 +207,69 @@ __device__ __forceinline__ void tile_m31_grouped(const PrimeCtx &ctx, uint64_t s
     const uint64_t L = len + (ch < rem ? 1 : 0);
     s_tail[k] = s + G * K;
     n_tail[k] = (uint32_t)(L - G * K);
-    // difference tables of G0 and G1 at s, s+K, s+2K, ...
-    int64_t va[DA + 1], vb[DB + 1];
+    // Difference tables of G0 and G1 at s, s + K, ..., s + DA K, as on the
+    // 64-bit path: each point's pair from the plain powers t = x^e of its K
+    // consecutive x by P <- REDC(P t), Q <- REDC(Q t) + P (start P = t,
+    // Q = R), which gives G0 = R^-(K-1) prod t_i and G1 = R^-(K-2) sum_i
+    // prod_{j != i} t_j -- the common factor R^-(K-1) on G0 and R G1 leaves
+    // c1 / c0 unchanged; points from the top down (x^e by backward
+    // differences), folded into the diagonals: e_j <- (-1)^j D^j.
+    {
+      const int64_t pp = (int64_t)p;
+      int64_t xr = (int64_t)((s + (uint64_t)(K * (DA + 1) - 1)) % ctx.p);
+      const int64_t sq = M.mulmod(xr, xr);
+      int64_t t, d1, d2;
+      if (EX == 3) {  // x^3, 3x^2 - 3x + 1, 6x - 6, 6
+        t = M.mulmod(sq, xr);
+        d1 = ((3 * sq + 1) % pp + pp - (3 * xr) % pp) % pp;
+        d2 = (6 * xr + 6 * pp - 6) % pp;
+      } else {        // x^2, 2x - 1, 2
+        t = sq;
+        d1 = (2 * xr + pp - 1) % pp;
+        d2 = 2;
+      }
+      int64_t va[DA + 1], vb[DB + 1];
 #pragma unroll
-    for (int i = 0; i <= DA; ++i) {
-      int64_t a, b;
-      group_poly<K, EX>(M, s + (uint64_t)i * K, a, b);
-      va[i] = a;
-      if (i <= DB) vb[i] = b;
+      for (int i = 0; i <= DA; ++i) va[i] = 0;
+#pragma unroll
+      for (int i = 0; i <= DB; ++i) vb[i] = 0;
+#pragma unroll
+      for (int m = DA; m >= 0; --m) {
+        int64_t P = 0, Q = M.one;
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+          if (i == 0) {
+            P = t;
+          } else {
+            Q = M.add(M.mul(Q, t), P);
+            P = M.mul(P, t);
+          }
+          t = M.sub(t, d1);
+          d1 = M.sub(d1, d2);
+          if (EX == 3) d2 = M.sub(d2, 6 % pp);
+        }
+        int64_t nv = P;
+#pragma unroll
+        for (int j = 0; j <= DA - m; ++j) {
+          const int64_t old = va[j];
+          va[j] = nv;
+          if (j < DA - m) nv = M.sub(nv, old);
+        }
+        if (m <= DB) {
+          nv = Q;
+#pragma unroll
+          for (int j = 0; j <= DB - m; ++j) {
+            const int64_t old = vb[j];
+            vb[j] = nv;
+            if (j < DB - m) nv = M.sub(nv, old);
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j <= DA; ++j) ga[k][j] = (int32_t)((j & 1) ? (va[j] ? pp - va[j] : 0) : va[j]);
+#pragma unroll
+      for (int j = 0; j <= DB; ++j) gb[k][j] = (int32_t)((j & 1) ? (vb[j] ? pp - vb[j] : 0) : vb[j]);
     }
-#pragma unroll
-    for (int j = 1; j <= DA; ++j)
-#pragma unroll
-      for (int i = DA; i >= j; --i) va[i] = M.sub(va[i], va[i - 1]);
-#pragma unroll
-    for (int j = 1; j <= DB; ++j)
-#pragma unroll
-      for (int i = DB; i >= j; --i) vb[i] = M.sub(vb[i], vb[i - 1]);
-#pragma unroll
-    for (int i = 0; i <= DA; ++i) ga[k][i] = (int32_t)va[i];
-#pragma unroll
-    for (int i = 0; i <= DB; ++i) gb[k][i] = (int32_t)vb[i];
     c0[k] = (int32_t)ctx.one;
     c1[k] = 0;
   }
@@ -812,13 +833,8 @@ template <bool WIDE, int ILP, int AR>
 __device__ __forceinline__ void process_tile(const Plan &P, uint32_t g) {
   const int lane = threadIdx.x & 31;
   const uint32_t nsegs = P.n * P.rows_pp;
-  // segment owning tile g: the last s with seg_first[s] <= g
-  uint32_t lo = 0, hi = nsegs;
-  while (hi - lo > 1) {
-    uint32_t mid = (lo + hi) >> 1;
-    if (__ldg(&P.seg_first[mid]) <= g) lo = mid; else hi = mid;
-  }
-  const uint32_t s = lo;
+  // segment owning tile g (the planner's tile -> segment map)
+  const uint32_t s = __ldg(&P.tile_seg[g]);
   const uint32_t slot = s / P.rows_pp, j = s - slot * P.rows_pp;
   const PrimeCtx ctx = P.ctx[slot];
   const uint32_t k = g - P.seg_first[s], T = P.seg_tiles[s];

@@ -37,9 +37,39 @@ struct DeviceState {
   cudaMemPool_t pool = nullptr;
   uint32_t *base_primes = nullptr;  // odd primes 3 .. sqrt(WV_P_MAX), device
   uint32_t n_base = 0;
+  // the congruence registry (wv_registry.cu), device copy
+  uint32_t *cg_rows = nullptr;
+  int64_t *cg_tc = nullptr;
+  uint16_t *cg_td = nullptr;
+  uint64_t *cg_dist = nullptr;
 };
 // State of the current device, created on first use.
 wv_status device_state(DeviceState **out);
+
+// ------------------------------------------------------------ congruences
+// Every runnable congruence (wv_registry.cu): ids 0 .. cong_count()-1 are the
+// built-in and generated ones (selectable through wv_options); the general-
+// index forms follow at cong_general_id(kind).  Row r of the registry is
+// (sum_k c_k d_k^t) S_t(xn/xd, yn/yd): words xn, xd, yn, yd, first term,
+// number of terms; term k is (cong_tc()[k], index cong_td()[k] into the
+// congruence's distinct bases cong_dist()[dist0 ..]).
+struct CongView {
+  const char *name;
+  int kind;       // 0 = Bernoulli, 1 = Euler
+  int nrows;
+  int64_t lhs;    // the left side (0 for the general-index forms)
+  uint32_t row0, dist0, ndist;
+};
+int cong_count();
+int cong_default(int kind);
+int cong_general_id(int kind);
+const CongView &cong_view(int id);
+const uint32_t *cong_row(uint32_t r);
+const int64_t *cong_tc();
+const uint16_t *cong_td();
+const uint64_t *cong_dist();
+uint64_t cong_row_terms(uint32_t r, uint64_t p);  // terms of row r for prime p
+wv_status cong_upload(DeviceState *d);
 
 // ------------------------------------------------------------ scratch
 // Stream-ordered allocation from the library's own memory pool.
@@ -92,8 +122,8 @@ wv_status scan_exclusive_u32_bare(const uint32_t *d_in, uint32_t *d_out, size_t 
 
 // ------------------------------------------------------------ residues
 struct ResidueConfig {
-  int cong_b = 6;        // BB30; -2 = skip
-  int cong_e = 12;       // EE33; -2 = skip
+  int cong_b = 6;        // set by resolve_config (cong_default); -2 = skip
+  int cong_e = 12;       // set by resolve_config (cong_default); -2 = skip
   int block = 256;
   int ilp = 2;            // chains per thread, p < 2^30
   int ilp64 = 1;          // chains per thread, 2^30 <= p < 2^37

@@ -99,8 +99,10 @@ __global__ void k_plan_segments(Plan P) {
   if (!(c.flags & 2u)) {
     const uint64_t p = c.p;
     // open interval (x p, y p): s = floor(xn p / xd) + 1 .. floor(yn p / yd)
-    lo = (uint64_t)P.xn[j] * p / P.xd[j] + 1;
-    uint64_t hi = (uint64_t)P.yn[j] * p / P.yd[j] + 1;
+    // (registry endpoints are below 2^26, so xn p < 2^63)
+    const uint32_t *w = P.cg_rows + 6 * (size_t)(j < P.rows_b ? P.rb0 + j : P.re0 + (j - P.rows_b));
+    lo = (uint64_t)w[0] * p / w[1] + 1;
+    uint64_t hi = (uint64_t)w[2] * p / w[3] + 1;
     cnt = hi > lo ? hi - lo : 0;
     if (cnt) {
       uint64_t t = (cnt + P.tile_terms - 1) / P.tile_terms;
@@ -110,6 +112,14 @@ __global__ void k_plan_segments(Plan P) {
   P.seg_lo[idx] = lo;
   P.seg_cnt[idx] = cnt;
   P.seg_tiles[idx] = tiles;
+}
+
+// tile -> segment map: every segment writes its index into its tiles' slots
+__global__ void k_plan_tilemap(Plan P) {
+  const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= P.n * P.rows_pp) return;
+  const uint32_t f = P.seg_first[idx], T = P.seg_tiles[idx];
+  for (uint32_t t = 0; t < T; ++t) P.tile_seg[f + t] = idx;
 }
 
 __global__ void k_plan_split(Plan P) {
@@ -133,7 +143,8 @@ __device__ __forceinline__ uint64_t special_value(uint64_t p, bool isB) {
   return WV_RESIDUE_INVALID;
 }
 
-__global__ void k_finalize(Plan P) {
+constexpr int kFinThreads = 256;
+__global__ void __launch_bounds__(kFinThreads) k_finalize(Plan P) {
   const int lane = threadIdx.x & 31;
   const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nk = (P.rows_b ? 1u : 0u) + (P.rows_e ? 1u : 0u);
@@ -157,6 +168,17 @@ __global__ void k_finalize(Plan P) {
   const uint32_t nrows = isB ? P.rows_b : P.rows_e;
   const uint32_t r0 = isB ? 0u : P.rows_b;
   const uint32_t seg0 = slot * P.rows_pp + r0;
+  // d^-ex for the congruence's distinct bases d, once per prime, per warp
+  __shared__ int64_t s_pow[kFinThreads / 32][kMaxDist];
+  int64_t *dpow = s_pow[threadIdx.x >> 5];
+  {
+    const uint32_t d0 = isB ? P.db0 : P.de0, nd = isB ? P.dbn : P.den;
+    const uint64_t ex = isB ? P.ex_b : P.ex_e;
+    for (uint32_t i = lane; i < nd; i += 32)
+      dpow[i] = M.pow(M.to_mont((int64_t)(P.cg_dist[d0 + i] % ctx.p)), ctx.p - 1 - ex);
+    __syncwarp();
+  }
+  const uint32_t reg0 = isB ? P.rb0 : P.re0;
   int64_t N = 0, D = M.one;  // running fraction N / D = sum coef_j c1_j / c0_j
   for (uint32_t j = lane; j < nrows; j += 32) {
     const uint32_t s = seg0 + j;
@@ -166,17 +188,11 @@ __global__ void k_finalize(Plan P) {
       const ulonglong2 v = P.partials[g];
       M.combine(C0, C1, (int64_t)v.x, (int64_t)v.y);
     }
-    int64_t aM;
-    if (ge) {  // sum_i c_i d_i^t with t = p - 1 - e
-      aM = 0;
-      for (int i = 0; i < 3; ++i) {
-        if (!P.gc[r0 + j][i]) continue;
-        const int64_t dt = M.pow(M.to_mont((int64_t)P.gd[r0 + j][i]), (uint64_t)(p - 1 - (int64_t)ge));
-        aM = M.add(aM, M.mul(M.to_mont(smod64(P.gc[r0 + j][i], p)), dt));
-      }
-    } else {
-      aM = M.to_mont(smod64(P.coef[r0 + j], p));
-    }
+    // coefficient sum_k c_k d_k^-ex, in Montgomery form
+    const uint32_t *w = P.cg_rows + 6 * (size_t)(reg0 + j);
+    int64_t aM = 0;
+    for (uint32_t t = w[4]; t < w[4] + w[5]; ++t)
+      aM = M.add(aM, M.mul(M.to_mont(smod64(P.cg_tc[t], p)), dpow[P.cg_td[t]]));
     const int64_t X = M.mul(aM, C1);  // coef * C1 at C1's scale
     N = M.add(M.mul(N, C0), M.mul(X, D));
     D = M.mul(D, C0);
@@ -277,7 +293,7 @@ static wv_status launch_accumulate(const Plan &P, const ResidueConfig &cfg, int 
   return WV_OK;
 }
 
-static void fill_rows(Plan &P, const ResidueConfig &cfg);
+static void fill_rows(Plan &P, const ResidueConfig &cfg, const DeviceState *dev);
 
 wv_status residues_device(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,
                           uint64_t *d_out_e, const ResidueConfig &cfg, cudaStream_t s) {
@@ -293,7 +309,7 @@ wv_status residues_device(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,
   ResidueConfig c2 = cfg;
   if (!do_b) c2.cong_b = -2, c2.gen_e_b = 0;
   if (!do_e) c2.cong_e = -2, c2.gen_e_e = 0;
-  fill_rows(P, c2);
+  fill_rows(P, c2, dev);
 
   const size_t cap = cfg.chunk > 0 ? (size_t)cfg.chunk : kChunkPrimes;
   const uint32_t chunk = (uint32_t)(n < cap ? n : cap);
@@ -309,6 +325,7 @@ wv_status residues_device(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,
   WV_CHECK(sc.get(&P.seg_tiles, nseg));
   WV_CHECK(sc.get(&P.seg_first, nseg));
   WV_CHECK(sc.get(&P.partials, nseg * P.max_tiles));
+  WV_CHECK(sc.get(&P.tile_seg, nseg * P.max_tiles));
   WV_CHECK(sc.get(&u32tmp, scan_tmp_elems(nseg)));
   WV_CHECK(sc.get(&scal, 256));
   P.bk = scal + 64;
@@ -330,6 +347,7 @@ wv_status residues_device(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,
     const size_t ns = (size_t)P.n * P.rows_pp;
     WV_LAUNCH("plan_segments", k_plan_segments, (unsigned)((ns + 255) / 256), 256, 0, s, P);
     WV_CHECK(scan_exclusive_u32(P.seg_tiles, P.seg_first, ns, P.total_tiles, u32tmp, s));
+    WV_LAUNCH("plan_tilemap", k_plan_tilemap, (unsigned)((ns + 255) / 256), 256, 0, s, P);
     WV_LAUNCH("plan_split", k_plan_split, 1, 1, 0, s, P);
     WV_CHECK(launch_accumulate<false>(P, cfg, dev->sms, s));
     WV_CHECK(launch_accumulate<true>(P, cfg, dev->sms, s));
@@ -346,54 +364,53 @@ wv_status residues_device(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,
 // plan_build -> plan_totals -> epoch_launch (any number of times, over any
 // tile ranges) -> plan_finalize -> plan_free.
 
-static void fill_rows(Plan &P, const ResidueConfig &cfg) {
+static void fill_rows(Plan &P, const ResidueConfig &cfg, const DeviceState *dev) {
+  P.cg_rows = dev->cg_rows;
+  P.cg_tc = dev->cg_tc;
+  P.cg_td = dev->cg_td;
+  P.cg_dist = dev->cg_dist;
   uint32_t r = 0;
-  // a general-index form: its rows with their coefficient descriptors
-  auto general = [&](const WvGenCongruence &c) {
-    for (int j = 0; j < c.nrows; ++j, ++r) {
-      const WvGenRow &w = c.rows[j];
-      P.xn[r] = w.xn; P.xd[r] = w.xd; P.yn[r] = w.yn; P.yd[r] = w.yd; P.coef[r] = 0;
-      for (int i = 0; i < 3; ++i) {
-        P.gc[r][i] = w.c[i];
-        P.gd[r][i] = w.d[i];
-      }
+  auto use = [&](int id, bool isB) {
+    const CongView &v = cong_view(id);
+    if (isB) {
+      P.rows_b = (uint32_t)v.nrows;
+      P.rb0 = v.row0;
+      P.db0 = v.dist0;
+      P.dbn = v.ndist;
+      P.lhs_b = v.lhs;
+    } else {
+      P.rows_e = (uint32_t)v.nrows;
+      P.re0 = v.row0;
+      P.de0 = v.dist0;
+      P.den = v.ndist;
+      P.lhs_e = v.lhs;
     }
-    return (uint32_t)c.nrows;
+    r += (uint32_t)v.nrows;
   };
   if (cfg.gen_e_b) {
-    P.rows_b = general(kWvGeneral[0]);
-    P.gen_e_b = cfg.gen_e_b;
+    use(cong_general_id(0), true);
+    P.gen_e_b = P.ex_b = cfg.gen_e_b;
     for (int i = 0; i < 3; ++i) P.glhs[i] = kWvGeneral[0].lhs[i];
   } else if (cfg.cong_b >= 0) {
-    const WvCongruence &c = kWvCongruences[cfg.cong_b];
-    for (int j = 0; j < c.nrows; ++j, ++r) {
-      const WvRow &w = kWvRows[c.row_offset + j];
-      P.xn[r] = w.xn; P.xd[r] = w.xd; P.yn[r] = w.yn; P.yd[r] = w.yd; P.coef[r] = w.coef;
-    }
-    P.rows_b = c.nrows;
-    P.lhs_b = c.lhs;
+    use(cfg.cong_b, true);
+    P.ex_b = 3;  // t = p - 4: d^t = d^-3
   }
   if (cfg.gen_e_e) {
-    P.rows_e = general(kWvGeneral[1]);
-    P.gen_e_e = cfg.gen_e_e;
+    use(cong_general_id(1), false);
+    P.gen_e_e = P.ex_e = cfg.gen_e_e;
   } else if (cfg.cong_e >= 0) {
-    const WvCongruence &c = kWvCongruences[cfg.cong_e];
-    for (int j = 0; j < c.nrows; ++j, ++r) {
-      const WvRow &w = kWvRows[c.row_offset + j];
-      P.xn[r] = w.xn; P.xd[r] = w.xd; P.yn[r] = w.yn; P.yd[r] = w.yd; P.coef[r] = w.coef;
-    }
-    P.rows_e = c.nrows;
-    P.lhs_e = c.lhs;
+    use(cfg.cong_e, false);
+    P.ex_e = 2;  // t = p - 3: d^t = d^-2
   }
   P.rows_pp = r;
 }
 
 static size_t rows_of(const ResidueConfig &cfg) {
   size_t r = 0;
-  if (cfg.gen_e_b) r += kWvGeneral[0].nrows;
-  else if (cfg.cong_b >= 0) r += kWvCongruences[cfg.cong_b].nrows;
-  if (cfg.gen_e_e) r += kWvGeneral[1].nrows;
-  else if (cfg.cong_e >= 0) r += kWvCongruences[cfg.cong_e].nrows;
+  if (cfg.gen_e_b) r += cong_view(cong_general_id(0)).nrows;
+  else if (cfg.cong_b >= 0) r += cong_view(cfg.cong_b).nrows;
+  if (cfg.gen_e_e) r += cong_view(cong_general_id(1)).nrows;
+  else if (cfg.cong_e >= 0) r += cong_view(cfg.cong_e).nrows;
   return r;
 }
 
@@ -401,7 +418,7 @@ size_t plan_bytes(uint32_t n, const ResidueConfig &cfg) {
   const size_t ns = (size_t)n * rows_of(cfg);
   uint32_t tt = 0, mt = 0;
   tile_shape(cfg, n, rows_of(cfg), &tt, &mt);
-  return n * (sizeof(PrimeCtx) + 8) + ns * (8 + 8 + 4 + 4) + ns * mt * sizeof(ulonglong2) +
+  return n * (sizeof(PrimeCtx) + 8) + ns * (8 + 8 + 4 + 4) + ns * mt * (sizeof(ulonglong2) + 4) +
          scan_tmp_elems(ns) * 4 + 1024 + 16 * 256;
 }
 
@@ -410,10 +427,12 @@ size_t plan_struct_bytes() { return sizeof(Plan); }
 wv_status plan_build(const uint64_t *d_primes, uint32_t n, const ResidueConfig &cfg, PlanState *ps,
                      cudaStream_t s) {
   if (n == 0 || n > 65536) return set_error(WV_EINVAL, "plan_build: n=%u not in [1, 65536]", n);
+  DeviceState *dev = nullptr;
+  WV_CHECK(device_state(&dev));
   ps->host = new Plan();
   Plan &P = *ps->host;
   memset(&P, 0, sizeof P);
-  fill_rows(P, cfg);
+  fill_rows(P, cfg, dev);
   tile_shape(cfg, n, P.rows_pp, &P.tile_terms, &P.max_tiles);
   const size_t ns = (size_t)n * P.rows_pp;
   auto get = [&](void **p, size_t bytes) -> wv_status {
@@ -430,6 +449,7 @@ wv_status plan_build(const uint64_t *d_primes, uint32_t n, const ResidueConfig &
   WV_CHECK(get((void **)&P.seg_tiles, ns * 4));
   WV_CHECK(get((void **)&P.seg_first, ns * 4));
   WV_CHECK(get((void **)&P.partials, ns * P.max_tiles * sizeof(ulonglong2)));
+  WV_CHECK(get((void **)&P.tile_seg, ns * P.max_tiles * sizeof(uint32_t)));
   WV_CHECK(get((void **)&u32tmp, scan_tmp_elems(ns) * 4));
   WV_CHECK(get((void **)&scal, 1024));
   P.pos = nullptr;
@@ -448,6 +468,7 @@ wv_status plan_build(const uint64_t *d_primes, uint32_t n, const ResidueConfig &
   WV_LAUNCH("plan_scatter", k_plan_scatter, gp, 256, 0, s, P);
   WV_LAUNCH("plan_segments", k_plan_segments, (unsigned)((ns + 255) / 256), 256, 0, s, P);
   WV_CHECK(scan_exclusive_u32(P.seg_tiles, P.seg_first, ns, P.total_tiles, u32tmp, s));
+  WV_LAUNCH("plan_tilemap", k_plan_tilemap, (unsigned)((ns + 255) / 256), 256, 0, s, P);
   WV_LAUNCH("plan_split", k_plan_split, 1, 1, 0, s, P);
   return WV_OK;
 }
@@ -541,12 +562,20 @@ constexpr size_t kNaScanTmp = kNaSegs / 4096 + 2;  // scan_tmp_elems bound for k
 constexpr size_t kNaBytes =
     na_align(kNoAllocMaxPrimes * sizeof(PrimeCtx)) + 2 * na_align(kNoAllocMaxPrimes * 4) +
     2 * na_align(kNaSegs * 8) + 2 * na_align(kNaSegs * 4) +
-    na_align(kNaSegs * kNoAllocTiles * sizeof(ulonglong2)) + na_align(kNaScanTmp * 4) + 1024;
+    na_align(kNaSegs * kNoAllocTiles * sizeof(ulonglong2)) +
+    na_align(kNaSegs * kNoAllocTiles * sizeof(uint32_t)) + na_align(kNaScanTmp * 4) + 1024;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
+// BB30 + EE33 in registry form (63 rows, one term each, base 1), written
+// once per device at the first call
+static __device__ uint32_t g_na_rows[kMaxRowsPP * 6];
+static __device__ int64_t g_na_tc[kMaxRowsPP];
+static __device__ uint16_t g_na_td[kMaxRowsPP];
+static __device__ uint64_t g_na_dist[2];
 static std::mutex g_na_mu;
 static void *g_na_addr[64];  // device address of g_noalloc_scratch, per device
+static void *g_na_cg[64][4];  // device addresses of the four arrays above, per device
 
 wv_status residues_noalloc(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,
                            uint64_t *d_out_e, cudaStream_t s) {
@@ -569,6 +598,35 @@ wv_status residues_noalloc(const uint64_t *d_primes, size_t n, uint64_t *d_out_b
       void *ptr = nullptr;
       cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
       if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(noalloc scratch)");
+      // the congruence rows, copied into their static arrays (no allocation)
+      uint32_t rows[kMaxRowsPP * 6];
+      int64_t tc[kMaxRowsPP];
+      uint16_t td[kMaxRowsPP];
+      const uint64_t dist[2] = {1, 1};
+      uint32_t r = 0;
+      for (int id : {kWvDefaultB, kWvDefaultE}) {
+        const CongView &v = cong_view(id);
+        for (int j = 0; j < v.nrows; ++j, ++r) {
+          const uint32_t *w = cong_row(v.row0 + j);
+          rows[6 * r + 0] = w[0];
+          rows[6 * r + 1] = w[1];
+          rows[6 * r + 2] = w[2];
+          rows[6 * r + 3] = w[3];
+          rows[6 * r + 4] = r;
+          rows[6 * r + 5] = 1;
+          tc[r] = cong_tc()[w[4]];
+          td[r] = 0;  // base d = 1, index 0 of each congruence's own list
+        }
+      }
+      if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_na_rows, rows, sizeof rows);
+      if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_na_tc, tc, sizeof tc);
+      if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_na_td, td, sizeof td);
+      if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_na_dist, dist, sizeof dist);
+      if (e == cudaSuccess) e = cudaGetSymbolAddress(&g_na_cg[dev][0], g_na_rows);
+      if (e == cudaSuccess) e = cudaGetSymbolAddress(&g_na_cg[dev][1], g_na_tc);
+      if (e == cudaSuccess) e = cudaGetSymbolAddress(&g_na_cg[dev][2], g_na_td);
+      if (e == cudaSuccess) e = cudaGetSymbolAddress(&g_na_cg[dev][3], g_na_dist);
+      if (e != cudaSuccess) return cuda_fail(e, "noalloc congruence tables");
       g_na_addr[dev] = ptr;
     }
     base = (unsigned char *)g_na_addr[dev];
@@ -576,29 +634,43 @@ wv_status residues_noalloc(const uint64_t *d_primes, size_t n, uint64_t *d_out_b
   int sms = 0;
   WV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
 
-  ResidueConfig cfg;  // library defaults
+  // BB30 + EE33 (63 rows), whatever the library default: the scratch array
+  // is sized for them
+  ResidueConfig cfg;
+  cfg.cong_b = do_b ? kWvDefaultB : -2;
+  cfg.cong_e = do_e ? kWvDefaultE : -2;
   Plan P;
   memset(&P, 0, sizeof P);
   uint32_t r = 0;
   if (do_b) {
-    const WvCongruence &c = kWvCongruences[cfg.cong_b];
-    for (int j = 0; j < c.nrows; ++j, ++r) {
-      const WvRow &w = kWvRows[c.row_offset + j];
-      P.xn[r] = w.xn; P.xd[r] = w.xd; P.yn[r] = w.yn; P.yd[r] = w.yd; P.coef[r] = w.coef;
-    }
-    P.rows_b = c.nrows;
-    P.lhs_b = c.lhs;
+    const CongView &v = cong_view(cfg.cong_b);
+    P.rows_b = (uint32_t)v.nrows;
+    P.lhs_b = v.lhs;
+    P.ex_b = 3;
+    r += P.rows_b;
   }
   if (do_e) {
-    const WvCongruence &c = kWvCongruences[cfg.cong_e];
-    for (int j = 0; j < c.nrows; ++j, ++r) {
-      const WvRow &w = kWvRows[c.row_offset + j];
-      P.xn[r] = w.xn; P.xd[r] = w.xd; P.yn[r] = w.yn; P.yd[r] = w.yd; P.coef[r] = w.coef;
-    }
-    P.rows_e = c.nrows;
-    P.lhs_e = c.lhs;
+    const CongView &v = cong_view(cfg.cong_e);
+    P.rows_e = (uint32_t)v.nrows;
+    P.lhs_e = v.lhs;
+    P.ex_e = 2;
+    r += P.rows_e;
   }
   P.rows_pp = r;
+  {
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    P.cg_rows = (const uint32_t *)g_na_cg[dev][0];
+    P.cg_tc = (const int64_t *)g_na_cg[dev][1];
+    P.cg_td = (const uint16_t *)g_na_cg[dev][2];
+    P.cg_dist = (const uint64_t *)g_na_cg[dev][3];
+  }
+  // rows: BB30 at 0 (base index 0), EE33 after it (base index 1)
+  P.rb0 = 0;
+  P.re0 = (uint32_t)cong_view(kWvDefaultB).nrows;
+  P.db0 = 0;
+  P.dbn = 1;
+  P.de0 = 1;
+  P.den = 1;
   P.tile_terms = (uint32_t)cfg.tile_terms;
   P.max_tiles = kNoAllocTiles;
   // carve the scratch array
@@ -616,6 +688,7 @@ wv_status residues_noalloc(const uint64_t *d_primes, size_t n, uint64_t *d_out_b
   P.seg_tiles = (uint32_t *)carve(kNaSegs * 4);
   P.seg_first = (uint32_t *)carve(kNaSegs * 4);
   P.partials = (ulonglong2 *)carve(kNaSegs * kNoAllocTiles * sizeof(ulonglong2));
+  P.tile_seg = (uint32_t *)carve(kNaSegs * kNoAllocTiles * sizeof(uint32_t));
   uint32_t *u32tmp = (uint32_t *)carve(kNaScanTmp * 4);
   uint32_t *scal = (uint32_t *)carve(256 * sizeof(uint32_t));
   if (off > kNaBytes) return set_error(WV_EINVAL, "internal: no-alloc scratch layout overflow");
@@ -637,6 +710,7 @@ wv_status residues_noalloc(const uint64_t *d_primes, size_t n, uint64_t *d_out_b
   k_plan_scatter<<<gp, 256, 0, s>>>(P);
   k_plan_segments<<<(unsigned)((ns + 255) / 256), 256, 0, s>>>(P);
   WV_CHECK(scan_exclusive_u32_bare(P.seg_tiles, P.seg_first, ns, P.total_tiles, u32tmp, s));
+  k_plan_tilemap<<<(unsigned)((ns + 255) / 256), 256, 0, s>>>(P);
   k_plan_split<<<1, 1, 0, s>>>(P);
   WV_CUDA(cudaGetLastError());
   AccKernel k31 = acc_kernel_m31(9, 2);

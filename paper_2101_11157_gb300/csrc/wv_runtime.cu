@@ -72,6 +72,7 @@ wv_status device_state(DeviceState **out) {
     WV_CUDA(cudaFree(cnt));
     d.base_primes = buf;
     d.n_base = n;
+    WV_CHECK(cong_upload(&d));
     d.device = dev;
   }
   *out = &d;
@@ -277,8 +278,8 @@ wv_status scan_exclusive_u32_bare(const uint32_t *in, uint32_t *out, size_t n, u
 // ================================================================ options
 wv_status resolve_config(const wv_options *opt, bool want_b, bool want_e, ResidueConfig *cfg) {
   ResidueConfig c;
-  c.cong_b = want_b ? kWvDefaultB : -2;
-  c.cong_e = want_e ? kWvDefaultE : -2;
+  c.cong_b = want_b ? cong_default(0) : -2;
+  c.cong_e = want_e ? cong_default(1) : -2;
   if (opt) {
     if (want_b && opt->cong_b >= 0) c.cong_b = opt->cong_b;
     if (want_e && opt->cong_e >= 0) c.cong_e = opt->cong_e;
@@ -290,9 +291,9 @@ wv_status resolve_config(const wv_options *opt, bool want_b, bool want_e, Residu
     if (opt->blocks_per_sm > 0) c.blocks_per_sm = opt->blocks_per_sm;
     if (opt->arith > 0) c.arith = opt->arith;
   }
-  if (c.cong_b >= 0 && (c.cong_b >= kWvNumCongruences || kWvCongruences[c.cong_b].kind != 0))
+  if (c.cong_b >= 0 && (c.cong_b >= cong_count() || cong_view(c.cong_b).kind != 0))
     return set_error(WV_EINVAL, "cong_b=%d is not a Bernoulli congruence", c.cong_b);
-  if (c.cong_e >= 0 && (c.cong_e >= kWvNumCongruences || kWvCongruences[c.cong_e].kind != 1))
+  if (c.cong_e >= 0 && (c.cong_e >= cong_count() || cong_view(c.cong_e).kind != 1))
     return set_error(WV_EINVAL, "cong_e=%d is not an Euler congruence", c.cong_e);
   if (c.block < 32 || c.block > 256 || c.block % 32)
     return set_error(WV_EINVAL, "block=%d must be a multiple of 32 in [32,256]", c.block);
@@ -317,11 +318,11 @@ extern "C" {
 const char *wv_version(void) { return "wv 0.1 (sm_103a)"; }
 const char *wv_last_error(void) { return g_err.c_str(); }
 
-int wv_congruence_count(void) { return kWvNumCongruences; }
+int wv_congruence_count(void) { return cong_count(); }
 
 wv_status wv_congruence_info(int id, int *kind, int *n_rows, int64_t *lhs, const char **name) {
-  if (id < 0 || id >= kWvNumCongruences) return set_error(WV_EINVAL, "congruence id %d", id);
-  const WvCongruence &c = kWvCongruences[id];
+  if (id < 0 || id >= cong_count()) return set_error(WV_EINVAL, "congruence id %d", id);
+  const CongView &c = cong_view(id);
   if (kind) *kind = c.kind;
   if (n_rows) *n_rows = c.nrows;
   if (lhs) *lhs = c.lhs;
@@ -331,15 +332,31 @@ wv_status wv_congruence_info(int id, int *kind, int *n_rows, int64_t *lhs, const
 
 wv_status wv_congruence_row(int id, int row, int64_t *coef, uint32_t *xn, uint32_t *xd,
                             uint32_t *yn, uint32_t *yd) {
-  if (id < 0 || id >= kWvNumCongruences) return set_error(WV_EINVAL, "congruence id %d", id);
-  const WvCongruence &c = kWvCongruences[id];
+  if (id < 0 || id >= cong_count()) return set_error(WV_EINVAL, "congruence id %d", id);
+  const CongView &c = cong_view(id);
   if (row < 0 || row >= c.nrows) return set_error(WV_EINVAL, "row %d of %s", row, c.name);
-  const WvRow &r = kWvRows[c.row_offset + row];
-  if (coef) *coef = r.coef;
-  if (xn) *xn = r.xn;
-  if (xd) *xd = r.xd;
-  if (yn) *yn = r.yn;
-  if (yd) *yd = r.yd;
+  const uint32_t *w = cong_row(c.row0 + (uint32_t)row);
+  if (xn) *xn = w[0];
+  if (xd) *xd = w[1];
+  if (yn) *yn = w[2];
+  if (yd) *yd = w[3];
+  const bool plain = w[5] == 1 && cong_dist()[c.dist0 + cong_td()[w[4]]] == 1;
+  if (coef) *coef = plain ? cong_tc()[w[4]] : 0;
+  if (!plain) return set_error(WV_ERANGE, "row %d of %s has a coefficient sum c_k d_k^t", row, c.name);
+  return WV_OK;
+}
+
+wv_status wv_congruence_terms(int id, int row, int64_t *c, uint64_t *d, int cap, int *n) {
+  if (id < 0 || id >= cong_count()) return set_error(WV_EINVAL, "congruence id %d", id);
+  const CongView &v = cong_view(id);
+  if (row < 0 || row >= v.nrows) return set_error(WV_EINVAL, "row %d of %s", row, v.name);
+  const uint32_t *w = cong_row(v.row0 + (uint32_t)row);
+  if (n) *n = (int)w[5];
+  for (uint32_t k = 0; k < w[5] && (int)k < cap; ++k) {
+    if (c) c[k] = cong_tc()[w[4] + k];
+    if (d) d[k] = cong_dist()[v.dist0 + cong_td()[w[4] + k]];
+  }
+  if ((int)w[5] > cap) return set_error(WV_ERANGE, "row has %u terms, capacity %d", w[5], cap);
   return WV_OK;
 }
 
@@ -363,31 +380,23 @@ wv_status wv_general_row(int kind, int row, uint32_t *xn, uint32_t *xd, uint32_t
 
 int wv_general_rows(int kind) { return (kind == 0 || kind == 1) ? kWvGeneral[kind].nrows : 0; }
 
-static uint64_t row_terms(const WvRow &r, uint64_t p) {
-  // s runs over floor(xn p/xd)+1 .. floor(yn p/yd) (no endpoint is an integer, p >= 7)
-  uint64_t lo = (uint64_t)r.xn * p / r.xd + 1;
-  uint64_t hi = (uint64_t)r.yn * p / r.yd + 1;
-  return hi > lo ? hi - lo : 0;
-}
-
 wv_status wv_count_terms(const uint64_t *h_primes, size_t n, int cong_b, int cong_e,
                          uint64_t *terms_b, uint64_t *terms_e) {
   if (n && !h_primes) return set_error(WV_EINVAL, "h_primes is NULL");
-  if (cong_b == -1 || cong_b < -2) cong_b = kWvDefaultB;
-  if (cong_e == -1 || cong_e < -2) cong_e = kWvDefaultE;
-  if (cong_b >= kWvNumCongruences || cong_e >= kWvNumCongruences)
-    return set_error(WV_EINVAL, "bad congruence id");
+  if (cong_b == -1 || cong_b < -2) cong_b = cong_default(0);
+  if (cong_e == -1 || cong_e < -2) cong_e = cong_default(1);
+  if (cong_b >= cong_count() || cong_e >= cong_count()) return set_error(WV_EINVAL, "bad congruence id");
   uint64_t tb = 0, te = 0;
   for (size_t i = 0; i < n; ++i) {
     uint64_t p = h_primes[i];
     if (p < 11 || p >= WV_P_MAX || (p & 1) == 0) continue;
     if (cong_b >= 0) {
-      const WvCongruence &c = kWvCongruences[cong_b];
-      for (int j = 0; j < c.nrows; ++j) tb += row_terms(kWvRows[c.row_offset + j], p);
+      const CongView &c = cong_view(cong_b);
+      for (int j = 0; j < c.nrows; ++j) tb += cong_row_terms(c.row0 + j, p);
     }
     if (cong_e >= 0) {
-      const WvCongruence &c = kWvCongruences[cong_e];
-      for (int j = 0; j < c.nrows; ++j) te += row_terms(kWvRows[c.row_offset + j], p);
+      const CongView &c = cong_view(cong_e);
+      for (int j = 0; j < c.nrows; ++j) te += cong_row_terms(c.row0 + j, p);
     }
   }
   if (terms_b) *terms_b = tb;

@@ -73,12 +73,6 @@ struct SQuery {
   wv_status count_status = WV_OK;
 };
 
-static uint64_t row_terms_host(const WvRow &r, uint64_t p) {
-  const uint64_t lo = (uint64_t)r.xn * p / r.xd + 1;
-  const uint64_t hi = (uint64_t)r.yn * p / r.yd + 1;
-  return hi > lo ? hi - lo : 0;
-}
-
 static void terms_host(const uint64_t *ps, size_t n, const ResidueConfig &cfg, double *t31,
                        double *t64) {
   double a = 0, b = 0;
@@ -89,8 +83,8 @@ static void terms_host(const uint64_t *ps, size_t n, const ResidueConfig &cfg, d
     for (int kind = 0; kind < 2; ++kind) {
       const int id = kind ? cfg.cong_e : cfg.cong_b;
       if (id < 0) continue;
-      const WvCongruence &c = kWvCongruences[id];
-      for (int j = 0; j < c.nrows; ++j) t += row_terms_host(kWvRows[c.row_offset + j], p);
+      const CongView &c = cong_view(id);
+      for (int j = 0; j < c.nrows; ++j) t += cong_row_terms(c.row0 + j, p);
     }
     if (p < (1ull << 30)) a += (double)t;
     else b += (double)t;

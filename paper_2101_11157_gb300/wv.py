@@ -82,6 +82,9 @@ _SIGS = {
     "wv_general_row": ([_i32, _i32] + [ctypes.POINTER(ctypes.c_uint32)] * 4 +
                        [ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_uint32),
                         ctypes.POINTER(ctypes.c_uint32)], _i32),
+    "wv_congruence_terms": ([_i32, _i32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_uint64),
+                             _i32, ctypes.POINTER(_i32)], _i32),
+    "wv_congruence_default": ([_i32], _i32),
     "wv_histogram": ([_u64, _u64, ctypes.c_uint32, _vp, _vp, _psz, _vp], _i32),
     "wv_search_ex": ([_u64, _u64, _u64, _vp, _sz, _psz, _vp, _vp, _vp, _sz, _psz,
                       ctypes.POINTER(wv_options), _vp], _i32),
@@ -293,6 +296,17 @@ def wv_congruence_info(cid: int):
     _check(load().wv_congruence_info(cid, ctypes.byref(k), ctypes.byref(n), ctypes.byref(l),
                                      ctypes.byref(nm)))
     return nm.value.decode(), k.value, n.value, l.value
+
+
+def wv_congruence_default(kind: int) -> int:
+    return load().wv_congruence_default(kind)
+
+
+def wv_congruence_terms(cid: int, row: int):
+    """[(c_k, d_k)]: the row's coefficient is sum_k c_k d_k^t."""
+    c, d, n = (ctypes.c_int64 * 64)(), (ctypes.c_uint64 * 64)(), _i32()
+    _check(load().wv_congruence_terms(cid, row, c, d, 64, ctypes.byref(n)))
+    return [(c[k], d[k]) for k in range(n.value)]
 
 
 def wv_congruence_row(cid: int, row: int):

@@ -71,3 +71,18 @@ def test_greedy_cost_never_increases():
 def test_subdivision_of_a_missing_interval_is_rejected():
     with pytest.raises(ValueError):
         C.subdivide(C.vandiver(), F(1, 4), F(1, 3), 2)
+
+
+def test_committed_generated_tables_are_the_generators_output():
+    # the first generated congruence of each kind, regenerated, equals the
+    # library's table row for row (the header is the generator's output)
+    from paper_2101_11157_gb300 import wv
+    gens = C.generated({"BB249", "EE200"})
+    ids = {wv.wv_congruence_info(i)[0]: i for i in range(wv.wv_congruence_count())}
+    for name, (cg, lhs) in gens.items():
+        cid = ids[name]
+        assert wv.wv_congruence_info(cid)[3] == lhs
+        assert wv.wv_congruence_info(cid)[2] == cg.m
+        for j, (x, y, c) in enumerate(cg.sums):
+            terms = wv.wv_congruence_terms(cid, j)
+            assert sorted(terms) == sorted((v, d) for d, v in c.items())

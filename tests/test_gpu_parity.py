@@ -105,11 +105,13 @@ def test_p1e9_window_full_launch_sampled_against_oracle(orc):
 
 
 def test_p1e9_window_cross_congruences():
-    """Every congruence family member gives the identical residue (Sec. 3, 5)."""
+    """Every congruence, printed or generated, gives the identical residue (Sec. 3, 5)."""
     ps = u64(api.sieve(*W.P1E9_WINDOW))
     ref_b, ref_e = gpu_residues(ps)
+    # the paper's 13 congruences and the 6 generated ones (the default is BB249 + EE404)
     for nb, ne in (("BB1", "EE3"), ("BB2", "EE5"), ("BB6", "EE9"), ("BB9", "EE16"),
-                   ("BB16", "EE24"), ("BB22", "EE33")):
+                   ("BB16", "EE24"), ("BB22", "EE33"), ("BB30", "EE200"), ("BB476", "EE967"),
+                   ("BB1115", "EE404")):
         gb, ge = gpu_residues(ps, {"cong_b": cong_id(nb), "cong_e": cong_id(ne)})
         assert np.array_equal(gb, ref_b), nb
         assert np.array_equal(ge, ref_e), ne

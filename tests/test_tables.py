@@ -28,13 +28,30 @@ PAPER = {
 }
 
 
+# generated congruences (greedy search over Prop. 2.1 from BB30 / EE33)
+GENERATED = {"BB249": 0, "BB476": 0, "BB1115": 0, "EE200": 1, "EE404": 1, "EE967": 1}
+
+
+def _interval(cid, j):
+    import ctypes
+    v = [ctypes.c_uint32() for _ in range(4)]
+    c = ctypes.c_int64()
+    wv.load().wv_congruence_row(cid, j, ctypes.byref(c), *[ctypes.byref(x) for x in v])
+    return tuple(x.value for x in v)
+
+
 def tables():
+    """name -> (id, kind, lhs, rows); a row is ([(c_k, d_k)], xn, xd, yn, yd)."""
     out = {}
     for cid in range(wv.wv_congruence_count()):
         name, kind, n, lhs = wv.wv_congruence_info(cid)
-        rows = [wv.wv_congruence_row(cid, j) for j in range(n)]
+        rows = [(wv.wv_congruence_terms(cid, j),) + _interval(cid, j) for j in range(n)]
         out[name] = (cid, kind, lhs, rows)
     return out
+
+
+def _coef(terms, p, e):
+    return sum(c * pow(d, -e, p) for c, d in terms) % p
 
 
 @pytest.fixture(scope="module")
@@ -43,8 +60,14 @@ def T():
 
 
 def test_all_congruences_present(T):
-    assert set(T) == set(PAPER)
-    assert len(T) == 13
+    assert set(T) == set(PAPER) | set(GENERATED)
+    assert len(T) == 13 + len(GENERATED)
+    assert [T[k][0] for k in sorted(PAPER, key=lambda k: T[k][0])] == list(range(13))
+    for name, kind in GENERATED.items():
+        assert T[name][1] == kind and len(T[name][3]) == int(name[2:])
+    # the paper's rows are plain integers (wv_congruence_row succeeds)
+    for name in PAPER:
+        assert all(len(r[0]) == 1 and r[0][0][1] == 1 for r in T[name][3])
     assert [len(T[k][3]) for k in ("BB1", "BB2", "BB6", "BB9", "BB16", "BB22", "BB30")] == \
         [1, 2, 6, 9, 16, 22, 30]
     assert [len(T[k][3]) for k in ("EE3", "EE5", "EE9", "EE16", "EE24", "EE33")] == \
@@ -76,14 +99,37 @@ def _S(p, x, y, e):
     return sum(pow(s, -e, p) for s in range(lo, hi + 1)) % p
 
 
-@pytest.mark.parametrize("name", sorted(PAPER))
+@pytest.mark.parametrize("name", sorted(GENERATED))
+def test_generated_costs_and_intervals(T, name):
+    cid, kind, lhs, rows = T[name]
+    cost = sum(Fraction(yn, yd) - Fraction(xn, xd) for _, xn, xd, yn, yd in rows)
+    # cheaper than the paper's B30 / E33, and cheaper with more sums
+    base = PAPER["BB30" if kind == 0 else "EE33"][2]
+    assert cost < base
+    prev = Fraction(0)
+    for terms, xn, xd, yn, yd in rows:
+        x, y = Fraction(xn, xd), Fraction(yn, yd)
+        assert prev <= x < y <= Fraction(1, 2) and yn < 2**26 and yd < 2**26
+        prev = y
+        for d in (xd, yd) + tuple(d for _, d in terms):  # subdivisions by d <= 8
+            for q in (2, 3, 5, 7):
+                while d % q == 0:
+                    d //= q
+            assert d == 1
+    same_kind = sorted((len(T[n][3]), sum(Fraction(r[3], r[4]) - Fraction(r[1], r[2]) for r in T[n][3]))
+                       for n, k in GENERATED.items() if k == kind)
+    assert all(b[1] < a[1] for a, b in zip(same_kind, same_kind[1:]))
+
+
+@pytest.mark.parametrize("name", sorted(PAPER) + sorted(GENERATED))
 def test_congruence_gives_definition(T, orc, name):
     cid, kind, lhs, rows = T[name]
     e = 3 if kind == 0 else 2
     for p in [p for p in range(11, 700) if is_prime(p)]:
         if lhs % p == 0:
             continue
-        rhs = sum(c * _S(p, Fraction(xn, xd), Fraction(yn, yd), e) for c, xn, xd, yn, yd in rows)
+        rhs = sum(_coef(c, p, e) * _S(p, Fraction(xn, xd), Fraction(yn, yd), e)
+                  for c, xn, xd, yn, yd in rows)
         val = rhs * pow(lhs, -1, p) % p
         ref = orc.bernoulli_def(p - 3, p) if kind == 0 else orc.euler_def(p - 3, p)
         assert val == ref, (name, p)
