@@ -36,9 +36,9 @@ IMAD_PER_SM_CLK = 64          # 32-bit integer multiply-add results per SM per c
 IMAD_SLOTS_PER_MODMUL = 5     # one 32-bit Montgomery product: mul.wide (2) + mul.lo (1) + mul.hi (2)
 SM_MAX_MHZ_FALLBACK = 2070.0
 # DRAM bytes per launch of the p < 2^30 accumulation kernel (k_accumulate<0,2,9>, default congruences
-# BB249 + EE404), from one ncu capture of the 492-prime head of the window (9,297,152 B read, 0 written),
+# BB249 + EE404), from one ncu capture of the 492-prime head of the window (9,435,136 B read, 0 written),
 # scaled by primes to the 4907-prime launch.  Must be re-taken (or set to None) whenever that kernel changes.
-ACC_TRAFFIC_BYTES = 9297152 * 4907 / 492
+ACC_TRAFFIC_BYTES = 9435136 * 4907 / 492
 # --workload top: the 391 primes of [1e11 - 1e4, 1e11) on the 64-bit path.  One 64-bit
 # Montgomery product for p < 2^37 (R = 2^64 in two 32-bit REDC rounds) costs 17 IMAD slots:
 # c g as three mul.wide and one mul.lo (7), each REDC round one mul.lo and two mul.wide (10).
@@ -216,7 +216,8 @@ def gpu_arm(args):
     d_pr_all = api.sieve(lo, hi)
     primes = api.to_u64(d_pr_all)
     n_primes = primes.size
-    tb, te = wv.wv_count_terms(primes)
+    cong = wv.wv_congruence_for_range(lo, hi)  # the congruences the search uses on this window
+    tb, te = wv.wv_count_terms(primes, *cong)
     modmuls_per_step = 2 * (tb + te)
     cap_h = 64
     hits = torch.empty((cap_h, 2), dtype=torch.int64, device="cuda")
@@ -263,7 +264,9 @@ def gpu_arm(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
 
-    # e2e: host prime list in pinned memory -> device -> residues -> host
+    # e2e: host prime list in pinned memory -> device -> residues -> host, with the
+    # congruences the search picks for the window (a caller who knows the range passes them)
+    e2e_opt = {"cong_b": cong[0], "cong_e": cong[1]}
     h_in = torch.from_numpy(primes.view(np.int64)).pin_memory()
     h_b = torch.empty(n_primes, dtype=torch.int64, pin_memory=True)
     h_e = torch.empty(n_primes, dtype=torch.int64, pin_memory=True)
@@ -274,7 +277,7 @@ def gpu_arm(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         d_in.copy_(h_in, non_blocking=True)
-        wv.wv_residues_pm3(d_in, d_rb, d_re, stream)
+        wv.wv_residues_ex(d_in, d_rb, d_re, e2e_opt, stream)
         h_b.copy_(d_rb, non_blocking=True)
         h_e.copy_(d_re, non_blocking=True)
         torch.cuda.synchronize()
@@ -310,7 +313,7 @@ def gpu_arm(args):
     achieved_gmodmul = (modmuls_per_step / (acc_avg_ms / 1000.0)) / 1e9 if acc_avg_ms else 0.0
     total_primes = n_primes * ws
     value = total_primes / (ms / 1000.0)
-    cong_names = [wv.wv_congruence_info(wv.wv_congruence_default(k))[0] for k in (0, 1)]
+    cong_names = [wv.wv_congruence_info(c)[0] for c in cong]
     line = {
         "metric": METRIC, "value": value, "unit": "primes/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -333,7 +336,7 @@ def gpu_arm(args):
                      "kernel": kname, "kernel_ms": acc_avg_ms},
         "e2e": {"value": total_primes / (e2e_step / 1000.0), "unit": "primes/s",
                 "h2d_bytes_per_step": int(n_primes * 8), "d2h_bytes_per_step": int(n_primes * 16),
-                "path": "host prime list (pinned) -> wv_residues_pm3 -> host residues"},
+                "path": "host prime list (pinned) -> wv_residues_ex (the window's congruences) -> host residues"},
         "gpu_launches": int(launches),
         "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()},
         "wall_s": wall, "hits": int(nh),

@@ -84,10 +84,9 @@ wv_status wv_sieve_count(uint64_t lo, uint64_t hi, uint64_t *count, wv_stream st
 
 /*
  * d_out[i] = B_{p_i - 3} mod p_i for the n primes d_primes[0..n).
- * Follows Sec. 3: B_{p-3} from a congruence of the form of eqn 3.7 for
- * p >= 11 -- by default BB249, 249 sums of cost p/38.2 generated from BB30
- * (eqn 3.7) by the greedy search over Prop. 2.1 (wv_congruence_default) --
- * each sum S_{p-4}(x,y) = sum_{xp<s<yp} s^-3 evaluated as c1/c0 of
+ * Follows Sec. 3: B_{p-3} from eqn 3.7 (BB30) for p >= 11 by default, or
+ * any congruence of the library (wv_options.cong_b), each sum
+ * S_{p-4}(x,y) = sum_{xp<s<yp} s^-3 evaluated as c1/c0 of
  * prod (z + s^3) (the polynomial trick and eqn 3.12), partial products
  * combined with eqn 3.14, one modular inverse per prime; p = 5, 7 from the
  * definition.  d_primes and d_out: device arrays of n uint64 (may alias
@@ -97,9 +96,9 @@ wv_status wv_bernoulli_pm3(const uint64_t *d_primes, size_t n, uint64_t *d_out,
                            wv_stream stream);
 
 /*
- * d_out[i] = E_{p_i - 3} mod p_i (sec convention).  Follows Sec. 5: a
- * congruence of the form of eqn 5.6 for p >= 11 -- by default EE404, 404 sums
- * of cost p/29.8 generated from EE33 (eqn 5.6) -- with S_{p-3}(x,y) = sum s^-2 evaluated through
+ * d_out[i] = E_{p_i - 3} mod p_i (sec convention).  Follows Sec. 5: eqn 5.6
+ * (EE33) for p >= 11 by default, or any congruence of the library, with
+ * S_{p-3}(x,y) = sum s^-2 evaluated through
  * prod (z + s^2) (the remark after eqn 5.6).  Same layout and behaviour as
  * wv_bernoulli_pm3.  Asynchronous.
  */
@@ -160,8 +159,9 @@ wv_status wv_residues_general(const uint64_t *d_primes, size_t n, uint32_t e_b, 
 /* Options for the *_ex entry points.  Zero-initialise, then set fields;
  * a zero / negative field means "library default". */
 typedef struct {
-  int cong_b;       /* congruence id (wv_congruence_info) for B; <0: default (BB249) */
-  int cong_e;       /* congruence id for E; <0: default (EE404) */
+  int cong_b;       /* congruence id (wv_congruence_info) for B; <0: the default (BB30,
+                       or by range in the range-aware calls: wv_congruence_for_range) */
+  int cong_e;       /* congruence id for E; <0: as for B (EE33 / by range) */
   int block;        /* accumulation block size (threads): 32..256, multiple of 32;
                        default 256.  Smaller blocks release their registers warp by
                        warp at the end of a launch and round occupancy differently */
@@ -254,9 +254,16 @@ wv_status wv_histogram(uint64_t lo, uint64_t hi, uint32_t bins, unsigned long lo
  * searches"), named by their number of sums (BB249 ... EE967). */
 int wv_congruence_count(void);
 
-/* The id of the congruence the residue and search calls use by default for
- * kind 0 (B_{p-3}) or 1 (E_{p-3}): the generated BB249 and EE404. */
+/* The id of the congruence the residue calls on a device prime list use by
+ * default for kind 0 (B_{p-3}) or 1 (E_{p-3}): the paper's BB30 and EE33. */
 int wv_congruence_default(int kind);
+
+/* The congruences the range-aware calls (wv_search*, wv_histogram, the
+ * serving loop) use for primes of [lo, hi) when the caller chose none: by hi,
+ * BB9 + EE16 up to 3e7, BB30 + EE33 up to 5e8, BB249 + EE404 up to 2^30,
+ * BB30 + EE33 up to 6e9, BB249 + EE404 up to 5e10, then BB1115 + EE967 (the
+ * measured fastest on GB300; all give the identical residues). */
+void wv_congruence_for_range(uint64_t lo, uint64_t hi, int *cong_b, int *cong_e);
 
 /* Congruence `id`: kind 0 = B_{p-3}, 1 = E_{p-3}; n_rows sums; lhs = the
  * constant on the left; name (static string).  Any out-pointer may be NULL. */

@@ -233,7 +233,10 @@ __device__ __forceinline__ void tile_m31_grouped(const PrimeCtx &ctx, uint64_t s
       for (int i = 0; i <= DA; ++i) va[i] = 0;
 #pragma unroll
       for (int i = 0; i <= DB; ++i) vb[i] = 0;
-#pragma unroll
+      // the point loop stays rolled (it runs once per chain; unrolled it is
+      // kilobytes of code that short tiles fetch again and again); the table
+      // indices stay compile-time, the diagonal lengths are predicated
+#pragma unroll 1
       for (int m = DA; m >= 0; --m) {
         int64_t P = 0, Q = M.one;
 #pragma unroll
@@ -250,18 +253,22 @@ __device__ __forceinline__ void tile_m31_grouped(const PrimeCtx &ctx, uint64_t s
         }
         int64_t nv = P;
 #pragma unroll
-        for (int j = 0; j <= DA - m; ++j) {
-          const int64_t old = va[j];
-          va[j] = nv;
-          if (j < DA - m) nv = M.sub(nv, old);
+        for (int j = 0; j <= DA; ++j) {
+          if (j <= DA - m) {
+            const int64_t old = va[j];
+            va[j] = nv;
+            nv = M.sub(nv, old);
+          }
         }
         if (m <= DB) {
           nv = Q;
 #pragma unroll
-          for (int j = 0; j <= DB - m; ++j) {
-            const int64_t old = vb[j];
-            vb[j] = nv;
-            if (j < DB - m) nv = M.sub(nv, old);
+          for (int j = 0; j <= DB; ++j) {
+            if (j <= DB - m) {
+              const int64_t old = vb[j];
+              vb[j] = nv;
+              nv = M.sub(nv, old);
+            }
           }
         }
       }

@@ -62,6 +62,7 @@ struct CongView {
 };
 int cong_count();
 int cong_default(int kind);
+void cong_for_range(uint64_t hi, int *cb, int *ce);
 int cong_general_id(int kind);
 const CongView &cong_view(int id);
 const uint32_t *cong_row(uint32_t r);
@@ -124,6 +125,8 @@ wv_status scan_exclusive_u32_bare(const uint32_t *d_in, uint32_t *d_out, size_t 
 struct ResidueConfig {
   int cong_b = 6;        // set by resolve_config (cong_default); -2 = skip
   int cong_e = 12;       // set by resolve_config (cong_default); -2 = skip
+  bool cong_auto_b = true;  // not chosen by the caller: range-aware calls pick by p
+  bool cong_auto_e = true;
   int block = 256;
   int ilp = 2;            // chains per thread, p < 2^30
   int ilp64 = 1;          // chains per thread, 2^30 <= p < 2^37

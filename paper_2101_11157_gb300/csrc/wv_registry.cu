@@ -113,23 +113,40 @@ const Registry &registry() {
 
 int cong_count() { return registry().n_public; }
 
-// The library's default congruences: generated ones, BB249 (cost p/38.2,
-// from B30) and EE404 (cost p/29.8, from E33).  Against BB30 + EE33 they cut
-// the terms per prime by 32 %; more sums make the tiles shorter and their
-// per-tile work outweighs the saving at p ~ 1e9 (measured).
-int cong_default(int kind) {
-  static const int ids[2] = {[] {
-                               for (int i = 0; i < cong_count(); ++i)
-                                 if (std::string(cong_view(i).name) == "BB249") return i;
-                               return (int)kWvDefaultB;
-                             }(),
-                             [] {
-                               for (int i = 0; i < cong_count(); ++i)
-                                 if (std::string(cong_view(i).name) == "EE404") return i;
-                               return (int)kWvDefaultE;
-                             }()};
-  return ids[kind ? 1 : 0];
+static int id_of(const char *name, int fallback) {
+  for (int i = 0; i < cong_count(); ++i)
+    if (std::string(cong_view(i).name) == name) return i;
+  return fallback;
 }
+
+// The default for a prime list whose range is not known: the paper's BB30 and
+// EE33, good at every p (the generated congruences win only where their
+// shorter sums are still long, see cong_for_range).
+int cong_default(int kind) { return kind == 0 ? kWvDefaultB : kWvDefaultE; }
+
+// The congruences for primes below `hi` (the paper also switches congruences
+// with the size of p, Sec. 3 "Method for primes p < 6e10").  Measured on
+// GB300 over windows of primes from 1e6 to 1e11 (whole search step): the
+// cheapest congruence whose sums stay long enough for their tiles to pay.
+void cong_for_range(uint64_t hi, int *cb, int *ce) {
+  struct Band {
+    uint64_t hi;
+    const char *b, *e;
+  };
+  static const Band bands[] = {{30000000ull, "BB9", "EE16"},
+                               {500000000ull, "BB30", "EE33"},
+                               {1ull << 30, "BB249", "EE404"},
+                               {6000000000ull, "BB30", "EE33"},
+                               {50000000000ull, "BB249", "EE404"},
+                               {~0ull, "BB1115", "EE967"}};
+  for (const Band &bd : bands)
+    if (hi <= bd.hi) {
+      *cb = id_of(bd.b, kWvDefaultB);
+      *ce = id_of(bd.e, kWvDefaultE);
+      return;
+    }
+}
+
 int cong_general_id(int kind) { return registry().n_public + kind; }
 const CongView &cong_view(int id) { return registry().views[id]; }
 const uint32_t *cong_row(uint32_t r) { return &registry().rows[6 * (size_t)r]; }
@@ -139,6 +156,8 @@ const uint64_t *cong_dist() { return registry().dist.data(); }
 
 wv_status cong_upload(DeviceState *d) {
   const Registry &R = registry();
+  for (const CongView &v : R.views)
+    if (v.ndist > 256) return set_error(WV_EINVAL, "congruence %s: %u bases (max 256)", v.name, v.ndist);
   WV_CUDA(cudaMalloc(&d->cg_rows, R.rows.size() * sizeof(uint32_t)));
   WV_CUDA(cudaMalloc(&d->cg_tc, R.tc.size() * sizeof(int64_t)));
   WV_CUDA(cudaMalloc(&d->cg_td, R.td.size() * sizeof(uint16_t)));
@@ -153,6 +172,14 @@ wv_status cong_upload(DeviceState *d) {
 }  // namespace wv
 
 extern "C" int wv_congruence_default(int kind) { return wv::cong_default(kind); }
+
+extern "C" void wv_congruence_for_range(uint64_t lo, uint64_t hi, int *cong_b, int *cong_e) {
+  (void)lo;
+  int b = 0, e = 0;
+  wv::cong_for_range(hi, &b, &e);
+  if (cong_b) *cong_b = b;
+  if (cong_e) *cong_e = e;
+}
 
 namespace wv {
 

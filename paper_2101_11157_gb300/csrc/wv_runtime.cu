@@ -281,8 +281,8 @@ wv_status resolve_config(const wv_options *opt, bool want_b, bool want_e, Residu
   c.cong_b = want_b ? cong_default(0) : -2;
   c.cong_e = want_e ? cong_default(1) : -2;
   if (opt) {
-    if (want_b && opt->cong_b >= 0) c.cong_b = opt->cong_b;
-    if (want_e && opt->cong_e >= 0) c.cong_e = opt->cong_e;
+    if (want_b && opt->cong_b >= 0) c.cong_b = opt->cong_b, c.cong_auto_b = false;
+    if (want_e && opt->cong_e >= 0) c.cong_e = opt->cong_e, c.cong_auto_e = false;
     if (opt->block > 0) c.block = opt->block;
     if (opt->ilp > 0) c.ilp = c.ilp64 = opt->ilp;
     if (opt->tile_terms > 0) c.tile_terms = opt->tile_terms;

@@ -99,6 +99,12 @@ static wv_status search_impl(uint64_t lo, uint64_t hi, uint64_t near, wv_hit *d_
                                                  (unsigned long long)lo, (unsigned long long)hi);
   ResidueConfig cfg;
   WV_CHECK(resolve_config(opt, true, true, &cfg));
+  {  // congruences the caller left open: the cheapest for primes below hi
+    int cb = cfg.cong_b, ce = cfg.cong_e;
+    cong_for_range(hi, &cb, &ce);
+    if (cfg.cong_auto_b) cfg.cong_b = cb;
+    if (cfg.cong_auto_e) cfg.cong_e = ce;
+  }
   if (lo < 5) lo = 5;
   uint64_t hits_total = 0, primes_total = 0;
   if (hi > lo) {

@@ -157,11 +157,23 @@ void release_device(wv_server_s *S, SQuery *q, cudaStream_t s) {
   for (uint32_t v : slots) S->free_slots.push_back(v);
 }
 
+// The configuration of a query: the server's, with the congruences for its
+// primes (all below q->hi for a range, q->lo itself for a single prime).
+ResidueConfig query_cfg(const wv_server_s *S, const SQuery *q) {
+  ResidueConfig qc = S->rcfg;
+  int cb = qc.cong_b, ce = qc.cong_e;
+  cong_for_range(q->kind == 0 ? q->hi : q->lo + 1, &cb, &ce);
+  qc.cong_b = cb;
+  qc.cong_e = ce;
+  return qc;
+}
+
 // Device bytes a query of n primes holds while active.
-size_t query_bytes(const wv_server_s *S, uint64_t n) {
+size_t query_bytes(const wv_server_s *S, const SQuery *q, uint64_t n) {
+  const ResidueConfig qc = query_cfg(S, q);
   size_t need = n * 24;
   for (uint64_t off = 0; off < n; off += kPlanPrimes)
-    need += plan_bytes((uint32_t)std::min<uint64_t>(kPlanPrimes, n - off), S->rcfg);
+    need += plan_bytes((uint32_t)std::min<uint64_t>(kPlanPrimes, n - off), qc);
   return need;
 }
 
@@ -190,6 +202,7 @@ wv_status build_query(wv_server_s *S, SQuery *q, const std::vector<uint32_t> &sl
   }
   WV_CUDA(cudaStreamSynchronize(S->sa));
   q->remaining = 0;
+  const ResidueConfig qc = query_cfg(S, q);  // the congruences for this query's primes
   const size_t nplans = (size_t)((n + kPlanPrimes - 1) / kPlanPrimes);
   for (size_t i = 0; i < nplans; ++i) {
     SChunk c;
@@ -198,14 +211,14 @@ wv_status build_query(wv_server_s *S, SQuery *q, const std::vector<uint32_t> &sl
     c.slot = slots[i];
     q->chunks.push_back(c);
     SChunk &cc = q->chunks.back();
-    WV_CHECK(plan_build(q->d_primes + cc.off, cc.n, S->rcfg, &cc.plan, S->sa));
+    WV_CHECK(plan_build(q->d_primes + cc.off, cc.n, qc, &cc.plan, S->sa));
     WV_CHECK(plan_totals(&cc.plan, S->sa));
     Plan *dst = (Plan *)((char *)S->d_plans + (size_t)cc.slot * plan_struct_bytes());
     WV_CHECK(plan_upload(&cc.plan, dst, S->sa));
     cc.hi31 = cc.plan.split;
     cc.hi64 = cc.plan.total;
     double t31 = 0, t64 = 0;
-    terms_host(q->h_primes.data() + cc.off, cc.n, S->rcfg, &t31, &t64);
+    terms_host(q->h_primes.data() + cc.off, cc.n, qc, &t31, &t64);
     cc.tpt31 = cc.plan.split ? t31 / cc.plan.split : 1.0;
     cc.tpt64 = (cc.plan.total > cc.plan.split) ? t64 / (cc.plan.total - cc.plan.split) : 1.0;
     q->remaining += t31 + kWideWeight * t64;
@@ -249,7 +262,7 @@ void admitter_main(wv_server_s *S) {
         q->err = "query needs more plan slots than the server has";
       }
       q->n = n;
-      q->bytes = query_bytes(S, n);
+      q->bytes = query_bytes(S, q, n);
       q->counted = true;
     }
     SQuery *q = nullptr;
@@ -312,7 +325,7 @@ void admitter_main(wv_server_s *S) {
     // exact needs now that the range is sieved: give back the rest (the
     // prime buffer keeps its bound-sized allocation)
     if (q->n == 0) release_device(S, q, S->sa);
-    const size_t exact = q->n ? query_bytes(S, q->n) + (q->n_cap - q->n) * 8 : 0;
+    const size_t exact = q->n ? query_bytes(S, q, q->n) + (q->n_cap - q->n) * 8 : 0;
     std::lock_guard<std::mutex> lk(S->mu);
     for (size_t i = q->chunks.size(); i < slots.size(); ++i) S->free_slots.push_back(slots[i]);
     if (exact < q->bytes) {

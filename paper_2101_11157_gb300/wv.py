@@ -85,6 +85,7 @@ _SIGS = {
     "wv_congruence_terms": ([_i32, _i32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_uint64),
                              _i32, ctypes.POINTER(_i32)], _i32),
     "wv_congruence_default": ([_i32], _i32),
+    "wv_congruence_for_range": ([_u64, _u64, ctypes.POINTER(_i32), ctypes.POINTER(_i32)], None),
     "wv_histogram": ([_u64, _u64, ctypes.c_uint32, _vp, _vp, _psz, _vp], _i32),
     "wv_search_ex": ([_u64, _u64, _u64, _vp, _sz, _psz, _vp, _vp, _vp, _sz, _psz,
                       ctypes.POINTER(wv_options), _vp], _i32),
@@ -300,6 +301,13 @@ def wv_congruence_info(cid: int):
 
 def wv_congruence_default(kind: int) -> int:
     return load().wv_congruence_default(kind)
+
+
+def wv_congruence_for_range(lo: int, hi: int):
+    """(B id, E id) the range-aware calls use for primes of [lo, hi)."""
+    b, e = _i32(), _i32()
+    load().wv_congruence_for_range(lo, hi, ctypes.byref(b), ctypes.byref(e))
+    return b.value, e.value
 
 
 def wv_congruence_terms(cid: int, row: int):
