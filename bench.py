@@ -44,10 +44,11 @@ ACC_TRAFFIC_BYTES = 9153280 * 4907 / 492
 # c g as three mul.wide and one mul.lo (7), each REDC round one mul.lo and two mul.wide (10).
 TOP_LO, TOP_WIDTH = 10**11 - 10**4, 10**4
 IMAD_SLOTS_PER_MODMUL64 = 17
-# DRAM bytes per launch of the 64-bit accumulation kernel (k_accumulate_m64cap<9,128>), from one ncu
-# capture of the 17-prime head of the window below 1e11 (1,231,104 B read, 0 written), scaled by primes
-# to the 391-prime launch.  Must be re-taken (or set to None) whenever that kernel changes.
-ACC64_TRAFFIC_BYTES = 1231104 * 391 / 17
+# DRAM bytes per launch of the 64-bit accumulation kernel (k_accumulate_m64cap<9,128>, congruences
+# BB1115 + EE967), from one ncu capture of the 17-prime head of the window below 1e11 (1,959,936 B read,
+# 0 written), scaled by primes to the 391-prime launch.  Must be re-taken (or set to None) whenever that
+# kernel changes.
+ACC64_TRAFFIC_BYTES = 1959936 * 391 / 17
 
 
 def dist_env():
