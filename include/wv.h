@@ -166,7 +166,7 @@ typedef struct {
                        default 256.  Smaller blocks release their registers warp by
                        warp at the end of a launch and round occupancy differently */
   int ilp;          /* independent accumulator chains per thread for p < 2^30: 1, 2 or 4
-                       (4 only with arith >= 9; default 2).  The grouped 64-bit forms
+                       (4 only with arith 9..23; default 2).  The grouped 64-bit forms
                        (arith >= 9) run one chain per thread; the single-term 64-bit
                        form takes this value too */
   int tile_terms;   /* target terms per warp tile (default 2^20) */
@@ -174,7 +174,7 @@ typedef struct {
                        call with few primes gets more and shorter tiles (up to 64 per
                        sum) so that one launch still holds ~1e5 tiles */
   int blocks_per_sm;/* persistent grid = SMs x this */
-  int arith;        /* hot-loop formulation, 1..23 (default 9: grouped terms, REDC folded
+  int arith;        /* hot-loop formulation, 1..23 or 25..28 (default 9: grouped terms, REDC folded
                        into wide multiply-adds, on both paths).  1..8 select the single-
                        term and intermediate forms of the 32-bit path for ablation, and
                        any value below 9 the single-term 64-bit path; 10..22 select other
@@ -182,7 +182,12 @@ typedef struct {
                        choices, register budget; one chain per thread) for ablation,
                        with formulation 9 on the 32-bit path; 23 selects the paper's own
                        arithmetic on both paths (plain residues, eqn 3.15 split products,
-                       remainders from a double-precision quotient, single terms) */
+                       remainders from a double-precision quotient, single terms);
+                       25..28 are formulation 9 on the 32-bit path with none, 4, 6 or
+                       all of a group's difference-table additions written as ALU-only
+                       three-input adds (9 itself: 4 of a Bernoulli group's 9 and 2 of
+                       an Euler group's 10; the 64-bit path runs 9; ilp 1 or 2).
+                       Other values: WV_EINVAL */
   int reserved[8];
 } wv_options;
 

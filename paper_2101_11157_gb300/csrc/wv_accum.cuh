@@ -178,8 +178,14 @@ __device__ __forceinline__ void tile_m31(const PrimeCtx &ctx, uint64_t start, ui
 //   c0 <- c0 G0,   c1 <- c1 G0 + c0 G1.
 // The tables are built so that G0 and R G1 carry the same power of R; as in
 // the single-term step the ratio c1/c0 then accumulates R * sum t^-1.
+//
+// NF of the table additions per group (the G0 table's from the low order up,
+// then G1's) are written as an inline PTX block whose a + b - p is a
+// three-input add, which only the integer ALU executes.  The others are
+// plain C; the compiler may place their two-input adds on the multiply pipe,
+// which the products already fill.  NF moves work from that pipe to the ALU.
 
-template <int ILP, bool CUBES, int AR>
+template <int ILP, bool CUBES, int AR, int NF = 0>
 __device__ __forceinline__ void tile_m31_grouped(const PrimeCtx &ctx, uint64_t start, uint64_t n,
                                                  int64_t &r0, int64_t &r1) {
   constexpr int K = CUBES ? 2 : 3;     // terms per group
@@ -285,6 +291,20 @@ __device__ __forceinline__ void tile_m31_grouped(const PrimeCtx &ctx, uint64_t s
     const uint32_t y = (uint32_t)a + (uint32_t)b - up;
     a = (int32_t)min(x, y);
   };
+  // the same modular add as one PTX block: a - p + b (a three-input add once
+  // fused), a + b and their unsigned minimum; opaque to the front end, so
+  // the two sums are not merged into a shared a + b
+  auto modadd_alu = [&](int32_t &a, int32_t b) {
+    uint32_t r;
+    asm("{\n\t.reg .u32 t;\n\t"
+        "add.u32 t, %1, %3;\n\t"
+        "add.u32 t, t, %2;\n\t"
+        "add.u32 %0, %1, %2;\n\t"
+        "min.u32 %0, %0, t;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)a), "r"((uint32_t)b), "r"((uint32_t)np));
+    a = (int32_t)r;
+  };
 #pragma unroll 1
   for (uint64_t g = 0; g < G; ++g) {
 #pragma unroll
@@ -311,9 +331,15 @@ __device__ __forceinline__ void tile_m31_grouped(const PrimeCtx &ctx, uint64_t s
       }
       // step both difference tables by one group (low order first)
 #pragma unroll
-      for (int j = 0; j < DA; ++j) modadd(ga[k][j], ga[k][j + 1]);
+      for (int j = 0; j < DA; ++j) {
+        if (j < NF) modadd_alu(ga[k][j], ga[k][j + 1]);
+        else modadd(ga[k][j], ga[k][j + 1]);
+      }
 #pragma unroll
-      for (int j = 0; j < DB; ++j) modadd(gb[k][j], gb[k][j + 1]);
+      for (int j = 0; j < DB; ++j) {
+        if (DA + j < NF) modadd_alu(gb[k][j], gb[k][j + 1]);
+        else modadd(gb[k][j], gb[k][j + 1]);
+      }
     }
   }
   // the last (at most K) terms of each chain one at a time (eqn 3.12)
@@ -851,6 +877,12 @@ __device__ __forceinline__ void process_tile(const Plan &P, uint32_t g) {
   int64_t r0, r1;
   // single-term form used beside the grouped one
   constexpr int AS = (AR == 5 || AR >= 8) ? 4 : AR;
+  // ALU-only table additions per group of the 32-bit grouped form, for the
+  // Bernoulli (cubes, 9 additions per group) and Euler (squares, 10) sums:
+  // 4 and 2 in the default 9 (the fastest on GB300 of 0, 2..6 and all);
+  // 25: none, 26: 4 and 4, 27: 6 and 6, 28: all (ablation)
+  constexpr int NFC = AR == 9 ? 4 : AR == 26 ? 4 : AR == 27 ? 6 : AR == 28 ? 10 : 0;
+  constexpr int NFS = AR == 9 ? 2 : AR == 26 ? 4 : AR == 27 ? 6 : AR == 28 ? 10 : 0;
   const bool grp_ok = n >= 32ull * ILP * kGroupMinChain;
   if (AR == 24) {
     tile_general(ctx, start, n, j < P.rows_b ? P.gen_e_b : P.gen_e_e, r0, r1);
@@ -861,9 +893,9 @@ __device__ __forceinline__ void process_tile(const Plan &P, uint32_t g) {
     if (j < P.rows_b) tile_m31_grouped<ILP, true, 5>(ctx, start, n, r0, r1);
     else tile_m31_grouped<ILP, false, 5>(ctx, start, n, r0, r1);
   } else if (!WIDE && AR >= 7 && grp_ok && j >= P.rows_b) {
-    tile_m31_grouped<ILP, false, 7>(ctx, start, n, r0, r1);
+    tile_m31_grouped<ILP, false, 7, NFS>(ctx, start, n, r0, r1);
   } else if (!WIDE && AR >= 9 && grp_ok) {
-    tile_m31_grouped<ILP, true, 7>(ctx, start, n, r0, r1);
+    tile_m31_grouped<ILP, true, 7, NFC>(ctx, start, n, r0, r1);
   } else if (!WIDE) {
     if (j < P.rows_b) tile_m31<ILP, true, AS>(ctx, start, n, r0, r1);
     else tile_m31<ILP, false, AS>(ctx, start, n, r0, r1);
@@ -982,6 +1014,8 @@ AccKernel acc_kernel_m31(int arith, int ilp);
 AccKernel acc_kernel_m64(int arith, int ilp);
 // 64-bit path formulations kept for ablation (arith 10..22), one chain per thread
 AccKernel acc_kernel_m64x(int arith, int ilp);
+// 32-bit path: formulation 9 with ALU-only table additions (arith 25..28), ILP 1 or 2
+AccKernel acc_kernel_m31x(int arith, int ilp);
 // serving-loop epoch kernels (formulation 9; one chain per thread on the 64-bit path)
 EpochKernel epoch_kernel(bool wide, int ilp);
 EpochKernel epoch_mixed_kernel(int ilp31, int ilp64);

@@ -268,6 +268,7 @@ AccKernel acc_kernel_m31(int ar, int ilp) {
    : ar == 5 ? k_accumulate<false, I, 5> : ar == 6 ? k_accumulate<false, I, 6>  \
    : ar == 7 ? k_accumulate<false, I, 7> : ar == 8 ? k_accumulate<false, I, 8>  \
    : k_accumulate<false, I, 9>)
+  if (ar >= 25) return acc_kernel_m31x(ar, ilp);
   if (ilp == 1) return WV_PICK(1);
   if (ilp == 2) return WV_PICK(2);
 #undef WV_PICK
@@ -279,8 +280,9 @@ static wv_status launch_accumulate(const Plan &P, const ResidueConfig &cfg, int 
   const char *name = WIDE ? "accumulate_m64" : "accumulate_m31";
   AccKernel kern = nullptr;
   if (WIDE) {
-    kern = cfg.arith > 9 ? acc_kernel_m64x(cfg.arith, cfg.ilp64)
-                         : acc_kernel_m64(cfg.arith == 9 ? 9 : 1, cfg.ilp64);
+    // arith 25..28 vary the 32-bit path only; the 64-bit path runs its default
+    kern = (cfg.arith > 9 && cfg.arith <= 24) ? acc_kernel_m64x(cfg.arith, cfg.ilp64)
+                                               : acc_kernel_m64(cfg.arith >= 9 ? 9 : 1, cfg.ilp64);
   } else {
     kern = acc_kernel_m31(cfg.arith >= 23 ? cfg.arith : cfg.arith > 9 ? 9 : cfg.arith, cfg.ilp);
   }

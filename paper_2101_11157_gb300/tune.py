@@ -9,6 +9,7 @@ sequence of ``wv_batch_create``) and caches its choice per GPU and workload.
 
     python -m paper_2101_11157_gb300.tune --lo 1062200000 --hi 1062300000 --grid arith
     python -m paper_2101_11157_gb300.tune --lo 1062200000 --hi 1062300000 --grid shape --save
+    python -m paper_2101_11157_gb300.tune --grid alu --range-congruences
 """
 from __future__ import annotations
 
@@ -35,6 +36,8 @@ GRIDS = {
     "m64": [{"arith": a} for a in (9, *range(12, 24))],
     # the paper's own arithmetic (eqn 3.15, double-precision quotients) against the default
     "paper": [{"arith": 9}, {"arith": 23}],
+    # the 32-bit grouped form with 0 / 4 / 6 / all of its table additions ALU-only (9: 4 and 2)
+    "alu": [{"arith": a, "ilp": i} for a, i in itertools.product((9, 25, 26, 27, 28), (2, 1))],
     "block": [{"block": b} for b in (32, 64, 128, 256)],
     "default": [{}],
 }
@@ -58,10 +61,12 @@ def _time(d, rb, re, opt, reps):
 def sweep(primes, grid, reps: int = 2):
     """Yield dicts {options, acc_ms, terms_per_clk_sm, identical} for each shape."""
     import torch
+    grid = list(grid)
     d = torch.from_numpy(np.asarray(primes, dtype=np.uint64).view(np.int64)).cuda()
     rb, re = torch.empty_like(d), torch.empty_like(d)
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
-    tb, te = wv.wv_count_terms(np.asarray(primes, dtype=np.uint64))
+    cong = next(((o.get("cong_b", -1), o.get("cong_e", -1)) for o in grid), (-1, -1))
+    tb, te = wv.wv_count_terms(np.asarray(primes, dtype=np.uint64), *cong)
     ref = None
     for opt in grid:
         ms = _time(d, rb, re, opt, reps)
@@ -165,13 +170,20 @@ def main():
     ap.add_argument("--grid", default="shape", choices=sorted(GRIDS))
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--save", action="store_true", help="record the fastest shape in the cache")
+    ap.add_argument("--range-congruences", action="store_true",
+                    help="sum the congruences the range-aware calls pick for [lo, hi) "
+                         "(default: those of the prime-list calls, BB30 and EE33)")
     args = ap.parse_args()
     import torch
 
     from . import api
     primes = api.to_u64(api.sieve(args.lo, args.hi))
+    grid = GRIDS[args.grid]
+    if args.range_congruences:
+        cb, ce = wv.wv_congruence_for_range(args.lo, args.hi)
+        grid = [{**o, "cong_b": cb, "cong_e": ce} for o in grid]
     rows = []
-    for r in sweep(primes, GRIDS[args.grid], args.reps):
+    for r in sweep(primes, grid, args.reps):
         print(json.dumps(r), flush=True)
         rows.append(r)
     bad = [r for r in rows if not r["identical"]]
