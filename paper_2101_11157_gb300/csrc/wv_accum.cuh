@@ -865,7 +865,6 @@ __device__ __forceinline__ void tile_general(const PrimeCtx &ctx, uint64_t start
 template <bool WIDE, int ILP, int AR>
 __device__ __forceinline__ void process_tile(const Plan &P, uint32_t g) {
   const int lane = threadIdx.x & 31;
-  const uint32_t nsegs = P.n * P.rows_pp;
   // segment owning tile g (the planner's tile -> segment map)
   const uint32_t s = __ldg(&P.tile_seg[g]);
   const uint32_t slot = s / P.rows_pp, j = s - slot * P.rows_pp;
@@ -1014,6 +1013,11 @@ AccKernel acc_kernel_m31(int arith, int ilp);
 AccKernel acc_kernel_m64(int arith, int ilp);
 // 64-bit path formulations kept for ablation (arith 10..22), one chain per thread
 AccKernel acc_kernel_m64x(int arith, int ilp);
+// forms 16..18, 19..21 and 22..24, each its own translation unit
+// (acc_kernel_m64x falls through to y, y to z, z to w)
+AccKernel acc_kernel_m64y(int arith, int ilp);
+AccKernel acc_kernel_m64z(int arith, int ilp);
+AccKernel acc_kernel_m64w(int arith, int ilp);
 // 32-bit path: formulation 9 with ALU-only table additions (arith 25..28), ILP 1 or 2
 AccKernel acc_kernel_m31x(int arith, int ilp);
 // serving-loop epoch kernels (formulation 9; one chain per thread on the 64-bit path)
