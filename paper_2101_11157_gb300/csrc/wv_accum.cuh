@@ -221,20 +221,25 @@ __device__ __forceinline__ void tile_m31_grouped(const PrimeCtx &ctx, uint64_t s
     // c1 / c0 unchanged; points from the top down (x^e by backward
     // differences), folded into the diagonals: e_j <- (-1)^j D^j.
     {
-      const int64_t pp = (int64_t)p;
-      int64_t xr = (int64_t)((s + (uint64_t)(K * (DA + 1) - 1)) % ctx.p);
-      const int64_t sq = M.mulmod(xr, xr);
-      int64_t t, d1, d2;
+      // 32-bit residues in [0, p) throughout (p < 2^30); s < p, so the top
+      // point needs at most one subtraction of p
+      const M31Set S(ctx);
+      uint64_t x64 = s + (uint64_t)(K * (DA + 1) - 1);
+      x64 = x64 >= ctx.p ? (x64 >= 2 * ctx.p ? x64 % ctx.p : x64 - ctx.p) : x64;
+      const uint32_t xr = (uint32_t)x64;
+      const uint32_t sq = S.mulmod(xr, xr);
+      const uint32_t x2 = S.add(xr, xr);
+      uint32_t t, d1, d2;
       if (EX == 3) {  // x^3, 3x^2 - 3x + 1, 6x - 6, 6
-        t = M.mulmod(sq, xr);
-        d1 = ((3 * sq + 1) % pp + pp - (3 * xr) % pp) % pp;
-        d2 = (6 * xr + 6 * pp - 6) % pp;
+        t = S.mulmod(sq, xr);
+        d1 = S.sub(S.add(S.add(S.add(sq, sq), sq), S.c1), S.add(x2, xr));
+        d2 = S.sub(S.add(S.add(x2, xr), S.add(x2, xr)), S.c6);
       } else {        // x^2, 2x - 1, 2
         t = sq;
-        d1 = (2 * xr + pp - 1) % pp;
-        d2 = 2;
+        d1 = S.sub(x2, S.c1);
+        d2 = S.c2;
       }
-      int64_t va[DA + 1], vb[DB + 1];
+      uint32_t va[DA + 1], vb[DB + 1];
 #pragma unroll
       for (int i = 0; i <= DA; ++i) va[i] = 0;
 #pragma unroll
@@ -244,26 +249,26 @@ __device__ __forceinline__ void tile_m31_grouped(const PrimeCtx &ctx, uint64_t s
       // indices stay compile-time, the diagonal lengths are predicated
 #pragma unroll 1
       for (int m = DA; m >= 0; --m) {
-        int64_t P = 0, Q = M.one;
+        uint32_t P = 0, Q = S.one;
 #pragma unroll
         for (int i = 0; i < K; ++i) {
           if (i == 0) {
             P = t;
           } else {
-            Q = M.add(M.mul(Q, t), P);
-            P = M.mul(P, t);
+            Q = S.add(S.mul(Q, t), P);
+            P = S.mul(P, t);
           }
-          t = M.sub(t, d1);
-          d1 = M.sub(d1, d2);
-          if (EX == 3) d2 = M.sub(d2, 6 % pp);
+          t = S.sub(t, d1);
+          d1 = S.sub(d1, d2);
+          if (EX == 3) d2 = S.sub(d2, S.c6);
         }
-        int64_t nv = P;
+        uint32_t nv = P;
 #pragma unroll
         for (int j = 0; j <= DA; ++j) {
           if (j <= DA - m) {
-            const int64_t old = va[j];
+            const uint32_t old = va[j];
             va[j] = nv;
-            nv = M.sub(nv, old);
+            nv = S.sub(nv, old);
           }
         }
         if (m <= DB) {
@@ -271,17 +276,17 @@ __device__ __forceinline__ void tile_m31_grouped(const PrimeCtx &ctx, uint64_t s
 #pragma unroll
           for (int j = 0; j <= DB; ++j) {
             if (j <= DB - m) {
-              const int64_t old = vb[j];
+              const uint32_t old = vb[j];
               vb[j] = nv;
-              nv = M.sub(nv, old);
+              nv = S.sub(nv, old);
             }
           }
         }
       }
 #pragma unroll
-      for (int j = 0; j <= DA; ++j) ga[k][j] = (int32_t)((j & 1) ? (va[j] ? pp - va[j] : 0) : va[j]);
+      for (int j = 0; j <= DA; ++j) ga[k][j] = (int32_t)((j & 1) ? S.sub(0, va[j]) : va[j]);
 #pragma unroll
-      for (int j = 0; j <= DB; ++j) gb[k][j] = (int32_t)((j & 1) ? (vb[j] ? pp - vb[j] : 0) : vb[j]);
+      for (int j = 0; j <= DB; ++j) gb[k][j] = (int32_t)((j & 1) ? S.sub(0, vb[j]) : vb[j]);
     }
     c0[k] = (int32_t)ctx.one;
     c1[k] = 0;
@@ -305,8 +310,9 @@ __device__ __forceinline__ void tile_m31_grouped(const PrimeCtx &ctx, uint64_t s
         : "r"((uint32_t)a), "r"((uint32_t)b), "r"((uint32_t)np));
     a = (int32_t)r;
   };
+  const uint32_t G32 = (uint32_t)G;  // chains hold fewer than 2^32 groups (tiles < 2^32 terms)
 #pragma unroll 1
-  for (uint64_t g = 0; g < G; ++g) {
+  for (uint32_t g = 0; g < G32; ++g) {
 #pragma unroll
     for (int k = 0; k < ILP; ++k) {
       const int32_t A = ga[k][0], B = gb[k][0];
@@ -925,7 +931,7 @@ __device__ __forceinline__ void accumulate_loop(const Plan &P) {
 }
 
 template <bool WIDE, int ILP, int AR>
-__global__ void __launch_bounds__(kAccThreads) k_accumulate(Plan P) {
+__global__ void __launch_bounds__(kAccThreads, 3) k_accumulate(Plan P) {
   accumulate_loop<WIDE, ILP, AR>(P);
 }
 

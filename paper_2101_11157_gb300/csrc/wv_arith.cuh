@@ -127,6 +127,33 @@ __device__ __forceinline__ int32_t m31_mul(int32_t a, int32_t b, int32_t p, uint
   return m31_canon(m31_redc(a, b, p, q), p);
 }
 
+// Branch-free p < 2^30 residue arithmetic for per-chain set-up: canonical
+// values in [0, p) as unsigned words; add and subtract by the unsigned
+// minimum of the two candidates (the wrapped one is the larger).
+struct M31Set {
+  int32_t p;
+  uint32_t q;
+  uint32_t one, r2, c1, c2, c6;  // R, R^2 mod p; the plain constants 1, 2, 6 mod p
+  __device__ __forceinline__ explicit M31Set(const PrimeCtx &c)
+      : p((int32_t)c.p), q((uint32_t)c.q), one((uint32_t)c.one), r2((uint32_t)c.r2),
+        c1(c.p > 1 ? 1u : 0u), c2(c.p > 2 ? 2u : (uint32_t)(2 % c.p)),
+        c6(c.p > 6 ? 6u : (uint32_t)(6 % c.p)) {}
+  __device__ __forceinline__ uint32_t mul(uint32_t a, uint32_t b) const {  // a b R^-1
+    return (uint32_t)m31_mul((int32_t)a, (int32_t)b, p, q);
+  }
+  __device__ __forceinline__ uint32_t mulmod(uint32_t a, uint32_t b) const {  // a b
+    return mul(mul(a, b), r2);
+  }
+  __device__ __forceinline__ uint32_t add(uint32_t a, uint32_t b) const {
+    const uint32_t x = a + b;
+    return min(x, x - (uint32_t)p);
+  }
+  __device__ __forceinline__ uint32_t sub(uint32_t a, uint32_t b) const {
+    const uint32_t x = a - b;
+    return min(x, x + (uint32_t)p);
+  }
+};
+
 // ---------------------------------------------------------------- M64
 __device__ __forceinline__ int64_t m64_redc(int64_t a, int64_t b, int64_t p, uint64_t q) {
   int64_t hi = __mul64hi(a, b);
