@@ -36,9 +36,9 @@ IMAD_PER_SM_CLK = 64          # 32-bit integer multiply-add results per SM per c
 IMAD_SLOTS_PER_MODMUL = 5     # one 32-bit Montgomery product: mul.wide (2) + mul.lo (1) + mul.hi (2)
 SM_MAX_MHZ_FALLBACK = 2070.0
 # DRAM bytes per launch of the p < 2^30 accumulation kernel (k_accumulate<0,2,9>, default congruences
-# BB249 + EE404), from one ncu capture of the 492-prime head of the window (9,153,024 B read, 0 written),
+# BB249 + EE404), from one ncu capture of the 492-prime head of the window (9,202,688 B read, 0 written),
 # scaled by primes to the 4907-prime launch.  Must be re-taken (or set to None) whenever that kernel changes.
-ACC_TRAFFIC_BYTES = 9153024 * 4907 / 492
+ACC_TRAFFIC_BYTES = 9202688 * 4907 / 492
 # --workload top: the 391 primes of [1e11 - 1e4, 1e11) on the 64-bit path.  One 64-bit
 # Montgomery product for p < 2^37 (R = 2^64 in two 32-bit REDC rounds) costs 17 IMAD slots:
 # c g as three mul.wide and one mul.lo (7), each REDC round one mul.lo and two mul.wide (10).
