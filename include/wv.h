@@ -21,6 +21,8 @@
  *  - Supported primes: 5 <= p < 2^37 (WV_P_MAX).  Primality is the caller's
  *    contract for d_primes; an odd p outside the range, or an even p, gives
  *    WV_RESIDUE_INVALID in its output slot (the call itself still succeeds).
+ *    wv_options.check_primes makes the calls verify it (a composite's slot
+ *    is then WV_RESIDUE_INVALID too); wv_is_prime is the same test on the host.
  *  - The Euler numbers use the sec convention (E_2 = +1), as the paper does.
  */
 #ifndef WV_H
@@ -57,6 +59,12 @@ const char *wv_version(void);
 
 /* Message for the last failing call made on this host thread ("" if none). */
 const char *wv_last_error(void);
+
+/* 1 if n is a prime, else 0; host only, no device work.  Deterministic
+ * Miller-Rabin with the bases 2..17, exact for n < 2^37 (Jaeschke 1993);
+ * n >= 2^37 returns -1 (outside the supported range).  The same test that
+ * wv_options.check_primes runs on the device. */
+int wv_is_prime(uint64_t n);
 
 /* ---------------------------------------------------------------------- */
 /* a1: prime enumeration (the paper enumerates primes over intervals with */
@@ -188,7 +196,12 @@ typedef struct {
                        three-input adds (9 itself: 4 of a Bernoulli group's 9 and 2 of
                        an Euler group's 10; the 64-bit path runs 9; ilp 1 or 2).
                        Other values: WV_EINVAL */
-  int reserved[8];
+  int check_primes; /* nonzero: the planner also verifies that every input is a prime
+                       (deterministic Miller-Rabin, bases 2..17, exact below 2^37); a
+                       composite gets WV_RESIDUE_INVALID in its slot like an input
+                       outside the supported range.  Default 0: primality stays the
+                       caller's contract and a composite's slot is unspecified */
+  int reserved[7];
 } wv_options;
 
 /* wv_residues_pm3 with explicit congruence choice and launch shape.

@@ -23,6 +23,7 @@ constexpr uint64_t kGroupMinChain = 48;   // grouped path only for chains of >= 
 
 struct Plan {
   uint32_t n;                   // primes in this chunk
+  uint32_t check;               // nonzero: the planner verifies each input's primality
   uint32_t rows_b, rows_e, rows_pp;
   uint32_t tile_terms, max_tiles;
   const uint64_t *primes;       // caller's primes (chunk base)

@@ -138,6 +138,7 @@ struct ResidueConfig {
   uint32_t gen_e_b = 0;   // general index: B_{p-e} (e odd); 0 = the B_{p-3} forms
   uint32_t gen_e_e = 0;   // general index: E_{p-1-e} (e even); 0 = the E_{p-3} forms
   size_t chunk = 0;       // primes per launch sequence (0: library default 16384)
+  bool check_primes = false;  // planner verifies primality (composites -> invalid slot)
 };
 wv_status resolve_config(const wv_options *opt, bool want_b, bool want_e, ResidueConfig *cfg);
 

@@ -29,6 +29,7 @@
 // c0 and c1 drift by powers of R, but the ratio c1/c0 always equals S * R
 // (true initially for (c0, c1) = (R, 0) and preserved by both eqn 3.12 steps
 // and by eqn 3.14 under REDC).  The finaliser therefore divides by R once.
+#include "wv_prime.cuh"
 #include <stdio.h>
 #include <string.h>
 
@@ -80,6 +81,7 @@ __global__ void k_plan_scatter(Plan P) {
   const uint32_t slot = P.bk[64 + b] + atomicAdd(&P.bk[128 + b], 1u);
   PrimeCtx c;
   bool valid = (p >= 5) && (p & 1) && (p < kPMax);
+  if (valid && P.check) valid = is_prime37(p);
   if (valid && p >= 11) {
     c = make_ctx(p, i);
   } else {
@@ -305,6 +307,7 @@ wv_status residues_device(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,
   WV_CHECK(device_state(&dev));
   Plan P;
   memset(&P, 0, sizeof P);
+  P.check = cfg.check_primes ? 1u : 0u;
   const bool do_b = (cfg.gen_e_b ? true : cfg.cong_b >= 0) && d_out_b;
   const bool do_e = (cfg.gen_e_e ? true : cfg.cong_e >= 0) && d_out_e;
   if (!do_b && !do_e) return WV_OK;
@@ -434,6 +437,7 @@ wv_status plan_build(const uint64_t *d_primes, uint32_t n, const ResidueConfig &
   ps->host = new Plan();
   Plan &P = *ps->host;
   memset(&P, 0, sizeof P);
+  P.check = cfg.check_primes ? 1u : 0u;
   fill_rows(P, cfg, dev);
   tile_shape(cfg, n, P.rows_pp, &P.tile_terms, &P.max_tiles);
   const size_t ns = (size_t)n * P.rows_pp;

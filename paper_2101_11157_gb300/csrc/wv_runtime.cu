@@ -1,5 +1,6 @@
 // wv_runtime.cu -- errors, per-device state, scratch pool, launch profiling,
 // device-wide scans, and the host-side congruence-table API.
+#include "wv_prime.cuh"
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -290,6 +291,7 @@ wv_status resolve_config(const wv_options *opt, bool want_b, bool want_e, Residu
     if (opt->tile_terms > 0 || opt->max_tiles > 0) c.tiles_auto = false;
     if (opt->blocks_per_sm > 0) c.blocks_per_sm = opt->blocks_per_sm;
     if (opt->arith > 0) c.arith = opt->arith;
+    c.check_primes = opt->check_primes != 0;
   }
   if (c.cong_b >= 0 && (c.cong_b >= cong_count() || cong_view(c.cong_b).kind != 0))
     return set_error(WV_EINVAL, "cong_b=%d is not a Bernoulli congruence", c.cong_b);
@@ -317,6 +319,11 @@ using namespace wv;
 extern "C" {
 
 const char *wv_version(void) { return "wv 0.1 (sm_103a)"; }
+
+int wv_is_prime(uint64_t n) {
+  if (n >= WV_P_MAX) return -1;
+  return wv::is_prime37(n) ? 1 : 0;
+}
 const char *wv_last_error(void) { return g_err.c_str(); }
 
 int wv_congruence_count(void) { return cong_count(); }

@@ -58,7 +58,7 @@ class wv_options(ctypes.Structure):
     _fields_ = [("cong_b", ctypes.c_int), ("cong_e", ctypes.c_int), ("block", ctypes.c_int),
                 ("ilp", ctypes.c_int), ("tile_terms", ctypes.c_int), ("max_tiles", ctypes.c_int),
                 ("blocks_per_sm", ctypes.c_int), ("arith", ctypes.c_int),
-                ("reserved", ctypes.c_int * 8)]
+                ("check_primes", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
 
 
 _lock = threading.Lock()
@@ -69,6 +69,7 @@ _pu64, _psz = ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_size_t)
 _SIGS = {
     "wv_version": ([], ctypes.c_char_p),
     "wv_last_error": ([], ctypes.c_char_p),
+    "wv_is_prime": ([_u64], _i32),
     "wv_sieve": ([_u64, _u64, _vp, _sz, _psz, _vp], _i32),
     "wv_sieve_count": ([_u64, _u64, _pu64, _vp], _i32),
     "wv_bernoulli_pm3": ([_vp, _sz, _vp, _vp], _i32),
@@ -188,6 +189,11 @@ def wv_version() -> str:
 
 def wv_last_error() -> str:
     return load().wv_last_error().decode()
+
+
+def wv_is_prime(n: int) -> int:
+    """1 if n is prime, 0 if not, -1 for n >= 2^37 (host only)."""
+    return load().wv_is_prime(n)
 
 
 def wv_sieve(lo: int, hi: int, d_out, stream=None) -> int:

@@ -60,5 +60,6 @@ def test_host_validation_without_gpu():
     for bad in ({"arith": 24}, {"arith": 29}, {"arith": 25, "ilp": 4}, {"arith": 2, "ilp": 4},
                 {"ilp": 3}, {"block": 48}):
         assert lib.wv_residues_ex(None, 0, None, None, wv._options(bad), None) == wv.WV_EINVAL, bad
-    for good in ({"arith": 23}, {"arith": 25}, {"arith": 28, "ilp": 1}, {"arith": 9, "ilp": 4}):
+    for good in ({"arith": 23}, {"arith": 25}, {"arith": 28, "ilp": 1}, {"arith": 9, "ilp": 4},
+                 {"check_primes": 1}):
         assert lib.wv_residues_ex(None, 0, None, None, wv._options(good), None) == wv.WV_OK, good
