@@ -63,3 +63,16 @@ def test_host_validation_without_gpu():
     for good in ({"arith": 23}, {"arith": 25}, {"arith": 28, "ilp": 1}, {"arith": 9, "ilp": 4},
                  {"check_primes": 1}):
         assert lib.wv_residues_ex(None, 0, None, None, wv._options(good), None) == wv.WV_OK, good
+
+
+def test_every_tuning_grid_passes_option_validation():
+    # each option set a tuning grid times must be one the library accepts
+    # (n == 0: validated, then nothing runs)
+    from paper_2101_11157_gb300 import tune
+    lib = wv.load()
+    grids = dict(tune.GRIDS)
+    grids["batch"] = tune.BATCH_GRID
+    for name, grid in grids.items():
+        for opt in grid:
+            st = lib.wv_residues_ex(None, 0, None, None, wv._options(opt), None)
+            assert st == wv.WV_OK, (name, opt, wv.wv_last_error())
