@@ -931,6 +931,10 @@ __device__ __forceinline__ void accumulate_loop(const Plan &P) {
   }
 }
 
+// At least 3 resident blocks of 256 threads per SM: a register budget of up
+// to 85 per thread.  Without the minimum the compiler fits the 32-bit
+// grouped kernel into 64 registers (4 blocks) and schedules its group loop
+// tighter, which measured slower on GB300 than 3 blocks of 70 registers.
 template <bool WIDE, int ILP, int AR>
 __global__ void __launch_bounds__(kAccThreads, 3) k_accumulate(Plan P) {
   accumulate_loop<WIDE, ILP, AR>(P);
