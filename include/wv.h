@@ -182,7 +182,7 @@ typedef struct {
                        call with few primes gets more and shorter tiles (up to 64 per
                        sum) so that one launch still holds ~1e5 tiles */
   int blocks_per_sm;/* persistent grid = SMs x this */
-  int arith;        /* hot-loop formulation, 1..23 or 25..28 (default 9: grouped terms, REDC folded
+  int arith;        /* hot-loop formulation, 1..23 or 25..31 (default 9: grouped terms, REDC folded
                        into wide multiply-adds, on both paths).  1..8 select the single-
                        term and intermediate forms of the 32-bit path for ablation, and
                        any value below 9 the single-term 64-bit path; 10..22 select other
@@ -194,8 +194,9 @@ typedef struct {
                        25..28 are formulation 9 on the 32-bit path with none, 4, 6 or
                        all of a group's difference-table additions written as ALU-only
                        three-input adds (9 itself: 4 of a Bernoulli group's 9 and 2 of
-                       an Euler group's 10; the 64-bit path runs 9; ilp 1 or 2).
-                       Other values: WV_EINVAL */
+                       an Euler group's 10; the 64-bit path runs 9; ilp 1 or 2);
+                       29..31 are 9 with groups of 3 cubes, of 4 squares, or both on
+                       the 32-bit path (same conditions).  Other values: WV_EINVAL */
   int check_primes; /* nonzero: the planner also verifies that every input is a prime
                        (deterministic Miller-Rabin, bases 2..17, exact below 2^37); a
                        composite gets WV_RESIDUE_INVALID in its slot like an input

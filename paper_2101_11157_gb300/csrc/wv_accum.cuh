@@ -186,10 +186,10 @@ __device__ __forceinline__ void tile_m31(const PrimeCtx &ctx, uint64_t start, ui
 // plain C; the compiler may place their two-input adds on the multiply pipe,
 // which the products already fill.  NF moves work from that pipe to the ALU.
 
-template <int ILP, bool CUBES, int AR, int NF = 0>
+template <int ILP, bool CUBES, int AR, int NF = 0, int KG = 0>
 __device__ __forceinline__ void tile_m31_grouped(const PrimeCtx &ctx, uint64_t start, uint64_t n,
                                                  int64_t &r0, int64_t &r1) {
-  constexpr int K = CUBES ? 2 : 3;     // terms per group
+  constexpr int K = KG ? KG : (CUBES ? 2 : 3);  // terms per group (default 2 cubes / 3 squares)
   constexpr int EX = CUBES ? 3 : 2;    // t = s^EX
   constexpr int DA = K * EX;           // degree of G0
   constexpr int DB = (K - 1) * EX;     // degree of G1
@@ -886,9 +886,13 @@ __device__ __forceinline__ void process_tile(const Plan &P, uint32_t g) {
   // ALU-only table additions per group of the 32-bit grouped form, for the
   // Bernoulli (cubes, 9 additions per group) and Euler (squares, 10) sums:
   // 4 and 2 in the default 9 (the fastest on GB300 of 0, 2..6 and all);
-  // 25: none, 26: 4 and 4, 27: 6 and 6, 28: all (ablation)
-  constexpr int NFC = AR == 9 ? 4 : AR == 26 ? 4 : AR == 27 ? 6 : AR == 28 ? 10 : 0;
-  constexpr int NFS = AR == 9 ? 2 : AR == 26 ? 4 : AR == 27 ? 6 : AR == 28 ? 10 : 0;
+  // 25: none, 26: 4 and 4, 27: 6 and 6, 28: all (ablation).  29..31 are 9
+  // with larger groups: 3 cubes (15 additions, 6 ALU-only), 4 squares (14
+  // additions, 4 ALU-only), or both.
+  constexpr bool G3C = AR == 29 || AR == 31, G4S = AR == 30 || AR == 31;
+  constexpr int NFC = G3C ? 6 : (AR == 9 || AR >= 29) ? 4 : AR == 26 ? 4 : AR == 27 ? 6 : AR == 28 ? 10 : 0;
+  constexpr int NFS = G4S ? 4 : (AR == 9 || AR >= 29) ? 2 : AR == 26 ? 4 : AR == 27 ? 6 : AR == 28 ? 10 : 0;
+  constexpr int KC = G3C ? 3 : 0, KS = G4S ? 4 : 0;
   const bool grp_ok = n >= 32ull * ILP * kGroupMinChain;
   if (AR == 24) {
     tile_general(ctx, start, n, j < P.rows_b ? P.gen_e_b : P.gen_e_e, r0, r1);
@@ -899,9 +903,9 @@ __device__ __forceinline__ void process_tile(const Plan &P, uint32_t g) {
     if (j < P.rows_b) tile_m31_grouped<ILP, true, 5>(ctx, start, n, r0, r1);
     else tile_m31_grouped<ILP, false, 5>(ctx, start, n, r0, r1);
   } else if (!WIDE && AR >= 7 && grp_ok && j >= P.rows_b) {
-    tile_m31_grouped<ILP, false, 7, NFS>(ctx, start, n, r0, r1);
+    tile_m31_grouped<ILP, false, 7, NFS, KS>(ctx, start, n, r0, r1);
   } else if (!WIDE && AR >= 9 && grp_ok) {
-    tile_m31_grouped<ILP, true, 7, NFC>(ctx, start, n, r0, r1);
+    tile_m31_grouped<ILP, true, 7, NFC, KC>(ctx, start, n, r0, r1);
   } else if (!WIDE) {
     if (j < P.rows_b) tile_m31<ILP, true, AS>(ctx, start, n, r0, r1);
     else tile_m31<ILP, false, AS>(ctx, start, n, r0, r1);
@@ -1029,7 +1033,7 @@ AccKernel acc_kernel_m64x(int arith, int ilp);
 AccKernel acc_kernel_m64y(int arith, int ilp);
 AccKernel acc_kernel_m64z(int arith, int ilp);
 AccKernel acc_kernel_m64w(int arith, int ilp);
-// 32-bit path: formulation 9 with ALU-only table additions (arith 25..28), ILP 1 or 2
+// 32-bit path: formulation 9 with other ALU-only splits or group sizes (arith 25..31), ILP 1 or 2
 AccKernel acc_kernel_m31x(int arith, int ilp);
 // serving-loop epoch kernels (formulation 9; one chain per thread on the 64-bit path)
 EpochKernel epoch_kernel(bool wide, int ilp);

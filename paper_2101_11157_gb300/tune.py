@@ -38,6 +38,8 @@ GRIDS = {
     "paper": [{"arith": 9}, {"arith": 23}],
     # the 32-bit grouped form with 0 / 4 / 6 / all of its table additions ALU-only (9: 4 and 2)
     "alu": [{"arith": a, "ilp": i} for a, i in itertools.product((9, 25, 26, 27, 28), (2, 1))],
+    # group sizes of the 32-bit form: 9 (2 cubes / 3 squares) against 3 cubes, 4 squares, both
+    "groups": [{"arith": a, "ilp": i} for a, i in itertools.product((9, 29, 30, 31), (2, 1))],
     # resident blocks per SM (persistent grid) for the 32-bit forms 9 and 26
     "occ": [{"arith": a, "ilp": i, "blocks_per_sm": b}
             for a, i, b in itertools.product((9, 26), (2, 1), (3, 4, 5, 6))],
