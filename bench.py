@@ -333,7 +333,7 @@ def gpu_arm(args):
                      if width == (TOP_WIDTH if top else WIDTH) else None,
                      "peak_basis": f"{sms} SMs x {IMAD_PER_SM_CLK} IMAD lanes/clk x {sm_max:.0f} MHz / "
                                    f"{slots} IMAD slots per {'64' if top else '32'}-bit Montgomery product "
-                                   "(slot costs measured by wv_diag_throughput)",
+                                   "(slot costs: profiles/int_pipe_probes.md)",
                      "kernel": kname, "kernel_ms": acc_avg_ms},
         "e2e": {"value": total_primes / (e2e_step / 1000.0), "unit": "primes/s",
                 "h2d_bytes_per_step": int(n_primes * 8), "d2h_bytes_per_step": int(n_primes * 16),

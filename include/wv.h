@@ -128,14 +128,19 @@ wv_status wv_residues_pm3(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,
  * that cannot afford the device-wide synchronisation cudaMalloc/cudaFree
  * imply.  The paper has no counterpart to this call.
  *
- * It computes exactly what wv_residues_pm3 computes (default congruences and
- * launch shape) but allocates nothing: all scratch lives in one fixed device
- * array inside the library, about 12 MB, that every GPU which loads the
- * library keeps until the process exits.  Limits and behaviour:
+ * It returns the same residues as wv_residues_pm3 but allocates nothing: all
+ * scratch lives in one fixed device array inside the library, about 12 MB,
+ * that every GPU which loads the library keeps until the process exits.  It
+ * always sums BB30 (eqn 3.7) and EE33 (eqn 5.6), for which that array is
+ * sized, with a fixed launch shape (at most 8 tiles per sum, the default
+ * hot-loop formulation, grids sized by occupancy); options and the automatic
+ * tile shape for short lists do not apply, so a short list may run slower
+ * than through wv_residues_pm3.  Limits and behaviour:
  *  - n <= 1024 primes per call; larger n returns WV_ERANGE (split the list).
  *  - The first call on each device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *    (cudaGetSymbolAddress) with that device current, uploads the two
+ *    congruences into fixed device tables and waits for the device once;
+ *    make that first call before any stream capture.
  *  - Every call uses the same array and leaves its contents behind; the call
  *    itself clears what must start at zero.  Calls that overlap on the GPU
  *    (different streams, or different host threads, without ordering between

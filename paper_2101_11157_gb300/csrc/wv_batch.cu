@@ -96,6 +96,9 @@ wv_status wv_batch_create(const wv_request *reqs, size_t k, const wv_options *op
   if (e == cudaSuccess) e = cudaMalloc(&b->d_reqs, k * sizeof(ReqDesc));
   if (e == cudaSuccess)
     e = cudaMemcpy(b->d_reqs, table.data(), k * sizeof(ReqDesc), cudaMemcpyHostToDevice);
+  // the replays run on the caller's stream, which need not be ordered after
+  // a pageable copy: make sure it has landed
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     batch_free(b);

@@ -166,6 +166,9 @@ wv_status cong_upload(DeviceState *d) {
   WV_CUDA(cudaMemcpy(d->cg_tc, R.tc.data(), R.tc.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
   WV_CUDA(cudaMemcpy(d->cg_td, R.td.data(), R.td.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
   WV_CUDA(cudaMemcpy(d->cg_dist, R.dist.data(), R.dist.size() * sizeof(uint64_t), cudaMemcpyHostToDevice));
+  // copies from pageable memory can return before the data is on the device;
+  // a caller's non-blocking stream is not ordered after them
+  WV_CUDA(cudaDeviceSynchronize());
   return WV_OK;
 }
 

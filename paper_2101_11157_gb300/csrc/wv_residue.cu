@@ -604,7 +604,22 @@ wv_status residues_noalloc(const uint64_t *d_primes, size_t n, uint64_t *d_out_b
       void *ptr = nullptr;
       cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
       if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(noalloc scratch)");
-      // the congruence rows, copied into their static arrays (no allocation)
+      // the congruence rows, copied into their static arrays (no allocation).
+      // The arrays hold at most kMaxRowsPP rows of one term each with base
+      // d = 1; a congruence outside that shape is refused, not truncated.
+      uint32_t nrows_all = 0;
+      for (int id : {kWvDefaultB, kWvDefaultE}) {
+        const CongView &v = cong_view(id);
+        nrows_all += (uint32_t)v.nrows;
+        bool ok = v.ndist == 1 && cong_dist()[v.dist0] == 1;
+        for (int j = 0; ok && j < v.nrows; ++j) ok = cong_row(v.row0 + j)[5] == 1;
+        if (!ok)
+          return set_error(WV_EINVAL, "internal: congruence %s does not fit the no-alloc tables",
+                           v.name);
+      }
+      if (nrows_all > (uint32_t)kMaxRowsPP)
+        return set_error(WV_EINVAL, "internal: %u congruence rows exceed the no-alloc tables (%d)",
+                         nrows_all, kMaxRowsPP);
       uint32_t rows[kMaxRowsPP * 6];
       int64_t tc[kMaxRowsPP];
       uint16_t td[kMaxRowsPP];
@@ -628,6 +643,10 @@ wv_status residues_noalloc(const uint64_t *d_primes, size_t n, uint64_t *d_out_b
       if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_na_tc, tc, sizeof tc);
       if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_na_td, td, sizeof td);
       if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_na_dist, dist, sizeof dist);
+      // A copy from pageable host memory may return before it has reached the
+      // device, and a caller's non-blocking stream is not ordered after it:
+      // wait for the device once, here, so the first launch sees the rows.
+      if (e == cudaSuccess) e = cudaDeviceSynchronize();
       if (e == cudaSuccess) e = cudaGetSymbolAddress(&g_na_cg[dev][0], g_na_rows);
       if (e == cudaSuccess) e = cudaGetSymbolAddress(&g_na_cg[dev][1], g_na_tc);
       if (e == cudaSuccess) e = cudaGetSymbolAddress(&g_na_cg[dev][2], g_na_td);

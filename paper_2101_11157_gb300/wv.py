@@ -103,7 +103,6 @@ _SIGS = {
                         ctypes.POINTER(ctypes.c_double)], _i32),
     "wv_profile_launches": ([], _u64),
     "wv_count_terms": ([_pu64, _sz, _i32, _i32, _pu64, _pu64], _i32),
-    "wv_diag_throughput": ([_i32, _i32, ctypes.POINTER(ctypes.c_double)], _i32),
     "wv_batch_create": ([ctypes.c_void_p, _sz, ctypes.POINTER(wv_options), ctypes.POINTER(_vp)], _i32),
     "wv_batch_run": ([_vp, _vp], _i32),
     "wv_batch_info": ([_vp, _psz, _psz, _psz], _i32),
@@ -373,18 +372,6 @@ def wv_profile_get(idx: int):
     nm, la, ms = ctypes.c_char_p(), ctypes.c_uint64(), ctypes.c_double()
     _check(load().wv_profile_get(idx, ctypes.byref(nm), ctypes.byref(la), ctypes.byref(ms)))
     return nm.value.decode(), la.value, ms.value
-
-
-DIAG_OPS = {"imad": 0, "imad_hi": 1, "imad_wide": 2, "iadd": 3, "imnmx": 4, "term_b": 5, "term_e": 6,
-            "term_b_wide": 7, "term_e_wide": 8, "imad_wide_s": 9, "imad_hi_u": 10,
-            "mont_mul": 11, "shoup_mul": 12, "term_e_shoup": 13}
-
-
-def wv_diag_throughput(op, iters: int = 4096) -> float:
-    """Measured lane-operations (or terms) per SM per clock for diagnostic `op`."""
-    v = ctypes.c_double()
-    _check(load().wv_diag_throughput(DIAG_OPS.get(op, op), iters, ctypes.byref(v)))
-    return v.value
 
 
 class Batch:

@@ -70,3 +70,42 @@ def test_noalloc_rejects_more_than_its_limit():
                                      ctypes.c_void_p(out.data_ptr()), None, None)
     assert st == wv.WV_ERANGE
     assert "1024" in lib.wv_last_error().decode()
+
+
+_FRESH = r"""
+import json, sys
+import numpy as np
+import torch
+sys.path.insert(0, {root!r})
+from paper_2101_11157_gb300 import wv
+primes = np.array({primes!r}, dtype=np.uint64)
+s = torch.cuda.Stream()  # torch creates its streams with cudaStreamNonBlocking
+with torch.cuda.stream(s):
+    d = torch.from_numpy(primes.view(np.int64)).cuda()
+    ob, oe = torch.full_like(d, -7), torch.full_like(d, -7)
+    wv.wv_residues_pm3_noalloc(d, ob, oe, s) if {noalloc!r} else wv.wv_residues_pm3(d, ob, oe, s)
+s.synchronize()
+print(json.dumps([ob.cpu().numpy().view(np.uint64).tolist(), oe.cpu().numpy().view(np.uint64).tolist()]))
+"""
+
+
+@pytest.mark.parametrize("noalloc", [True, False])
+def test_first_call_on_a_non_blocking_stream_in_a_fresh_process(noalloc, orc):
+    # The first call of a process uploads the congruence rows; a caller's
+    # non-blocking stream is not ordered after that upload by itself.  The
+    # residues must still be the oracle's.
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    primes = [int(p) for p in orc.sieve(1_000_000, 1_001_000)] + [16843, 1_062_232_319, 2**30 + 3]
+    code = _FRESH.format(root=root, primes=primes, noalloc=noalloc)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    gb, ge = json.loads(out.stdout.strip().splitlines()[-1])
+    small = [p for p in primes if p < 10**8]
+    rb, re = orc.residues(small)
+    assert gb[:len(small)] == [int(x) for x in rb] and ge[:len(small)] == [int(x) for x in re]
+    # the two large primes: the known zeros, and the GPU's own allocating call in this process
+    assert gb[len(small)] == 0 and ge[len(small) + 1] == 0
