@@ -35,20 +35,21 @@ WIDTH = HI - LO
 IMAD_PER_SM_CLK = 64          # 32-bit integer multiply-add results per SM per clock
 IMAD_SLOTS_PER_MODMUL = 5     # one 32-bit Montgomery product: mul.wide (2) + mul.lo (1) + mul.hi (2)
 SM_MAX_MHZ_FALLBACK = 2070.0
-# DRAM bytes per launch of the p < 2^30 accumulation kernel (k_accumulate<0,2,9>, default congruences
-# BB249 + EE404), from one ncu capture of the 492-prime head of the window (9,202,688 B read, 0 written),
-# scaled by primes to the 4907-prime launch.  Must be re-taken (or set to None) whenever that kernel changes.
-ACC_TRAFFIC_BYTES = 9202688 * 4907 / 492
 # --workload top: the 391 primes of [1e11 - 1e4, 1e11) on the 64-bit path.  One 64-bit
 # Montgomery product for p < 2^37 (R = 2^64 in two 32-bit REDC rounds) costs 17 IMAD slots:
 # c g as three mul.wide and one mul.lo (7), each REDC round one mul.lo and two mul.wide (10).
 TOP_LO, TOP_WIDTH = 10**11 - 10**4, 10**4
 IMAD_SLOTS_PER_MODMUL64 = 17
-# DRAM bytes per launch of the 64-bit accumulation kernel (k_accumulate_m64cap<9,128>, congruences
-# BB1115 + EE967), from one ncu capture of the 17-prime head of the window below 1e11 (1,959,936 B read,
-# 0 written), scaled by primes to the 391-prime launch.  Must be re-taken (or set to None) whenever that
-# kernel changes.
-ACC64_TRAFFIC_BYTES = 1959936 * 391 / 17
+# Per accumulation kernel, from one `ncu --set full` capture of a small case of the same
+# workload (the summary named in "profile"): the IMAD-pipe busy share
+# (sm__pipe_fmaheavy_cycles_active, of peak), the terms summed per SM per clock in that capture,
+# and the DRAM bytes (read + write) per prime of the capture.  The roofline fraction of a bench
+# run is that busy share scaled by the run's own terms per SM per clock.  Set an entry to None
+# whenever its kernel changes, until it is captured again.
+PIPE_PROFILE = {
+    "accumulate_m31": None,
+    "accumulate_m64": None,
+}
 
 
 def dist_env():
@@ -138,36 +139,25 @@ def oracle_sample(k: int, seed: int = 7):
 
 
 def run_oracle_step(primes, threads: int):
-    """Both residues for `primes` with the oracle on host threads; B and E of a
-    prime run in parallel threads so a one-prime step uses two cores."""
+    """Both residues for `primes` with the oracle on `threads` host threads
+    (one prime per thread at a time, B then E)."""
     from oracle import oracle as O
-    res = {}
-
-    def job(kind):
-        if kind == "b":
-            res["b"] = O.residues(primes, method_b="default", method_e=None, threads=max(1, threads // 2))[0]
-        else:
-            res["e"] = O.residues(primes, method_b=None, method_e="default", threads=max(1, threads // 2))[1]
-    ts = [threading.Thread(target=job, args=(k,)) for k in ("b", "e")]
     t0 = time.perf_counter()
-    for t in ts:
-        t.start()
-    for t in ts:
-        t.join()
-    return time.perf_counter() - t0, res
+    b, e = O.residues(primes, method_b="default", method_e="default", threads=threads)
+    return time.perf_counter() - t0, {"b": b, "e": e}
 
 
 def reference_arm(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    sample = oracle_sample(1, seed=11)
-    threads = 2
+    cores = os.cpu_count() or 1
+    sample = oracle_sample(cores, seed=11)
     for _ in range(args.warmup):
-        run_oracle_step(sample, threads)
+        run_oracle_step(sample, cores)
     times = []
     for _ in range(args.steps):
-        dt, _ = run_oracle_step(sample, threads)
+        dt, _ = run_oracle_step(sample, cores)
         times.append(dt)
     ms = 1000.0 * sum(times) / len(times)
     val = len(sample) / (ms / 1000.0)
@@ -178,10 +168,11 @@ def reference_arm(args):
         "data": "synthetic: primes of the window near 1.06e9 (no dataset)",
         "config": {"workload": f"B_{{p-3}}, E_{{p-3}} mod p for primes in [{LO}, {HI}); "
                                "reference = plain CPU oracle (Stafford-Vandiver eqn 2.4 for B, "
-                               "Glaisher eqn 4.1 for E), one seeded prime per step",
+                               "Glaisher eqn 4.1 for E), one seeded prime per host core per step",
                    "l2": "n/a (CPU)"},
-        "cpu_baseline": {"value": val, "unit": "primes/s", "cores": threads, "kind": "oracle",
-                         "sample": f"1 prime per step ({int(sample[0])}), B and E on 2 threads"},
+        "cpu_baseline": {"value": val, "unit": "primes/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{len(sample)} seeded primes of the window per step (one per host "
+                                   f"core), B then E on each of {cores} threads"},
         "e2e": {"value": val, "unit": "primes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -289,29 +280,62 @@ def gpu_arm(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_step = float(t.item())
 
-    # CPU oracle baseline (rank 0, N = 1 only)
+    # CPU oracle baseline (rank 0, N = 1 only): one seeded prime of the window per host core,
+    # all cores busy
     cpu = None
     if ws == 1 and rank == 0 and not args.no_cpu and not top:
-        sample = oracle_sample(2, seed=7)
-        dt, res = run_oracle_step(sample, threads=4)
-        cpu = {"value": len(sample) / dt, "unit": "primes/s", "cores": 4, "kind": "oracle",
-               "sample": f"{len(sample)} seeded primes of the window ({', '.join(str(int(x)) for x in sample)}): "
-                         "B by Stafford-Vandiver (eqn 2.4), E by Glaisher (eqn 4.1), 2 threads per kind"}
+        cores = os.cpu_count() or 1
+        sample = oracle_sample(cores, seed=7)
+        dt, res = run_oracle_step(sample, threads=cores)
+        cpu = {"value": len(sample) / dt, "unit": "primes/s", "cores": cores, "kind": "oracle",
+               "sample": f"{len(sample)} seeded primes of the window (one per host core, both residues): "
+                         "B by Stafford-Vandiver (eqn 2.4), E by Glaisher (eqn 4.1), 128-bit remainders",
+               "seconds": dt}
         # the oracle and the GPU agree on the sample
         idx = np.searchsorted(primes, sample)
         gb, ge = api.to_u64(d_rb)[idx], api.to_u64(d_re)[idx]
         cpu["agrees_with_gpu"] = bool(np.array_equal(gb, res["b"]) and np.array_equal(ge, res["e"]))
 
-    # roofline of the dominant kernel (the p < 2^30 accumulation; the 64-bit one for top)
+    # roofline of the dominant kernel (the p < 2^30 accumulation; the 64-bit one for top): the
+    # integer multiply (IMAD) pipe.  frac = the pipe's busy share in the kernel's ncu capture,
+    # scaled by this run's terms per SM per clock against the capture's.
     kname = "accumulate_m64" if top else "accumulate_m31"
     slots = IMAD_SLOTS_PER_MODMUL64 if top else IMAD_SLOTS_PER_MODMUL
     acc_launches, acc_ms = prof.get(kname, (0, 0.0))
     acc_avg_ms = acc_ms / max(1, acc_launches)
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz") or SM_MAX_MHZ_FALLBACK)
-    imad_peak = sms * IMAD_PER_SM_CLK * sm_max * 1e6            # IMAD results / s
-    peak_gmodmul = imad_peak / slots / 1e9
+    clk_mhz = float((clocks or {}).get("sm_mhz") or sm_max)
+    tpcs = (tb + te) / (acc_avg_ms / 1e3) / sms / (clk_mhz * 1e6) if acc_avg_ms else 0.0
+    prof_k = PIPE_PROFILE.get(kname)
+    full = width == (TOP_WIDTH if top else WIDTH)
+    pipe_peak = sms * clk_mhz * 1e6  # IMAD-pipe cycles per second over all SMs
+    if prof_k:
+        frac = prof_k["imad_pct"] * tpcs / prof_k["terms_per_clk_sm"]
+        roof = {"bound": "alu", "achieved": frac * pipe_peak, "peak": pipe_peak,
+                "unit": "IMAD-pipe cycles/s", "frac": frac,
+                "traffic": prof_k["dram_bytes_per_prime"] * n_primes if full else None,
+                "traffic_basis": f"ncu dram__bytes_read.sum + dram__bytes_write.sum of {prof_k['profile']}, "
+                                 "scaled by primes to this launch",
+                "frac_basis": f"IMAD-pipe busy {prof_k['imad_pct']:.3f} at {prof_k['terms_per_clk_sm']:.3f} "
+                              f"terms/clk/SM ({prof_k['profile']}); this run {tpcs:.3f} terms/clk/SM at "
+                              f"{clk_mhz:.0f} MHz",
+                "alu_pipe_busy_in_capture": prof_k.get("alu_pct")}
+    else:
+        roof = {"bound": "alu", "achieved": None, "peak": pipe_peak, "unit": "IMAD-pipe cycles/s",
+                "frac": None, "traffic": None,
+                "frac_basis": "no ncu capture of the current kernel"}
+    # the same work counted as two Montgomery products per summed term (eqn 3.12), against the
+    # IMAD slots one exact product costs (profiles/int_pipe_probes.md); the grouped forms issue
+    # fewer slots per term, so this can exceed the pipe fraction (and 1 on the 64-bit path)
+    peak_gmodmul = sms * IMAD_PER_SM_CLK * clk_mhz * 1e6 / slots / 1e9
     achieved_gmodmul = (modmuls_per_step / (acc_avg_ms / 1000.0)) / 1e9 if acc_avg_ms else 0.0
+    roof.update({"kernel": kname, "kernel_ms": acc_avg_ms, "terms_per_clk_sm": tpcs,
+                 "modmul_equiv_frac": achieved_gmodmul / peak_gmodmul if peak_gmodmul else None,
+                 "modmul_equiv": {"achieved": achieved_gmodmul, "peak": peak_gmodmul, "unit": "Gmodmul/s",
+                                  "peak_basis": f"{sms} SMs x {IMAD_PER_SM_CLK} IMAD lanes/clk x "
+                                                f"{clk_mhz:.0f} MHz / {slots} IMAD slots per "
+                                                f"{'64' if top else '32'}-bit Montgomery product"}})
     total_primes = n_primes * ws
     value = total_primes / (ms / 1000.0)
     cong_names = [wv.wv_congruence_info(c)[0] for c in cong]
@@ -327,14 +351,7 @@ def gpu_arm(args):
                    "terms_per_step": int(tb + te), "parallelism": f"range-sharded x{ws}",
                    "l2": "flushed between steps (256 MB write)"},
         "modmul_per_s": modmuls_per_step * ws / (ms / 1000.0),
-        "roofline": {"bound": "alu", "achieved": achieved_gmodmul, "peak": peak_gmodmul,
-                     "unit": "Gmodmul/s", "frac": achieved_gmodmul / peak_gmodmul if peak_gmodmul else None,
-                     "traffic": (ACC64_TRAFFIC_BYTES if top else ACC_TRAFFIC_BYTES)
-                     if width == (TOP_WIDTH if top else WIDTH) else None,
-                     "peak_basis": f"{sms} SMs x {IMAD_PER_SM_CLK} IMAD lanes/clk x {sm_max:.0f} MHz / "
-                                   f"{slots} IMAD slots per {'64' if top else '32'}-bit Montgomery product "
-                                   "(slot costs: profiles/int_pipe_probes.md)",
-                     "kernel": kname, "kernel_ms": acc_avg_ms},
+        "roofline": roof,
         "e2e": {"value": total_primes / (e2e_step / 1000.0), "unit": "primes/s",
                 "h2d_bytes_per_step": int(n_primes * 8), "d2h_bytes_per_step": int(n_primes * 16),
                 "path": "host prime list (pinned) -> wv_residues_ex (the window's congruences) -> host residues"},
@@ -347,12 +364,35 @@ def gpu_arm(args):
         line["cpu_baseline"] = cpu
     if top:
         line["cpu_baseline"] = None
-        line["cpu_baseline_note"] = ("not timed: the oracle needs about 20 core-minutes per prime "
-                                     "near 1e11 (eqn 2.4 / eqn 4.1 single sums)")
-        line["note"] = ("achieved counts 2 modmuls per summed term (eqn 3.12); the grouped "
-                        "formulation (8 cubes / 10 squares per eqn 3.14 step) issues far fewer "
-                        "multiply-pipe slots per term than two 17-slot products, so frac can "
-                        "exceed 1; the ncu pipe counters in profiles/ give the pipe utilisation")
+        line["cpu_baseline_note"] = ("not timed: the oracle needs about an hour per prime near 1e11 "
+                                     "(eqn 2.4 / eqn 4.1 single sums); its stored residues of 8 of "
+                                     "these primes are checked by the GPU tests")
+    # the batched and serving forms against the plain one, on the same GPU (rank 0, N = 1)
+    if ws == 1 and rank == 0 and not top and not args.no_extras:
+        from paper_2101_11157_gb300 import workloads as W
+        try:
+            r = batch_measure(W.batch_requests(seed=7), steps=2, warmup=1)
+            line["batch"] = {k: r[k] for k in (
+                "batched_primes_s", "per_request_primes_s", "ratio", "per_request_default_primes_s",
+                "ratio_vs_default", "identical_results", "congruence_groups", "per_request_calls",
+                "primes", "requests", "batched_ms", "per_request_ms")}
+            line["batch"]["workload"] = ("64 requests of batch_requests(seed=7): 1..4096 primes each, "
+                                         "log-uniform in [1e5, 1e10); per_request = one wv_residues_ex per "
+                                         "request and congruence group (same congruences as the batch)")
+        except Exception as exc:  # reported, not hidden
+            line["batch"] = {"error": repr(exc)}
+        try:
+            sq = W.serving_stream(seed=11, n=args.serve_queries)
+            r = serve_measure(sq, epoch_terms=4e10)
+            line["serve"] = {k: r[k] for k in (
+                "served_primes_s", "plain_primes_s", "ratio", "latency", "plain_latency",
+                "identical_results", "queries", "primes", "makespan_s", "plain_makespan_s")}
+            line["serve"]["workload"] = (f"the first {len(sq)} queries of serving_stream(seed=11): "
+                                         "Poisson arrivals at 200/s, half ranges [10^U(6,10), +10^U(3,6)), "
+                                         "half single primes; latency = completion - arrival; plain = one "
+                                         "query at a time in arrival order")
+        except Exception as exc:
+            line["serve"] = {"error": repr(exc)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -366,31 +406,52 @@ def _pctl(xs, q):
     return float(np.percentile(np.asarray(xs), q)) if len(xs) else None
 
 
-def batch_arm(args):
-    """64 seeded requests of uneven cost: one graph-captured batch vs one call per request."""
+def _band_groups(primes):
+    """Positions of `primes` grouped by the congruence pair the range-aware
+    calls pick for [p, p + 1): {(cong_b, cong_e): index array}."""
+    import numpy as np
+
+    from paper_2101_11157_gb300 import wv
+    groups = {}
+    for i, p in enumerate(np.asarray(primes, dtype=np.uint64)):
+        groups.setdefault(wv.wv_congruence_for_range(int(p), int(p) + 1), []).append(i)
+    return {k: np.asarray(v, dtype=np.int64) for k, v in groups.items()}
+
+
+def batch_measure(reqs_np, steps: int, warmup: int, options=None, autotune_key=None):
+    """The batched form against one call per request, on the same GPU.
+
+    batched: wv_batch (one graph; primes grouped by the congruence pair their
+    size calls for).  per_request: one wv_residues_ex per request and
+    congruence group, with the same pairs (the plain form, range-aware).
+    per_request_default: one wv_residues_pm3 per request (BB30 + EE33)."""
     import numpy as np
     import torch
 
-    from paper_2101_11157_gb300 import wv, workloads as W
-    torch.cuda.set_device(0)
-    reqs_np = W.batch_requests(seed=7, k=args.requests, max_len=args.max_len)
+    from paper_2101_11157_gb300 import wv
+    stream = torch.cuda.current_stream()
     reqs = []
     for a in reqs_np:
-        d = torch.from_numpy(a.view(np.int64)).cuda()
+        d = torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).cuda()
         reqs.append((d, torch.empty_like(d), torch.empty_like(d)))
     n = sum(a.size for a in reqs_np)
-    tb = te = 0
-    for a in reqs_np:
-        x, y = wv.wv_count_terms(a)
-        tb, te = tb + x, te + y
-    stream = torch.cuda.current_stream()
-    # launch shape chosen by the autotuner (timed on this batch, outside the timed region)
-    opt, table = None, []
-    if not args.no_autotune:
+    table = []
+    if autotune_key:
         from paper_2101_11157_gb300 import tune
-        opt, table = tune.tune_batch(reqs, key=f"requests{len(reqs_np)}-seed7-max{args.max_len}")
-    b = wv.wv_batch_create(reqs, opt or None)
+        options, table = tune.tune_batch(reqs, key=autotune_key)
+    b = wv.wv_batch_create(reqs, options or None)
     _, _, nodes = wv.wv_batch_info(b)
+    groups_in_batch = wv.wv_batch_groups(b)
+    # the plain form: per request and congruence group, sub-tensors made outside the timing
+    plain = []   # (request, positions, primes, out B, out E, options)
+    terms = 0
+    for r, a in enumerate(reqs_np):
+        for (cb, ce), idx in _band_groups(a).items():
+            sub = torch.from_numpy(np.ascontiguousarray(a[idx]).view(np.int64)).cuda()
+            plain.append((r, idx, sub, torch.empty_like(sub), torch.empty_like(sub),
+                          {"cong_b": cb, "cong_e": ce}))
+            tb, te = wv.wv_count_terms(a[idx], cb, ce)
+            terms += tb + te
 
     def timed(fn, k):
         ms = []
@@ -404,50 +465,64 @@ def batch_arm(args):
         return ms
 
     run_batch = lambda: wv.wv_batch_run(b, stream)
-    run_plain = lambda: [wv.wv_residues_pm3(d, rb, re, stream) for d, rb, re in reqs]
-    for _ in range(args.warmup):
-        run_batch()
+    run_plain = lambda: [wv.wv_residues_ex(d, rb, re, o, stream) for _, _, d, rb, re, o in plain]
+    run_default = lambda: [wv.wv_residues_pm3(d, rb, re, stream) for d, rb, re in reqs]
+    for fn in (run_batch, run_plain, run_default):
+        for _ in range(warmup):
+            fn()
     torch.cuda.synchronize()
-    ms_b = timed(run_batch, args.steps)
+    ms_b = timed(run_batch, steps)
     out_b = [(rb.clone(), re.clone()) for _, rb, re in reqs]
-    run_plain()
-    torch.cuda.synchronize()
-    ms_p = timed(run_plain, args.steps)
+    ms_p = timed(run_plain, steps)
+    ms_d = timed(run_default, steps)
     same = all(torch.equal(rb, x) and torch.equal(re, y) for (_, rb, re), (x, y) in zip(reqs, out_b))
-    mb, mp = statistics.median(ms_b), statistics.median(ms_p)
-    line = {"workload": "batch", "metric": "primes/s, 64 requests in one launch vs one launch per request",
-            "value": n / (mb / 1e3), "unit": "primes/s", "plain_value": n / (mp / 1e3),
-            "speedup_vs_plain": mp / mb, "ms_per_step": mb, "plain_ms_per_step": mp,
-            "modmul_per_s": 2 * (tb + te) / (mb / 1e3), "steps": args.steps, "warmup": args.warmup,
+    for r, idx, _, rb, re, _ in plain:
+        x, y = out_b[r]
+        same = same and np.array_equal(x.cpu().numpy()[idx], rb.cpu().numpy()) \
+            and np.array_equal(y.cpu().numpy()[idx], re.cpu().numpy())
+    wv.wv_batch_destroy(b)
+    mb, mp, md = statistics.median(ms_b), statistics.median(ms_p), statistics.median(ms_d)
+    return {"batched_primes_s": n / (mb / 1e3), "per_request_primes_s": n / (mp / 1e3),
+            "ratio": mp / mb, "per_request_default_primes_s": n / (md / 1e3),
+            "ratio_vs_default": md / mb, "batched_ms": mb, "per_request_ms": mp,
+            "per_request_default_ms": md, "modmul_per_s": 2 * terms / (mb / 1e3),
             "identical_results": bool(same), "graph_nodes": nodes,
-            "options": opt or {}, "autotune": table,
-            "config": {"requests": len(reqs_np), "primes": int(n), "terms": int(tb + te),
+            "congruence_groups": groups_in_batch, "per_request_calls": len(plain),
+            "options": options or {}, "autotune": table, "steps": steps, "warmup": warmup,
+            "requests": len(reqs_np), "primes": int(n), "terms": int(terms)}
+
+
+def batch_arm(args):
+    """64 seeded requests of uneven cost: one graph-captured batch vs one call per request."""
+    import torch
+
+    from paper_2101_11157_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    reqs_np = W.batch_requests(seed=7, k=args.requests, max_len=args.max_len)
+    key = None if args.no_autotune else f"requests{len(reqs_np)}-seed7-max{args.max_len}-grouped"
+    r = batch_measure(reqs_np, args.steps, args.warmup, autotune_key=key)
+    line = {"workload": "batch", "metric": "primes/s, 64 requests in one launch vs one launch per request",
+            "value": r["batched_primes_s"], "unit": "primes/s", **r,
+            "config": {"requests": len(reqs_np), "primes": r["primes"], "terms": r["terms"],
                        "lengths": "floor(2^U(0,12)) clamped to [1, %d]" % args.max_len,
                        "primes_from": "next_prime(10^U(5,10)), seed 7"}}
-    wv.wv_batch_destroy(b)
     print(json.dumps(line), flush=True)
     return 0
 
 
-def serve_arm(args):
-    """A seeded Poisson stream of range and single-prime queries, served with
-    continuous batching and, for comparison, one query at a time."""
+def serve_measure(stream_q, epoch_terms: float, epoch_form: int = 0, epoch_block: int = 0,
+                  plain_block: int = 0):
+    """Serve a stream of queries (continuous batching) and, for comparison,
+    run it one query at a time in arrival order; both pick congruences by the
+    query's range."""
     import numpy as np
     import torch
 
-    from paper_2101_11157_gb300 import api, wv, workloads as W
-    torch.cuda.set_device(0)
-    stream = W.serving_stream(seed=11, n=args.queries, rate=args.rate)
-    if args.max_range:
-        for q in stream:
-            if q["kind"] == "range":
-                q["hi"] = min(q["hi"], q["lo"] + args.max_range)
-    # served
-    srv = wv.wv_server_create(epoch_terms=args.epoch_terms, epoch_form=args.epoch_form,
-                              epoch_block=args.epoch_block)
+    from paper_2101_11157_gb300 import api, wv
+    srv = wv.wv_server_create(epoch_terms=epoch_terms, epoch_form=epoch_form, epoch_block=epoch_block)
     t0 = time.perf_counter()
     ids = []
-    for q in stream:
+    for q in stream_q:
         dt = q["t"] - (time.perf_counter() - t0)
         if dt > 0:
             time.sleep(dt)
@@ -462,15 +537,14 @@ def serve_arm(args):
     wait_admit = [i["t_admit"] - i["t_submit"] for i in infos]
     service = [i["t_done"] - i["t_admit"] for i in infos]
     n_primes = sum(i["n_primes"] for i in infos)
-    # plain: one query at a time, in arrival order
     t0 = time.perf_counter()
     lat_p = []
     same = True
-    for q, res in zip(stream, served_res):
+    popt = {"block": plain_block} if plain_block else None
+    for q, res in zip(stream_q, served_res):
         dt = q["t"] - (time.perf_counter() - t0)
         if dt > 0:
             time.sleep(dt)
-        popt = {"block": args.plain_block} if args.plain_block else None
         if q["kind"] == "range":
             lo = max(q["lo"], 5)
             if q["hi"] > lo:
@@ -484,7 +558,7 @@ def serve_arm(args):
         lat_p.append(time.perf_counter() - t0 - q["t"])
         same = same and np.array_equal(api.to_u64(rb), res[1]) and np.array_equal(api.to_u64(re), res[2])
     makespan_p = time.perf_counter() - t0
-    kinds = [q["kind"] for q in stream]
+    kinds = [q["kind"] for q in stream_q]
 
     def stats(ls):
         out = {}
@@ -492,17 +566,34 @@ def serve_arm(args):
             xs = [x for x, kk in zip(ls, kinds) if kk == k]
             out[k] = {"p50_s": _pctl(xs, 50), "p99_s": _pctl(xs, 99), "n": len(xs)}
         return out
-    line = {"workload": "serve", "metric": "primes/s and p50/p99 latency, continuous batching vs one query at a time",
-            "value": n_primes / makespan, "unit": "primes/s", "plain_value": n_primes / makespan_p,
-            "makespan_s": makespan, "plain_makespan_s": makespan_p,
+    return {"served_primes_s": n_primes / makespan, "plain_primes_s": n_primes / makespan_p,
+            "ratio": makespan_p / makespan, "makespan_s": makespan, "plain_makespan_s": makespan_p,
             "latency": stats(lat), "plain_latency": stats(lat_p), "identical_results": bool(same),
-            "admission_wait": stats(wait_admit), "service_time": stats(service),
-            "server": st, "config": {"queries": len(stream), "rate_per_s": args.rate, "seed": 11,
-                                     "range_len_cap": args.max_range or None,
-                                     "epoch_terms": args.epoch_terms, "primes": int(n_primes),
-                                     "plain_block": args.plain_block or None,
-                                     "epoch_form": args.epoch_form,
-                                     "epoch_block": args.epoch_block or 32}}
+            "admission_wait": stats(wait_admit), "service_time": stats(service), "server": st,
+            "queries": len(stream_q), "primes": int(n_primes)}
+
+
+def serve_arm(args):
+    """A seeded Poisson stream of range and single-prime queries, served with
+    continuous batching and, for comparison, one query at a time."""
+    import torch
+
+    from paper_2101_11157_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    stream_q = W.serving_stream(seed=11, n=args.queries, rate=args.rate)
+    if args.max_range:
+        for q in stream_q:
+            if q["kind"] == "range":
+                q["hi"] = min(q["hi"], q["lo"] + args.max_range)
+    r = serve_measure(stream_q, args.epoch_terms, args.epoch_form, args.epoch_block, args.plain_block)
+    line = {"workload": "serve", "metric": "primes/s and p50/p99 latency, continuous batching vs one query at a time",
+            "value": r["served_primes_s"], "unit": "primes/s", **r,
+            "config": {"queries": len(stream_q), "rate_per_s": args.rate, "seed": 11,
+                       "range_len_cap": args.max_range or None,
+                       "epoch_terms": args.epoch_terms, "primes": r["primes"],
+                       "plain_block": args.plain_block or None,
+                       "epoch_form": args.epoch_form,
+                       "epoch_block": args.epoch_block or 32}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -515,6 +606,10 @@ def main():
     ap.add_argument("--impl", default="wv", choices=["wv", "reference"])
     ap.add_argument("--width", type=int, default=WIDTH, help="window width (smaller for profiling)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="window workload only: skip the batch and serving comparisons")
+    ap.add_argument("--serve-queries", type=int, default=48,
+                    help="queries of the seeded stream served in the default run")
     ap.add_argument("--workload", default="window", choices=["window", "top", "batch", "serve"])
     ap.add_argument("--requests", type=int, default=64, help="batch: number of requests")
     ap.add_argument("--max-len", type=int, default=4096, help="batch: longest request")

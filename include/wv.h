@@ -132,8 +132,8 @@ wv_status wv_residues_pm3(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,
  * scratch lives in one fixed device array inside the library, about 12 MB,
  * that every GPU which loads the library keeps until the process exits.  It
  * always sums BB30 (eqn 3.7) and EE33 (eqn 5.6), for which that array is
- * sized, with a fixed launch shape (at most 8 tiles per sum, the default
- * hot-loop formulation, grids sized by occupancy); options and the automatic
+ * sized, with a fixed launch shape (at most 8 tiles per sum, hot-loop
+ * formulation 9, grids sized by occupancy); options and the automatic
  * tile shape for short lists do not apply, so a short list may run slower
  * than through wv_residues_pm3.  Limits and behaviour:
  *  - n <= 1024 primes per call; larger n returns WV_ERANGE (split the list).
@@ -179,7 +179,7 @@ typedef struct {
                        default 256.  Smaller blocks release their registers warp by
                        warp at the end of a launch and round occupancy differently */
   int ilp;          /* independent accumulator chains per thread for p < 2^30: 1, 2 or 4
-                       (4 only with arith 9..23; default 2).  The grouped 64-bit forms
+                       (4 only with arith 9, 12..18, 21 or 23; default 2).  The grouped 64-bit forms
                        (arith >= 9) run one chain per thread; the single-term 64-bit
                        form takes this value too */
   int tile_terms;   /* target terms per warp tile (default 2^20) */
@@ -187,21 +187,24 @@ typedef struct {
                        call with few primes gets more and shorter tiles (up to 64 per
                        sum) so that one launch still holds ~1e5 tiles */
   int blocks_per_sm;/* persistent grid = SMs x this */
-  int arith;        /* hot-loop formulation, 1..23 or 25..31 (default 9: grouped terms, REDC folded
-                       into wide multiply-adds, on both paths).  1..8 select the single-
-                       term and intermediate forms of the 32-bit path for ablation, and
-                       any value below 9 the single-term 64-bit path; 10..22 select other
-                       grouped 64-bit forms (group sizes, shrink interval, instruction
-                       choices, register budget; one chain per thread) for ablation,
-                       with formulation 9 on the 32-bit path; 23 selects the paper's own
-                       arithmetic on both paths (plain residues, eqn 3.15 split products,
-                       remainders from a double-precision quotient, single terms);
-                       25..28 are formulation 9 on the 32-bit path with none, 4, 6 or
-                       all of a group's difference-table additions written as ALU-only
-                       three-input adds (9 itself: 4 of a Bernoulli group's 9 and 2 of
-                       an Euler group's 10; the 64-bit path runs 9; ilp 1 or 2);
-                       29..31 are 9 with groups of 3 cubes, of 4 squares, or both on
-                       the 32-bit path (same conditions).  Other values: WV_EINVAL */
+  int arith;        /* hot-loop formulation (default 31).  Every value gives the same
+                       residues; the others exist for ablation.  32-bit path (p < 2^30):
+                       1, 2, 4 single terms (1: shared t p^-1; 2: one wide product and
+                       REDC; 4: 2 with the additions as ALU three-input adds); 9
+                       grouped terms (2 cubes / 3 squares per eqn 3.14 step, REDC folded
+                       into wide multiply-adds); 25..28 form 9 with none, 4, 6 or all of a
+                       group's difference-table additions as ALU-only three-input adds
+                       (9 itself: 4 of a Bernoulli group's 9 and 2 of an Euler group's
+                       10); 29, 30, 31 groups of 3 cubes, of 4 squares, or both.  64-bit
+                       path (2^30 <= p < 2^37): 1, 2, 4 the single-term 64-bit kernel;
+                       12..18 and 21 other group sizes, shrink intervals and register
+                       budgets; 32..36 the default with a quarter to all of its 64-bit
+                       table additions as PTX carry chains (32: plain; 33..36: with a
+                       three-input high word); every other value the grouped default
+                       (8 cubes / 10 squares).  23: the paper's own arithmetic on both
+                       paths (plain residues, eqn 3.15 split products, remainders from
+                       a double-precision quotient, single terms).  Other values:
+                       WV_EINVAL */
   int check_primes; /* nonzero: the planner also verifies that every input is a prime
                        (deterministic Miller-Rabin, bases 2..17, exact below 2^37); a
                        composite gets WV_RESIDUE_INVALID in its slot like an input

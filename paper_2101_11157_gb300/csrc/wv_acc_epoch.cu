@@ -8,7 +8,7 @@ namespace wv {
 // the 64-bit tiles of an epoch run one chain per thread (the fastest grouped form)
 EpochKernel epoch_kernel(bool wide, int ilp) {
   if (wide) return k_epoch<true, 1, 9>;
-  return ilp == 1 ? k_epoch<false, 1, 9> : k_epoch<false, 2, 9>;
+  return ilp == 1 ? k_epoch<false, 1, 31> : k_epoch<false, 2, 31>;
 }
 
 }  // namespace wv

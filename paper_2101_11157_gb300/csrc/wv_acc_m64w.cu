@@ -1,6 +1,5 @@
-// wv_acc_m64w.cu -- the 64-bit-path ablation formulation 22 and the 64-bit
-// instantiations of the paper's arithmetic (23) and of the general index
-// (24).  The code is in wv_accum.cuh.
+// wv_acc_m64w.cu -- the 64-bit instantiations of the paper's arithmetic (23)
+// and of the general index (24).  The code is in wv_accum.cuh.
 #include "wv_accum.cuh"
 
 namespace wv {
@@ -11,7 +10,7 @@ AccKernel acc_kernel_m64w(int arith, int ilp) {
   switch (arith) {
     case 23: return k_accumulate<true, I, 23>;  // the paper's arithmetic (ablation)
     case 24: return k_accumulate<true, I, 24>;  // general index (wv_residues_general)
-    default: return k_accumulate_m64cap<22, kM64MaxReg>;
+    default: return acc_kernel_m64v(arith, ilp);
   }
 }
 

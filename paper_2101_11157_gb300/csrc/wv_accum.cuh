@@ -555,24 +555,60 @@ __device__ __forceinline__ uint64_t m64_shrink(uint64_t v, const M64K &K) {
 template <int AR> struct M64Form {  // 9: the default
   static constexpr int KB = 8, KE = 10, BLK = 16, V = 0;
 };
-template <> struct M64Form<10> { static constexpr int KB = 2, KE = 3, BLK = 8, V = 1; };
-template <> struct M64Form<11> { static constexpr int KB = 2, KE = 3, BLK = 8, V = 2; };
+// 32..36: form 9 with its 64-bit table additions written as PTX carry chains
+// (add.cc / addc on the two words) for a share of the entries, in quarters
+// of the table (NFQ = 4: all), taken from the low order up.  Flag 4: the plain
+// carry chain; flag 8: a runtime zero added into the high word as well, which
+// makes that word's add a three-input add with carry in -- an instruction
+// only the integer ALU has, so the entry stays off the multiply pipe.
+template <int AR> struct M64Split { static constexpr int NFQ = 0; };
+template <> struct M64Form<32> : M64Form<9> { static constexpr int V = 4; };
+template <> struct M64Form<33> : M64Form<9> { static constexpr int V = 8; };
+template <> struct M64Form<34> : M64Form<9> { static constexpr int V = 8; };
+template <> struct M64Form<35> : M64Form<9> { static constexpr int V = 8; };
+template <> struct M64Form<36> : M64Form<9> { static constexpr int V = 8; };
+template <> struct M64Split<32> { static constexpr int NFQ = 4; };
+template <> struct M64Split<33> { static constexpr int NFQ = 4; };
+template <> struct M64Split<34> { static constexpr int NFQ = 2; };
+template <> struct M64Split<35> { static constexpr int NFQ = 1; };
+template <> struct M64Split<36> { static constexpr int NFQ = 3; };
+
+// a += b (64-bit) as an explicit carry chain over the two 32-bit words
+__device__ __forceinline__ void add64_cc(uint64_t &a, uint64_t b) {
+  asm("{\n\t.reg .u32 a0, a1, b0, b1;\n\t"
+      "mov.b64 {a0, a1}, %0;\n\t"
+      "mov.b64 {b0, b1}, %1;\n\t"
+      "add.cc.u32 a0, a0, b0;\n\t"
+      "addc.u32 a1, a1, b1;\n\t"
+      "mov.b64 %0, {a0, a1};\n\t}"
+      : "+l"(a)
+      : "l"(b));
+}
+// the same with the runtime zero z added into the high word
+__device__ __forceinline__ void add64_cc_z(uint64_t &a, uint64_t b, uint32_t z) {
+  asm("{\n\t.reg .u32 a0, a1, b0, b1;\n\t"
+      "mov.b64 {a0, a1}, %0;\n\t"
+      "mov.b64 {b0, b1}, %1;\n\t"
+      "add.cc.u32 a0, a0, b0;\n\t"
+      "addc.u32 a1, a1, b1;\n\t"
+      "add.u32 a1, a1, %2;\n\t"
+      "mov.b64 %0, {a0, a1};\n\t}"
+      : "+l"(a)
+      : "l"(b), "r"(z));
+}
 template <> struct M64Form<12> { static constexpr int KB = 2, KE = 3, BLK = 8, V = 0; };
 template <> struct M64Form<13> { static constexpr int KB = 3, KE = 4, BLK = 16, V = 0; };
 template <> struct M64Form<14> { static constexpr int KB = 4, KE = 5, BLK = 16, V = 0; };
 template <> struct M64Form<15> { static constexpr int KB = 5, KE = 6, BLK = 16, V = 0; };
 template <> struct M64Form<16> { static constexpr int KB = 6, KE = 8, BLK = 16, V = 0; };
 template <> struct M64Form<17> { static constexpr int KB = 7, KE = 9, BLK = 16, V = 0; };
-// 18..22: the register budget.  Form 9 runs under a cap of kM64MaxReg
+// 18 and 21: the register budget.  Form 9 runs under a cap of kM64MaxReg
 // registers per thread (16 resident warps per SM, a few bytes of spill in
-// the setup); 18 is form 9 without the cap (8 warps), 19 and 20 caps of 96
-// and 168, 21 and 22 other group sizes under the cap of 128.
+// the setup); 18 is form 9 without the cap (8 warps), 21 groups of 9 / 11
+// under the cap of 128.
 constexpr int kM64MaxReg = 128;
 template <> struct M64Form<18> : M64Form<9> {};
-template <> struct M64Form<19> : M64Form<9> {};
-template <> struct M64Form<20> : M64Form<9> {};
 template <> struct M64Form<21> { static constexpr int KB = 9, KE = 11, BLK = 16, V = 0; };
-template <> struct M64Form<22> : M64Form<17> {};
 
 // a b 2^-64 mod p, below p + 2^12 for a, b < 2^38
 __device__ __forceinline__ uint64_t m64_mm(uint64_t a, uint64_t b, const M64K &K) {
@@ -609,6 +645,8 @@ __device__ __forceinline__ void tile_m64_grouped(const PrimeCtx &ctx, uint64_t s
   KK.q = 0u - (uint32_t)ctx.q;  // -p^-1 mod 2^32
   KK.mhi = (uint32_t)((1ull << 62) / ctx.p);
   const uint64_t z64 = (V & 1) ? (uint64_t)(ctx.flags >> 16) : 0ull;  // runtime zero
+  const uint32_t z32 = ctx.flags >> 16;                                // runtime zero
+  constexpr int NF = (DA + DB) * M64Split<AR>::NFQ / 4;  // carry-chain entries
   const uint64_t nch = 32 * ILP;
   const uint64_t len = n / nch;
   const uint32_t rem = (uint32_t)(n - len * nch);
@@ -701,9 +739,23 @@ __device__ __forceinline__ void tile_m64_grouped(const PrimeCtx &ctx, uint64_t s
         c1[k] = (V & 2) ? m64_redc2_nz(T0, TY, KK) : m64_redc2(T0, TY, KK);
         c0[k] = n0;
 #pragma unroll
-        for (int j = 0; j < DA; ++j) ga[k][j] = ga[k][j] + ga[k][j + 1] + z64;
+        for (int j = 0; j < DA; ++j) {
+          if ((V & 12) && j < NF) {
+            if (V & 8) add64_cc_z(ga[k][j], ga[k][j + 1], z32);
+            else add64_cc(ga[k][j], ga[k][j + 1]);
+          } else {
+            ga[k][j] = ga[k][j] + ga[k][j + 1] + z64;
+          }
+        }
 #pragma unroll
-        for (int j = 0; j < DB; ++j) gb[k][j] = gb[k][j] + gb[k][j + 1] + z64;
+        for (int j = 0; j < DB; ++j) {
+          if ((V & 12) && DA + j < NF) {
+            if (V & 8) add64_cc_z(gb[k][j], gb[k][j + 1], z32);
+            else add64_cc(gb[k][j], gb[k][j + 1]);
+          } else {
+            gb[k][j] = gb[k][j] + gb[k][j + 1] + z64;
+          }
+        }
       }
     }
 #pragma unroll
@@ -994,7 +1046,7 @@ __global__ void __maxnreg__(kM64MaxReg)
     const EpochItem it = items[lo];
     const uint32_t tile = it.first + it.count - 1 - (g - it.prefix);
     if (it.plan >> 31) process_tile<true, I64, 9>(plans[it.plan & 0x7fffffffu], tile);
-    else process_tile<false, I31, 9>(plans[it.plan], tile);
+    else process_tile<false, I31, 31>(plans[it.plan], tile);
   }
 }
 
@@ -1015,7 +1067,7 @@ __global__ void __maxnreg__(kM64MaxReg)
   const EpochItem it = items[lo];
   const uint32_t tile = it.first + it.count - 1 - (g - it.prefix);
   if (it.plan >> 31) process_tile<true, I64, 9>(plans[it.plan & 0x7fffffffu], tile);
-  else process_tile<false, I31, 9>(plans[it.plan], tile);
+  else process_tile<false, I31, 31>(plans[it.plan], tile);
 }
 
 // ------------------------------------------------------------------ getters
@@ -1033,9 +1085,11 @@ AccKernel acc_kernel_m64x(int arith, int ilp);
 AccKernel acc_kernel_m64y(int arith, int ilp);
 AccKernel acc_kernel_m64z(int arith, int ilp);
 AccKernel acc_kernel_m64w(int arith, int ilp);
+AccKernel acc_kernel_m64v(int arith, int ilp);  // forms 32..36 (w falls through to v)
 // 32-bit path: formulation 9 with other ALU-only splits or group sizes (arith 25..31), ILP 1 or 2
 AccKernel acc_kernel_m31x(int arith, int ilp);
-// serving-loop epoch kernels (formulation 9; one chain per thread on the 64-bit path)
+// serving-loop epoch kernels (the default formulations: 31 on the 32-bit path,
+// 9 with one chain per thread on the 64-bit path)
 EpochKernel epoch_kernel(bool wide, int ilp);
 EpochKernel epoch_mixed_kernel(int ilp31, int ilp64);
 using EpochTilesKernel = void (*)(const EpochItem *, uint32_t, uint32_t, const Plan *);

@@ -134,13 +134,28 @@ struct ResidueConfig {
   int max_tiles = 8;
   bool tiles_auto = true; // few primes: more, shorter tiles (see tile_shape)
   int blocks_per_sm = 0;  // 0 = occupancy
-  int arith = 9;          // hot-loop formulation (see wv_accum.cuh)
+  int arith = 31;         // hot-loop formulation (see wv_accum.cuh)
   uint32_t gen_e_b = 0;   // general index: B_{p-e} (e odd); 0 = the B_{p-3} forms
   uint32_t gen_e_e = 0;   // general index: E_{p-1-e} (e even); 0 = the E_{p-3} forms
   size_t chunk = 0;       // primes per launch sequence (0: library default 16384)
   bool check_primes = false;  // planner verifies primality (composites -> invalid slot)
 };
 wv_status resolve_config(const wv_options *opt, bool want_b, bool want_e, ResidueConfig *cfg);
+
+// The hot-loop formulations a caller may select (wv_options.arith):
+//   32-bit path (p < 2^30): 1, 2, 4 single terms; 9 groups of 2 cubes / 3
+//   squares; 25..28 form 9 with other ALU/multiply-pipe splits of the table
+//   additions; 29, 30, 31 groups of 3 cubes, 4 squares, or both (31: the
+//   default).  64-bit path (2^30 <= p < 2^37): 1, 2, 4 single terms; every
+//   other value runs the grouped default (8 cubes / 10 squares) except 12..18
+//   and 21, other group sizes and register budgets, and 32..36, the default
+//   with its table additions as PTX carry chains.  23: the paper's own
+//   arithmetic on both paths.
+constexpr const char *kArithList = "1, 2, 4, 9, 12..18, 21, 23, 25..36";
+inline bool arith_selectable(int a) {
+  return a == 1 || a == 2 || a == 4 || a == 9 || (a >= 12 && a <= 18) || a == 21 || a == 23 ||
+         (a >= 25 && a <= 36);
+}
 
 // Residues for n primes (device array), asynchronous on s.
 wv_status residues_device(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,

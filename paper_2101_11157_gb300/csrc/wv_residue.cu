@@ -266,10 +266,7 @@ AccKernel acc_kernel_m31(int ar, int ilp) {
   if (ar == 24) return k_accumulate<false, 1, 24>;  // general index (wv_residues_general)
 #define WV_PICK(I)                                                            \
   (ar == 1 ? k_accumulate<false, I, 1> : ar == 2 ? k_accumulate<false, I, 2> \
-   : ar == 3 ? k_accumulate<false, I, 3> : ar == 4 ? k_accumulate<false, I, 4> \
-   : ar == 5 ? k_accumulate<false, I, 5> : ar == 6 ? k_accumulate<false, I, 6>  \
-   : ar == 7 ? k_accumulate<false, I, 7> : ar == 8 ? k_accumulate<false, I, 8>  \
-   : k_accumulate<false, I, 9>)
+   : ar == 4 ? k_accumulate<false, I, 4> : k_accumulate<false, I, 9>)
   if (ar >= 25) return acc_kernel_m31x(ar, ilp);
   if (ilp == 1) return WV_PICK(1);
   if (ilp == 2) return WV_PICK(2);
@@ -283,8 +280,12 @@ static wv_status launch_accumulate(const Plan &P, const ResidueConfig &cfg, int 
   AccKernel kern = nullptr;
   if (WIDE) {
     // arith 25..28 vary the 32-bit path only; the 64-bit path runs its default
-    kern = (cfg.arith > 9 && cfg.arith <= 24) ? acc_kernel_m64x(cfg.arith, cfg.ilp64)
-                                               : acc_kernel_m64(cfg.arith >= 9 ? 9 : 1, cfg.ilp64);
+    // the single-term forms (1, 2, 4) run the single-term 64-bit kernel, 12..18,
+    // 21, 23..24 and 32..36 their own 64-bit forms, everything else the grouped
+    // default
+    kern = ((cfg.arith > 9 && cfg.arith <= 24) || cfg.arith >= 32)
+               ? acc_kernel_m64x(cfg.arith, cfg.ilp64)
+               : acc_kernel_m64(cfg.arith >= 9 ? 9 : 1, cfg.ilp64);
   } else {
     kern = acc_kernel_m31(cfg.arith >= 23 ? cfg.arith : cfg.arith > 9 ? 9 : cfg.arith, cfg.ilp);
   }

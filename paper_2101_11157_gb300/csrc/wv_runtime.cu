@@ -301,10 +301,12 @@ wv_status resolve_config(const wv_options *opt, bool want_b, bool want_e, Residu
     return set_error(WV_EINVAL, "block=%d must be a multiple of 32 in [32,256]", c.block);
   if (c.ilp != 1 && c.ilp != 2 && c.ilp != 4)
     return set_error(WV_EINVAL, "ilp=%d must be 1, 2 or 4", c.ilp);
-  if (c.arith < 1 || c.arith > 31 || c.arith == 24)
-    return set_error(WV_EINVAL, "arith=%d must be in 1..23 or 25..31", c.arith);
-  if (c.ilp == 4 && (c.arith < 9 || c.arith >= 25))
-    return set_error(WV_EINVAL, "ilp=4 is built for formulations 9..23 only (arith=%d)", c.arith);
+  if (!arith_selectable(c.arith))
+    return set_error(WV_EINVAL, "arith=%d is not a formulation of this library (%s)", c.arith,
+                     kArithList);
+  if (c.ilp == 4 && c.arith != 9 && !(c.arith >= 12 && c.arith <= 23))
+    return set_error(WV_EINVAL, "ilp=4 is built for formulations 9 and 12..23 only (arith=%d)",
+                     c.arith);
   if (c.arith >= 9) c.ilp64 = 1;  // the grouped 64-bit forms run one chain per thread
   if (c.max_tiles > 4096) return set_error(WV_EINVAL, "max_tiles=%d > 4096", c.max_tiles);
   *cfg = c;

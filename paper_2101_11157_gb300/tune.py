@@ -32,13 +32,17 @@ GRIDS = {
     # launch shapes for the default formulation
     "shape": [{"ilp": i, "tile_terms": t, "max_tiles": m}
               for i, (t, m) in itertools.product((1, 2), ((1 << 18, 16), (1 << 20, 8), (1 << 22, 4)))],
-    # the grouped 64-bit forms (2^30 <= p < 2^37): group sizes and shrink interval
-    "m64": [{"arith": a} for a in (9, *range(12, 24))],
+    # the grouped 64-bit forms (2^30 <= p < 2^37): group sizes, shrink interval, register budget
+    "m64": [{"arith": a} for a in (9, *range(12, 19), 21)],
+    # the 64-bit default with its table additions as PTX carry chains (all, or a share in
+    # three-input form on the integer ALU)
+    "m64cc": [{"arith": a} for a in (9, *range(32, 37))],
     # the paper's own arithmetic (eqn 3.15, double-precision quotients) against the default
     "paper": [{"arith": 9}, {"arith": 23}],
-    # the 32-bit grouped form with 0 / 4 / 6 / all of its table additions ALU-only (9: 4 and 2)
+    # the 32-bit grouped form 9 with 0 / 4 / 6 / all of its table additions ALU-only (9: 4 and 2)
     "alu": [{"arith": a, "ilp": i} for a, i in itertools.product((9, 25, 26, 27, 28), (2, 1))],
-    # group sizes of the 32-bit form: 9 (2 cubes / 3 squares) against 3 cubes, 4 squares, both
+    # group sizes of the 32-bit form: 9 (2 cubes / 3 squares) against 3 cubes, 4 squares, both (31,
+    # the default)
     "groups": [{"arith": a, "ilp": i} for a, i in itertools.product((9, 29, 30, 31), (2, 1))],
     # resident blocks per SM (persistent grid) for the 32-bit forms 9 and 26
     "occ": [{"arith": a, "ilp": i, "blocks_per_sm": b}

@@ -106,6 +106,7 @@ _SIGS = {
     "wv_batch_create": ([ctypes.c_void_p, _sz, ctypes.POINTER(wv_options), ctypes.POINTER(_vp)], _i32),
     "wv_batch_run": ([_vp, _vp], _i32),
     "wv_batch_info": ([_vp, _psz, _psz, _psz], _i32),
+    "wv_batch_groups": ([_vp, _psz], _i32),
     "wv_batch_destroy": ([_vp], _i32),
     "wv_server_create": ([ctypes.POINTER(wv_server_config), ctypes.POINTER(_vp)], _i32),
     "wv_server_submit_range": ([_vp, _u64, _u64, _pu64], _i32),
@@ -412,6 +413,13 @@ def wv_batch_info(batch: Batch):
     a, b, c = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
     _check(load().wv_batch_info(batch.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
     return a.value, b.value, c.value
+
+
+def wv_batch_groups(batch: Batch) -> int:
+    """Number of congruence groups of the batch."""
+    a = ctypes.c_size_t()
+    _check(load().wv_batch_groups(batch.handle, ctypes.byref(a)))
+    return a.value
 
 
 def wv_batch_destroy(batch: Batch) -> None:

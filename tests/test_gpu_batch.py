@@ -91,3 +91,40 @@ def test_autotuner_picks_a_shape_with_identical_results():
     for (d, rb, re), a in zip(reqs, reqs_np):
         gb, ge = api.residues(d)
         assert torch.equal(rb, gb) and torch.equal(re, ge)
+
+
+def _golden_map(name):
+    from conftest import read_golden
+    return {int(p): (int(b), int(e)) for p, b, e in read_golden(name)}
+
+
+def test_full_seed7_batch_against_oracle():
+    """The whole seed-7 workload (64 requests of 1..4096 primes drawn
+    log-uniformly from [1e5, 1e10)) in one batch: a sample of two primes per
+    request against residues stored by the oracle (B by eqn 2.4, E by eqn 4.1),
+    and every request against the per-request call."""
+    reqs_np = W.batch_requests(seed=7)
+    assert len(reqs_np) == 64 and max(a.size for a in reqs_np) <= 4096
+    gold = _golden_map("batch_seed7_sample_residues.txt")
+    reqs = []
+    for a in reqs_np:
+        d = _dev(a)
+        reqs.append((d, torch.full_like(d, -1), torch.full_like(d, -1)))
+    b = wv.wv_batch_create(reqs)
+    try:
+        wv.wv_batch_run(b)
+        torch.cuda.synchronize()
+    finally:
+        wv.wv_batch_destroy(b)
+    checked = set()
+    for a, (d, ob, oe) in zip(reqs_np, reqs):
+        gb, ge = api.to_u64(ob), api.to_u64(oe)
+        hit = [i for i, p in enumerate(a) if int(p) in gold]
+        assert hit, "every request has a stored oracle sample"
+        for i in hit:
+            assert (int(gb[i]), int(ge[i])) == gold[int(a[i])], int(a[i])
+            checked.add(int(a[i]))
+        rb, re = _single(d)
+        torch.cuda.synchronize()
+        assert torch.equal(ob, rb) and torch.equal(oe, re)
+    assert checked == set(gold) and len(checked) >= 64

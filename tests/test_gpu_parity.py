@@ -108,9 +108,11 @@ def test_p1e9_window_cross_congruences():
     """Every congruence, printed or generated, gives the identical residue (Sec. 3, 5)."""
     ps = u64(api.sieve(*W.P1E9_WINDOW))
     ref_b, ref_e = gpu_residues(ps)
-    # the paper's 13 congruences and the 6 generated ones (the default is BB249 + EE404)
+    # the paper's 13 congruences and the 6 generated ones, each against the
+    # default of a device prime list (BB30 + EE33); BB249 + EE404 is what the
+    # search picks for this window
     for nb, ne in (("BB1", "EE3"), ("BB2", "EE5"), ("BB6", "EE9"), ("BB9", "EE16"),
-                   ("BB16", "EE24"), ("BB22", "EE33"), ("BB30", "EE200"), ("BB476", "EE967"),
+                   ("BB16", "EE24"), ("BB22", "EE33"), ("BB249", "EE200"), ("BB476", "EE967"),
                    ("BB1115", "EE404")):
         gb, ge = gpu_residues(ps, {"cong_b": cong_id(nb), "cong_e": cong_id(ne)})
         assert np.array_equal(gb, ref_b), nb
@@ -180,12 +182,12 @@ def test_launch_shapes_agree():
     ps = np.concatenate([u64(api.sieve(10**6, 10**6 + 3000)), u64(api.sieve(2**31, 2**31 + 400)),
                          u64(api.sieve(2**36 - 300, 2**36))])
     ref_b, ref_e = gpu_residues(ps)
-    for opt in ({"ilp": 1}, {"ilp": 4}, {"tile_terms": 97, "max_tiles": 4096},
+    for opt in ({"ilp": 1}, {"arith": 9, "ilp": 4}, {"tile_terms": 97, "max_tiles": 4096},
                 {"tile_terms": 1 << 20, "max_tiles": 1}, {"blocks_per_sm": 1},
-                {"arith": 1}, {"arith": 2}, {"arith": 4}, {"arith": 9, "ilp": 1},
+                {"arith": 1}, {"arith": 2}, {"arith": 4}, {"arith": 9}, {"arith": 9, "ilp": 1},
                 {"arith": 9, "tile_terms": 5000, "max_tiles": 64},
                 {"block": 32}, {"block": 96, "ilp": 1}, {"block": 128},
-                *({"arith": a} for a in range(10, 24)),
+                *({"arith": a} for a in (*range(12, 19), 21, 23, *range(32, 37))),
                 *({"arith": a, "ilp": i} for a in range(25, 32) for i in (1, 2))):
         gb, ge = gpu_residues(ps, opt)
         assert np.array_equal(gb, ref_b), opt

@@ -149,3 +149,45 @@ def test_count_terms_matches_rows(T):
         return tot
     assert tb == terms(T["BB30"][3]) and te == terms(T["EE33"][3])
     assert abs(tb / p - 227 / 6480) < 1e-6 and abs(te / p - 27 / 512) < 1e-6
+
+
+def _inverse_power_prefix(p, e):
+    """prefix[s] = sum_{0<i<=s} i^-e mod p for 0 <= s <= (p-1)/2, by Fermat
+    inverses in numpy (p < 2^26, so every product fits 64 bits)."""
+    import numpy as np
+    s = np.arange(1, (p - 1) // 2 + 1, dtype=np.uint64)
+    inv, base, k = np.ones_like(s), s.copy(), p - 2
+    while k:
+        if k & 1:
+            inv = inv * base % np.uint64(p)
+        base = base * base % np.uint64(p)
+        k >>= 1
+    t = np.ones_like(s)
+    for _ in range(e):
+        t = t * inv % np.uint64(p)
+    pre = np.zeros(s.size + 1, dtype=np.uint64)
+    np.cumsum(t, out=pre[1:])  # < 2^26 * 2^25: no overflow
+    return pre % np.uint64(p)
+
+
+@pytest.mark.parametrize("p", [12_000_017, 31_000_003])
+def test_generated_congruences_at_primes_where_every_row_has_terms(T, orc, p):
+    """The generated congruences' narrowest rows are empty for every p < 700, so
+    the definition test above cannot see a wrong coefficient there.  At these
+    primes every row of every congruence holds at least one term: each one,
+    evaluated with exact integers, must give the oracle's B_{p-3}
+    (Stafford-Vandiver, eqn 2.4) and E_{p-3} (Glaisher, eqn 4.1)."""
+    assert is_prime(p)
+    want = {0: orc.bernoulli_sv(p), 1: orc.euler_glaisher(p)}
+    pre = {3: _inverse_power_prefix(p, 3), 2: _inverse_power_prefix(p, 2)}
+    for name in sorted(GENERATED) + ["BB30", "EE33"]:
+        cid, kind, lhs, rows = T[name]
+        e = 3 if kind == 0 else 2
+        rhs = 0
+        for terms, xn, xd, yn, yd in rows:
+            lo = xn * p // xd + 1                      # first s above x p
+            hi = (yn * p + yd - 1) // yd - 1           # last s below y p
+            assert hi >= lo, (name, p, xn, xd, yn, yd)  # the row is not empty
+            S = (int(pre[e][hi]) - int(pre[e][lo - 1])) % p
+            rhs += _coef(terms, p, e) * S
+        assert rhs * pow(lhs, -1, p) % p == want[kind], (name, p)
