@@ -47,8 +47,16 @@ IMAD_SLOTS_PER_MODMUL64 = 17
 # run is that busy share scaled by the run's own terms per SM per clock.  Set an entry to None
 # whenever its kernel changes, until it is captured again.
 PIPE_PROFILE = {
-    "accumulate_m31": None,
-    "accumulate_m64": None,
+    # k_accumulate<0,2,31>: 492 primes of [1062200000, 1062210000), BB249 + EE404, 3.1220e10 terms,
+    # 15.424 ms at 2.061 GHz; IMAD pipe 76.28 %, ALU 70.79 % of elapsed; 9.1392 MB read, 0 written
+    "accumulate_m31": {"imad_pct": 0.7628, "alu_pct": 0.7079, "terms_per_clk_sm": 6.461,
+                       "dram_bytes_per_prime": 9139200 / 492,
+                       "profile": "profiles/accumulate_m31_p1e9_small.md"},
+    # k_accumulate_m64cap<9,128>: 17 primes of [1e11 - 1e4, 1e11 - 9500), BB1115 + EE967,
+    # 8.4045e10 terms, 63.003 ms at 2.083 GHz; IMAD pipe 81.69 %, ALU 59.21 %; 1.8941 MB read
+    "accumulate_m64": {"imad_pct": 0.8169, "alu_pct": 0.5921, "terms_per_clk_sm": 4.215,
+                       "dram_bytes_per_prime": 1894144 / 17,
+                       "profile": "profiles/accumulate_m64_top_window.md"},
 }
 
 

@@ -454,19 +454,17 @@ __device__ __forceinline__ void tile_m64(const PrimeCtx &ctx, uint64_t start, ui
 //
 // The grouped scheme of the 32-bit path is used with larger groups here: the
 // group polynomials G0, G1 are stepped with plain 64-bit additions and no
-// reduction, and every BLK groups the tables are brought back below 10 p by
-// an approximate Barrett step (quotient from the high word times
-// floor(2^62 / p)).  Starting below 10 p, entry j of a degree-D table grows
-// over B steps to at most 10 p sum_{i <= D-j} C(B, i) <= 10 p 2^B, so with
-// BLK = 16 every entry stays below 10 p 2^16 < 2^57 (p < 2^37), whatever D.
+// reduction, and every BLK groups the tables are brought back below 6 p by an
+// approximate Barrett step (quotient from the high word times floor(2^62 / p),
+// m64_shrink_q; the earlier, longer form m64_shrink leaves them below 10 p).
+// Starting below 10 p, entry j of a degree-D table grows over B steps to at
+// most 10 p sum_{i <= D-j} C(B, i) <= 10 p 2^B, so with BLK = 16 every entry
+// stays below 10 p 2^16 < 2^57 (p < 2^37), whatever D.
 //
 // The scheme is parametrised by the group sizes (KB terms per group for the
 // cubes of the Bernoulli sums, KE for the squares of the Euler sums), the
-// shrink interval BLK and two ablation flags:
-//   1  difference-table additions written as three-input adds with a runtime
-//      zero, which keeps them on the integer ALU (off the multiply pipe);
-//   2  REDC rounds without zero-extended addends: the carry out of the
-//      cleared low word is (low word != 0), added to a high product.
+// shrink interval BLK and flags: 4 and 8 write (part of) the table additions
+// as PTX carry chains (M64Split below), 16 selects the four-step shrink.
 // A group costs the same 41 multiply-pipe slots whatever K, so larger groups
 // cut the products per term; the tables cost 2 (D_A + D_B) additions per
 // group and registers, which bound K.
@@ -511,15 +509,6 @@ __device__ __forceinline__ uint64_t m64_redc2(uint32_t T0, uint64_t TY, const M6
   const uint64_t B = umad_wide(m1, K.p0, (uint64_t)ulo(U));   // low word is 0
   return umad_wide(m1, K.p1, (uint64_t)uhi(U)) + uhi(B);      // (U + m1 p) / 2^32
 }
-// the same without zero-extended addends: T0 + lo(m0 p0) is 0 or 2^32, so its
-// carry is (T0 != 0) and only hi(m0 p0) enters the next word
-__device__ __forceinline__ uint64_t m64_redc2_nz(uint32_t T0, uint64_t TY, const M64K &K) {
-  const uint32_t m0 = T0 * K.q;
-  const uint64_t U = umad_wide(m0, K.p1, TY) + (uint64_t)(__umulhi(m0, K.p0) + (T0 != 0u));
-  const uint32_t u0 = ulo(U), u1 = uhi(U);
-  const uint32_t m1 = u0 * K.q;
-  return umul_wide(m1, K.p1) + (uint64_t)u1 + (uint64_t)(__umulhi(m1, K.p0) + (u0 != 0u));
-}
 // T = c g as (T0, TY); c < p + 2^31, g < 2^57
 __device__ __forceinline__ void m64_prod(uint64_t c, uint64_t g, uint32_t &T0, uint64_t &TY) {
   const uint32_t c0 = ulo(c), c1 = uhi(c), g0 = ulo(g), g1 = uhi(g);
@@ -551,9 +540,21 @@ __device__ __forceinline__ uint64_t m64_shrink(uint64_t v, const M64K &K) {
   return v - qp;
 }
 
+// v < 2^58  ->  v' = v (mod p) with v' < 6 p, in four multiply-pipe steps: the
+// quotient q = hi(4 hi(v) floor(2^62 / p)) is at most floor(v / p) and short
+// of it by less than 5.25, and v - q p is formed modulo 2^64 (where it is
+// exact) as v + q (2^64 - p): one wide multiply-add for the low word of
+// 2^64 - p, one low multiply-add into the high word for its high word.
+__device__ __forceinline__ uint64_t m64_shrink_q(uint64_t v, const M64K &K, uint32_t np0,
+                                                 uint32_t np1) {
+  const uint32_t q = __umulhi(uhi(v) << 2, K.mhi);
+  const uint64_t r = umad_wide(q, np0, v);
+  return upack(ulo(r), uhi(r) + q * np1);
+}
+
 // group sizes, shrink interval and flags of each 64-bit formulation (arith)
 template <int AR> struct M64Form {  // 9: the default
-  static constexpr int KB = 8, KE = 10, BLK = 16, V = 0;
+  static constexpr int KB = 8, KE = 10, BLK = 16, V = 16;
 };
 // 32..36: form 9 with its 64-bit table additions written as PTX carry chains
 // (add.cc / addc on the two words) for a share of the entries, in quarters
@@ -562,16 +563,19 @@ template <int AR> struct M64Form {  // 9: the default
 // makes that word's add a three-input add with carry in -- an instruction
 // only the integer ALU has, so the entry stays off the multiply pipe.
 template <int AR> struct M64Split { static constexpr int NFQ = 0; };
-template <> struct M64Form<32> : M64Form<9> { static constexpr int V = 4; };
-template <> struct M64Form<33> : M64Form<9> { static constexpr int V = 8; };
-template <> struct M64Form<34> : M64Form<9> { static constexpr int V = 8; };
-template <> struct M64Form<35> : M64Form<9> { static constexpr int V = 8; };
-template <> struct M64Form<36> : M64Form<9> { static constexpr int V = 8; };
+template <> struct M64Form<32> : M64Form<9> { static constexpr int V = 4 | 16; };
+template <> struct M64Form<33> : M64Form<9> { static constexpr int V = 8 | 16; };
+template <> struct M64Form<34> : M64Form<9> { static constexpr int V = 8 | 16; };
+template <> struct M64Form<35> : M64Form<9> { static constexpr int V = 8 | 16; };
+template <> struct M64Form<36> : M64Form<9> { static constexpr int V = 8 | 16; };
 template <> struct M64Split<32> { static constexpr int NFQ = 4; };
 template <> struct M64Split<33> { static constexpr int NFQ = 4; };
 template <> struct M64Split<34> { static constexpr int NFQ = 2; };
 template <> struct M64Split<35> { static constexpr int NFQ = 1; };
 template <> struct M64Split<36> { static constexpr int NFQ = 3; };
+// 37: form 9 with the earlier shrink (m64_shrink: a wide quotient, a 64-bit
+// product and a 64-bit subtraction) in place of the four-step one (flag 16)
+template <> struct M64Form<37> : M64Form<9> { static constexpr int V = 0; };
 
 // a += b (64-bit) as an explicit carry chain over the two 32-bit words
 __device__ __forceinline__ void add64_cc(uint64_t &a, uint64_t b) {
@@ -596,19 +600,19 @@ __device__ __forceinline__ void add64_cc_z(uint64_t &a, uint64_t b, uint32_t z) 
       : "+l"(a)
       : "l"(b), "r"(z));
 }
-template <> struct M64Form<12> { static constexpr int KB = 2, KE = 3, BLK = 8, V = 0; };
-template <> struct M64Form<13> { static constexpr int KB = 3, KE = 4, BLK = 16, V = 0; };
-template <> struct M64Form<14> { static constexpr int KB = 4, KE = 5, BLK = 16, V = 0; };
-template <> struct M64Form<15> { static constexpr int KB = 5, KE = 6, BLK = 16, V = 0; };
-template <> struct M64Form<16> { static constexpr int KB = 6, KE = 8, BLK = 16, V = 0; };
-template <> struct M64Form<17> { static constexpr int KB = 7, KE = 9, BLK = 16, V = 0; };
+template <> struct M64Form<12> { static constexpr int KB = 2, KE = 3, BLK = 8, V = 16; };
+template <> struct M64Form<13> { static constexpr int KB = 3, KE = 4, BLK = 16, V = 16; };
+template <> struct M64Form<14> { static constexpr int KB = 4, KE = 5, BLK = 16, V = 16; };
+template <> struct M64Form<15> { static constexpr int KB = 5, KE = 6, BLK = 16, V = 16; };
+template <> struct M64Form<16> { static constexpr int KB = 6, KE = 8, BLK = 16, V = 16; };
+template <> struct M64Form<17> { static constexpr int KB = 7, KE = 9, BLK = 16, V = 16; };
 // 18 and 21: the register budget.  Form 9 runs under a cap of kM64MaxReg
 // registers per thread (16 resident warps per SM, a few bytes of spill in
 // the setup); 18 is form 9 without the cap (8 warps), 21 groups of 9 / 11
 // under the cap of 128.
 constexpr int kM64MaxReg = 128;
 template <> struct M64Form<18> : M64Form<9> {};
-template <> struct M64Form<21> { static constexpr int KB = 9, KE = 11, BLK = 16, V = 0; };
+template <> struct M64Form<21> { static constexpr int KB = 9, KE = 11, BLK = 16, V = 16; };
 
 // a b 2^-64 mod p, below p + 2^12 for a, b < 2^38
 __device__ __forceinline__ uint64_t m64_mm(uint64_t a, uint64_t b, const M64K &K) {
@@ -644,8 +648,9 @@ __device__ __forceinline__ void tile_m64_grouped(const PrimeCtx &ctx, uint64_t s
   KK.p1 = (uint32_t)(ctx.p >> 32);
   KK.q = 0u - (uint32_t)ctx.q;  // -p^-1 mod 2^32
   KK.mhi = (uint32_t)((1ull << 62) / ctx.p);
-  const uint64_t z64 = (V & 1) ? (uint64_t)(ctx.flags >> 16) : 0ull;  // runtime zero
   const uint32_t z32 = ctx.flags >> 16;                                // runtime zero
+  const uint64_t np = 0ull - ctx.p;  // 2^64 - p, for the four-step shrink
+  const uint32_t np0 = (uint32_t)np, np1 = (uint32_t)(np >> 32);
   constexpr int NF = (DA + DB) * M64Split<AR>::NFQ / 4;  // carry-chain entries
   const uint64_t nch = 32 * ILP;
   const uint64_t len = n / nch;
@@ -734,9 +739,9 @@ __device__ __forceinline__ void tile_m64_grouped(const PrimeCtx &ctx, uint64_t s
         uint32_t T0;
         uint64_t TY;
         m64_prod(c0[k], ga[k][0], T0, TY);
-        const uint64_t n0 = (V & 2) ? m64_redc2_nz(T0, TY, KK) : m64_redc2(T0, TY, KK);
+        const uint64_t n0 = m64_redc2(T0, TY, KK);
         m64_prod2(c1[k], ga[k][0], c0[k], gb[k][0], T0, TY);
-        c1[k] = (V & 2) ? m64_redc2_nz(T0, TY, KK) : m64_redc2(T0, TY, KK);
+        c1[k] = m64_redc2(T0, TY, KK);
         c0[k] = n0;
 #pragma unroll
         for (int j = 0; j < DA; ++j) {
@@ -744,7 +749,7 @@ __device__ __forceinline__ void tile_m64_grouped(const PrimeCtx &ctx, uint64_t s
             if (V & 8) add64_cc_z(ga[k][j], ga[k][j + 1], z32);
             else add64_cc(ga[k][j], ga[k][j + 1]);
           } else {
-            ga[k][j] = ga[k][j] + ga[k][j + 1] + z64;
+            ga[k][j] = ga[k][j] + ga[k][j + 1];
           }
         }
 #pragma unroll
@@ -753,7 +758,7 @@ __device__ __forceinline__ void tile_m64_grouped(const PrimeCtx &ctx, uint64_t s
             if (V & 8) add64_cc_z(gb[k][j], gb[k][j + 1], z32);
             else add64_cc(gb[k][j], gb[k][j + 1]);
           } else {
-            gb[k][j] = gb[k][j] + gb[k][j + 1] + z64;
+            gb[k][j] = gb[k][j] + gb[k][j + 1];
           }
         }
       }
@@ -761,9 +766,11 @@ __device__ __forceinline__ void tile_m64_grouped(const PrimeCtx &ctx, uint64_t s
 #pragma unroll
     for (int k = 0; k < ILP; ++k) {
 #pragma unroll
-      for (int j = 0; j < DA; ++j) ga[k][j] = m64_shrink(ga[k][j], KK);
+      for (int j = 0; j < DA; ++j)
+        ga[k][j] = (V & 16) ? m64_shrink_q(ga[k][j], KK, np0, np1) : m64_shrink(ga[k][j], KK);
 #pragma unroll
-      for (int j = 0; j < DB; ++j) gb[k][j] = m64_shrink(gb[k][j], KK);
+      for (int j = 0; j < DB; ++j)
+        gb[k][j] = (V & 16) ? m64_shrink_q(gb[k][j], KK, np0, np1) : m64_shrink(gb[k][j], KK);
     }
     g += nb;
   }

@@ -148,13 +148,14 @@ wv_status resolve_config(const wv_options *opt, bool want_b, bool want_e, Residu
 //   additions; 29, 30, 31 groups of 3 cubes, 4 squares, or both (31: the
 //   default).  64-bit path (2^30 <= p < 2^37): 1, 2, 4 single terms; every
 //   other value runs the grouped default (8 cubes / 10 squares) except 12..18
-//   and 21, other group sizes and register budgets, and 32..36, the default
-//   with its table additions as PTX carry chains.  23: the paper's own
+//   and 21, other group sizes and register budgets, 32..36, the default
+//   with its table additions as PTX carry chains, and 37, the default with
+//   the earlier, longer shrink of its tables.  23: the paper's own
 //   arithmetic on both paths.
-constexpr const char *kArithList = "1, 2, 4, 9, 12..18, 21, 23, 25..36";
+constexpr const char *kArithList = "1, 2, 4, 9, 12..18, 21, 23, 25..37";
 inline bool arith_selectable(int a) {
   return a == 1 || a == 2 || a == 4 || a == 9 || (a >= 12 && a <= 18) || a == 21 || a == 23 ||
-         (a >= 25 && a <= 36);
+         (a >= 25 && a <= 37);
 }
 
 // Residues for n primes (device array), asynchronous on s.

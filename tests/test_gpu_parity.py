@@ -152,14 +152,6 @@ def test_top_window_cross_congruences():
     assert not np.any(gb == 0) and not np.any(ge == 0)  # Theorem 1.1
 
 
-@pytest.mark.skipif(not os.environ.get("WV_SLOW_ORACLE"), reason="oracle needs ~20 core-minutes per prime at 1e11")
-def test_top_window_oracle_spot_check(orc):
-    sub = W.top_window_subset(seed=5, k=int(os.environ.get("WV_SLOW_ORACLE_K", "2")))
-    gb, ge = gpu_residues(sub)
-    ob, oe = orc.residues(sub)
-    assert np.array_equal(gb, ob) and np.array_equal(ge, oe)
-
-
 def test_edge_cases(orc):
     ps = [5, 7, 11, 13, 17, 19, 23]
     gb, ge = gpu_residues(ps)
@@ -187,7 +179,7 @@ def test_launch_shapes_agree():
                 {"arith": 1}, {"arith": 2}, {"arith": 4}, {"arith": 9}, {"arith": 9, "ilp": 1},
                 {"arith": 9, "tile_terms": 5000, "max_tiles": 64},
                 {"block": 32}, {"block": 96, "ilp": 1}, {"block": 128},
-                *({"arith": a} for a in (*range(12, 19), 21, 23, *range(32, 37))),
+                *({"arith": a} for a in (*range(12, 19), 21, 23, *range(32, 38))),
                 *({"arith": a, "ilp": i} for a in range(25, 32) for i in (1, 2))):
         gb, ge = gpu_residues(ps, opt)
         assert np.array_equal(gb, ref_b), opt

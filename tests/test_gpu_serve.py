@@ -1,6 +1,7 @@
 """The serving loop: queries submitted while others run share epochs on the
-device (continuous batching), and each result equals the same query computed
-alone, bit for bit."""
+device (continuous batching); each result equals the same query computed
+alone, bit for bit, and the CPU oracle's residues (computed here for small
+primes, stored by tests/golden/make_oracle_residues.py for large ones)."""
 import time
 
 import numpy as np
@@ -12,7 +13,36 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
+from conftest import read_golden  # noqa: E402
 from paper_2101_11157_gb300 import api, wv  # noqa: E402
+
+TOP_PRIME = 99_999_998_237  # one of the 8 stored primes of [1e11 - 1e4, 1e11)
+
+
+def _gold():
+    out = {}
+    for name in ("serve_sample_residues.txt", "top_window_subset_residues.txt"):
+        out.update({int(p): (int(b), int(e)) for p, b, e in read_golden(name)})
+    return out
+
+
+def _oracle_check(orc, gold, pr, rb, re):
+    """Compare a served result with the oracle: every prime below 1e8 of a
+    small result (a seeded sample of 24 of a larger one) recomputed here, and
+    every prime with stored residues.  Returns how many primes were checked."""
+    small = [i for i, p in enumerate(pr) if int(p) < 10**8]
+    if len(small) > 24:
+        small = sorted(np.random.default_rng(3).choice(small, 24, replace=False))
+    n = 0
+    if small:
+        ob, oe = orc.residues(pr[small])
+        assert np.array_equal(rb[small], ob) and np.array_equal(re[small], oe)
+        n += len(small)
+    for i, p in enumerate(pr):
+        if int(p) in gold:
+            assert (int(rb[i]), int(re[i])) == gold[int(p)], int(p)
+            n += 1
+    return n
 
 
 def _alone_range(lo, hi):
@@ -38,7 +68,7 @@ QUERIES = [("range", 2 * 10**9, 2 * 10**9 + 30000),   # long-running, 64-bit pat
            ("range", 10**7, 10**7 + 20000),
            ("prime", 2**30 + 3, None),
            ("range", 999_999_000, 1_000_001_000),
-           ("prime", 99_999_999_977, None),              # near the top of the search range
+           ("prime", TOP_PRIME, None),                   # near the top of the search range
            ("range", 10, 10)]                            # empty
 
 
@@ -53,7 +83,8 @@ def _run(server, stagger):
     return ids, infos
 
 
-def test_serving_results_equal_alone_and_overlap():
+def test_serving_results_equal_alone_and_overlap(orc):
+    gold = _gold()
     s = wv.wv_server_create(epoch_terms=2e9)
     try:
         ids, infos = _run(s, stagger=True)
@@ -63,6 +94,10 @@ def test_serving_results_equal_alone_and_overlap():
             ref = _alone_range(a, b) if kind == "range" else _alone_prime(a)
             assert np.array_equal(pr, ref[0]) and np.array_equal(rb, ref[1]) and np.array_equal(re, ref[2])
             assert info["n_primes"] == pr.size
+            # against the oracle: every non-empty query has primes it checks
+            assert _oracle_check(orc, gold, pr, rb, re) >= min(pr.size, 1), (kind, a, b)
+        # the long range's primes are the oracle's sieve of it
+        assert orc.sieve(2 * 10**9, 2 * 10**9 + 30000).tolist() == wv.wv_server_result(s, ids[0])[0].tolist()
         # the known zeros came back
         assert wv.wv_server_result(s, ids[1])[2][0] == 0
         assert wv.wv_server_result(s, ids[3])[1][0] == 0
@@ -99,10 +134,13 @@ def test_small_query_backfills_past_a_blocked_large_one():
         ia, ib, ic = (wv.wv_server_wait(s, q, 300.0) for q in (a, b, c))
         assert ic["t_admit"] < ib["t_admit"] and ic["t_done"] < ib["t_admit"]
         assert ib["t_admit"] >= ia["t_done"] - 1e-3
+        gold = _gold()
         for q, (lo, hi) in ((a, (2 * 10**9, 2 * 10**9 + 30000)), (b, (2 * 10**9 + 30000, 2 * 10**9 + 60000))):
             pr, rb, re = wv.wv_server_result(s, q)
             ref = _alone_range(lo, hi)
             assert np.array_equal(pr, ref[0]) and np.array_equal(rb, ref[1]) and np.array_equal(re, ref[2])
+            assert sum(int(p) in gold for p in pr) == 6
+            assert _oracle_check(None, gold, pr, rb, re) == 6
         assert wv.wv_server_result(s, c)[2][0] == 0
     finally:
         wv.wv_server_destroy(s)
