@@ -11,8 +11,11 @@ residues); modmul/s counts two modular multiplications per summed term
 (eqn 3.12).
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-For N > 1 launch with torch.distributed.run; each rank takes its own
-1e5-wide window (weak scaling, no data-path collective).
+For N > 1 launch with torch.distributed.run; the N ranks search the N
+consecutive 1e5-wide windows from 1062200000, split into contiguous shards of
+equal estimated cost by the library's range sharding (weak scaling, no
+data-path collective; NCCL only for the max-over-ranks time and the prime
+count).
 """
 from __future__ import annotations
 
@@ -52,11 +55,8 @@ PIPE_PROFILE = {
     "accumulate_m31": {"imad_pct": 0.7628, "alu_pct": 0.7079, "terms_per_clk_sm": 6.461,
                        "dram_bytes_per_prime": 9139200 / 492,
                        "profile": "profiles/accumulate_m31_p1e9_small.md"},
-    # k_accumulate_m64cap<9,128>: 17 primes of [1e11 - 1e4, 1e11 - 9500), BB1115 + EE967,
-    # 8.4045e10 terms, 63.003 ms at 2.083 GHz; IMAD pipe 81.69 %, ALU 59.21 %; 1.8941 MB read
-    "accumulate_m64": {"imad_pct": 0.8169, "alu_pct": 0.5921, "terms_per_clk_sm": 4.215,
-                       "dram_bytes_per_prime": 1894144 / 17,
-                       "profile": "profiles/accumulate_m64_top_window.md"},
+    # k_accumulate_m64cap<9,128>: not yet captured since the four-step shrink of its tables
+    "accumulate_m64": None,
 }
 
 
@@ -201,13 +201,16 @@ def gpu_arm(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     top = args.workload == "top"
-    if top:  # rank r takes the r-th 1e4-wide window below 1e11
+    # N ranks search N windows' worth of the range (weak scaling), split into contiguous
+    # shards of equal estimated cost (sum of p) by the library's range sharding
+    from paper_2101_11157_gb300 import shard
+    if top:  # the ws 1e4-wide windows just below 1e11
         width = min(args.width, TOP_WIDTH)
-        lo = TOP_LO - rank * TOP_WIDTH
+        full = (TOP_LO - (ws - 1) * TOP_WIDTH, TOP_LO + width)
     else:
         width = args.width
-        lo = LO + rank * WIDTH
-    hi = lo + width
+        full = (LO, LO + (ws - 1) * WIDTH + width)
+    lo, hi = shard.shard_of(full[0], full[1], rank, ws)
     stream = torch.cuda.current_stream()
     props = torch.cuda.get_device_properties(local)
     sms = props.multi_processor_count
@@ -344,7 +347,11 @@ def gpu_arm(args):
                                   "peak_basis": f"{sms} SMs x {IMAD_PER_SM_CLK} IMAD lanes/clk x "
                                                 f"{clk_mhz:.0f} MHz / {slots} IMAD slots per "
                                                 f"{'64' if top else '32'}-bit Montgomery product"}})
-    total_primes = n_primes * ws
+    total_primes, total_modmuls = n_primes, modmuls_per_step
+    if dist:
+        t = torch.tensor([n_primes, modmuls_per_step], device="cuda", dtype=torch.int64)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        total_primes, total_modmuls = int(t[0].item()), int(t[1].item())
     value = total_primes / (ms / 1000.0)
     cong_names = [wv.wv_congruence_info(c)[0] for c in cong]
     line = {
@@ -357,8 +364,9 @@ def gpu_arm(args):
                                + (" (64-bit path, 2^30 <= p < 2^37)" if top else ""),
                    "primes_per_gpu": int(n_primes), "congruences": "+".join(cong_names),
                    "terms_per_step": int(tb + te), "parallelism": f"range-sharded x{ws}",
+                   "range": list(full), "shard": [lo, hi], "primes_all_gpus": int(total_primes),
                    "l2": "flushed between steps (256 MB write)"},
-        "modmul_per_s": modmuls_per_step * ws / (ms / 1000.0),
+        "modmul_per_s": total_modmuls / (ms / 1000.0),
         "roofline": roof,
         "e2e": {"value": total_primes / (e2e_step / 1000.0), "unit": "primes/s",
                 "h2d_bytes_per_step": int(n_primes * 8), "d2h_bytes_per_step": int(n_primes * 16),
