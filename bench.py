@@ -206,11 +206,11 @@ def gpu_arm(args):
     from paper_2101_11157_gb300 import shard
     if top:  # the ws 1e4-wide windows just below 1e11
         width = min(args.width, TOP_WIDTH)
-        full = (TOP_LO - (ws - 1) * TOP_WIDTH, TOP_LO + width)
+        span = (TOP_LO - (ws - 1) * TOP_WIDTH, TOP_LO + width)
     else:
         width = args.width
-        full = (LO, LO + (ws - 1) * WIDTH + width)
-    lo, hi = shard.shard_of(full[0], full[1], rank, ws)
+        span = (LO, LO + (ws - 1) * WIDTH + width)
+    lo, hi = shard.shard_of(span[0], span[1], rank, ws)
     stream = torch.cuda.current_stream()
     props = torch.cuda.get_device_properties(local)
     sms = props.multi_processor_count
@@ -319,13 +319,13 @@ def gpu_arm(args):
     clk_mhz = float((clocks or {}).get("sm_mhz") or sm_max)
     tpcs = (tb + te) / (acc_avg_ms / 1e3) / sms / (clk_mhz * 1e6) if acc_avg_ms else 0.0
     prof_k = PIPE_PROFILE.get(kname)
-    full = width == (TOP_WIDTH if top else WIDTH)
+    full_launch = width == (TOP_WIDTH if top else WIDTH)
     pipe_peak = sms * clk_mhz * 1e6  # IMAD-pipe cycles per second over all SMs
     if prof_k:
         frac = prof_k["imad_pct"] * tpcs / prof_k["terms_per_clk_sm"]
         roof = {"bound": "alu", "achieved": frac * pipe_peak, "peak": pipe_peak,
                 "unit": "IMAD-pipe cycles/s", "frac": frac,
-                "traffic": prof_k["dram_bytes_per_prime"] * n_primes if full else None,
+                "traffic": prof_k["dram_bytes_per_prime"] * n_primes if full_launch else None,
                 "traffic_basis": f"ncu dram__bytes_read.sum + dram__bytes_write.sum of {prof_k['profile']}, "
                                  "scaled by primes to this launch",
                 "frac_basis": f"IMAD-pipe busy {prof_k['imad_pct']:.3f} at {prof_k['terms_per_clk_sm']:.3f} "
@@ -364,7 +364,7 @@ def gpu_arm(args):
                                + (" (64-bit path, 2^30 <= p < 2^37)" if top else ""),
                    "primes_per_gpu": int(n_primes), "congruences": "+".join(cong_names),
                    "terms_per_step": int(tb + te), "parallelism": f"range-sharded x{ws}",
-                   "range": list(full), "shard": [lo, hi], "primes_all_gpus": int(total_primes),
+                   "range": list(span), "shard": [lo, hi], "primes_all_gpus": int(total_primes),
                    "l2": "flushed between steps (256 MB write)"},
         "modmul_per_s": total_modmuls / (ms / 1000.0),
         "roofline": roof,

@@ -195,7 +195,8 @@ typedef struct {
                        into wide multiply-adds); 25..28 form 9 with none, 4, 6 or all of a
                        group's difference-table additions as ALU-only three-input adds
                        (9 itself: 4 of a Bernoulli group's 9 and 2 of an Euler group's
-                       10); 29, 30, 31 groups of 3 cubes, of 4 squares, or both.  64-bit
+                       10); 29, 30, 31 groups of 3 cubes, of 4 squares, or both; 39
+                       groups of 4 cubes / 5 squares.  64-bit
                        path (2^30 <= p < 2^37): 1, 2, 4 the single-term 64-bit kernel;
                        12..18 and 21 other group sizes, shrink intervals and register
                        budgets; 32..36 the default with a quarter to all of its 64-bit

@@ -3,8 +3,8 @@
 // three-input adds that only the integer ALU executes (form 9 writes 4 of a
 // Bernoulli group's and 2 of an Euler group's that way), for ablation of the
 // balance between the ALU and the multiply pipe (25..28); and form 9 with
-// groups of 3 cubes, of 4 squares, or both (29..31).  The code is in
-// wv_accum.cuh.
+// groups of 3 cubes, of 4 squares, or both (29..31).  Groups of 4 / 5 (39)
+// are in wv_acc_m31y.cu.  The code is in wv_accum.cuh.
 #include "wv_accum.cuh"
 
 namespace wv {
@@ -15,6 +15,7 @@ AccKernel acc_kernel_m31x(int arith, int ilp) {
    : arith == 27 ? k_accumulate<false, I, 27> : arith == 28 ? k_accumulate<false, I, 28> \
    : arith == 29 ? k_accumulate<false, I, 29> : arith == 30 ? k_accumulate<false, I, 30> \
    : k_accumulate<false, I, 31>)
+  if (arith == 39) return acc_kernel_m31y(arith, ilp);
   return ilp == 1 ? WV_PICK(1) : WV_PICK(2);
 #undef WV_PICK
 }

@@ -928,6 +928,25 @@ __device__ __forceinline__ void tile_general(const PrimeCtx &ctx, uint64_t start
   r1 = c1;
 }
 
+// Group sizes (KC cubes, KS squares; 0: 2 cubes, 3 squares) and ALU-only
+// table additions per group (NFC of a Bernoulli group's, NFS of an Euler
+// group's) of each grouped 32-bit formulation.  9: 4 of 9 and 2 of 10 (the
+// fastest on GB300 of 0, 2..6 and all); 25: none, 26: 4 and 4, 27: 6 and 6,
+// 28: all (ablation).  29..31 are 9 with larger groups: 3 cubes (15
+// additions, 6 ALU-only), 4 squares (14 additions, 4 ALU-only), or both (31,
+// the default).  39: larger groups still, 4 cubes / 5 squares (21 and 18
+// additions, 6 and 4 ALU-only); of 4 / 5 with 8 / 6 ALU-only, 3 / 5 and 4 / 4
+// it was the fastest, and faster than 31 on long sums only.
+template <int AR> struct M31Form { static constexpr int KC = 0, KS = 0, NFC = 4, NFS = 2; };
+template <> struct M31Form<25> { static constexpr int KC = 0, KS = 0, NFC = 0, NFS = 0; };
+template <> struct M31Form<26> { static constexpr int KC = 0, KS = 0, NFC = 4, NFS = 4; };
+template <> struct M31Form<27> { static constexpr int KC = 0, KS = 0, NFC = 6, NFS = 6; };
+template <> struct M31Form<28> { static constexpr int KC = 0, KS = 0, NFC = 10, NFS = 10; };
+template <> struct M31Form<29> { static constexpr int KC = 3, KS = 0, NFC = 6, NFS = 2; };
+template <> struct M31Form<30> { static constexpr int KC = 0, KS = 4, NFC = 4, NFS = 4; };
+template <> struct M31Form<31> { static constexpr int KC = 3, KS = 4, NFC = 6, NFS = 4; };
+template <> struct M31Form<39> { static constexpr int KC = 4, KS = 5, NFC = 6, NFS = 4; };
+
 template <bool WIDE, int ILP, int AR>
 __device__ __forceinline__ void process_tile(const Plan &P, uint32_t g) {
   const int lane = threadIdx.x & 31;
@@ -942,16 +961,9 @@ __device__ __forceinline__ void process_tile(const Plan &P, uint32_t g) {
   int64_t r0, r1;
   // single-term form used beside the grouped one
   constexpr int AS = (AR == 5 || AR >= 8) ? 4 : AR;
-  // ALU-only table additions per group of the 32-bit grouped form, for the
-  // Bernoulli (cubes, 9 additions per group) and Euler (squares, 10) sums:
-  // 4 and 2 in the default 9 (the fastest on GB300 of 0, 2..6 and all);
-  // 25: none, 26: 4 and 4, 27: 6 and 6, 28: all (ablation).  29..31 are 9
-  // with larger groups: 3 cubes (15 additions, 6 ALU-only), 4 squares (14
-  // additions, 4 ALU-only), or both.
-  constexpr bool G3C = AR == 29 || AR == 31, G4S = AR == 30 || AR == 31;
-  constexpr int NFC = G3C ? 6 : (AR == 9 || AR >= 29) ? 4 : AR == 26 ? 4 : AR == 27 ? 6 : AR == 28 ? 10 : 0;
-  constexpr int NFS = G4S ? 4 : (AR == 9 || AR >= 29) ? 2 : AR == 26 ? 4 : AR == 27 ? 6 : AR == 28 ? 10 : 0;
-  constexpr int KC = G3C ? 3 : 0, KS = G4S ? 4 : 0;
+  // group sizes and ALU-only table additions of the grouped 32-bit form
+  constexpr int NFC = M31Form<AR>::NFC, NFS = M31Form<AR>::NFS;
+  constexpr int KC = M31Form<AR>::KC, KS = M31Form<AR>::KS;
   const bool grp_ok = n >= 32ull * ILP * kGroupMinChain;
   if (AR == 24) {
     tile_general(ctx, start, n, j < P.rows_b ? P.gen_e_b : P.gen_e_e, r0, r1);
@@ -1095,6 +1107,7 @@ AccKernel acc_kernel_m64w(int arith, int ilp);
 AccKernel acc_kernel_m64v(int arith, int ilp);  // forms 32..36 (w falls through to v)
 // 32-bit path: formulation 9 with other ALU-only splits or group sizes (arith 25..31), ILP 1 or 2
 AccKernel acc_kernel_m31x(int arith, int ilp);
+AccKernel acc_kernel_m31y(int arith, int ilp);  // form 39 (x falls through to y)
 // serving-loop epoch kernels (the default formulations: 31 on the 32-bit path,
 // 9 with one chain per thread on the 64-bit path)
 EpochKernel epoch_kernel(bool wide, int ilp);

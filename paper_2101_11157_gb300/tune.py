@@ -46,6 +46,8 @@ GRIDS = {
     # group sizes of the 32-bit form: 9 (2 cubes / 3 squares) against 3 cubes, 4 squares, both (31,
     # the default)
     "groups": [{"arith": a, "ilp": i} for a, i in itertools.product((9, 29, 30, 31), (2, 1))],
+    # groups of 4 cubes / 5 squares (39) against the default 31
+    "groups2": [{"arith": a, "ilp": 2} for a in (31, 39)],
     # resident blocks per SM (persistent grid) for the 32-bit forms 9 and 26
     "occ": [{"arith": a, "ilp": i, "blocks_per_sm": b}
             for a, i, b in itertools.product((9, 26), (2, 1), (3, 4, 5, 6))],

@@ -180,7 +180,7 @@ def test_launch_shapes_agree():
                 {"arith": 9, "tile_terms": 5000, "max_tiles": 64},
                 {"block": 32}, {"block": 96, "ilp": 1}, {"block": 128},
                 *({"arith": a} for a in (*range(12, 19), 21, 23, *range(32, 38))),
-                *({"arith": a, "ilp": i} for a in range(25, 32) for i in (1, 2))):
+                *({"arith": a, "ilp": i} for a in (*range(25, 32), 39) for i in (1, 2))):
         gb, ge = gpu_residues(ps, opt)
         assert np.array_equal(gb, ref_b), opt
         assert np.array_equal(ge, ref_e), opt
