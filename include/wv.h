@@ -178,7 +178,7 @@ typedef struct {
   int block;        /* accumulation block size (threads): 32..256, multiple of 32;
                        default 256.  Smaller blocks release their registers warp by
                        warp at the end of a launch and round occupancy differently */
-  int ilp;          /* independent accumulator chains per thread for p < 2^30: 1, 2 or 4
+  int ilp;          /* independent accumulator chains per thread for p < 2^31: 1, 2 or 4
                        (4 only with arith 9, 12..18, 21 or 23; default 2).  The grouped 64-bit forms
                        (arith >= 9) run one chain per thread; the single-term 64-bit
                        form takes this value too */
@@ -188,7 +188,8 @@ typedef struct {
                        sum) so that one launch still holds ~1e5 tiles */
   int blocks_per_sm;/* persistent grid = SMs x this */
   int arith;        /* hot-loop formulation (default 31).  Every value gives the same
-                       residues; the others exist for ablation.  32-bit path (p < 2^30):
+                       residues; the others exist for ablation.  32-bit path (p < 2^31;
+                       signed words below 2^30, unsigned from 2^30 to 2^31):
                        1, 2, 4 single terms (1: shared t p^-1; 2: one wide product and
                        REDC; 4: 2 with the additions as ALU three-input adds); 9
                        grouped terms (2 cubes / 3 squares per eqn 3.14 step, REDC folded
@@ -197,7 +198,7 @@ typedef struct {
                        (9 itself: 4 of a Bernoulli group's 9 and 2 of an Euler group's
                        10); 29, 30, 31 groups of 3 cubes, of 4 squares, or both; 39
                        groups of 4 cubes / 5 squares.  64-bit
-                       path (2^30 <= p < 2^37): 1, 2, 4 the single-term 64-bit kernel;
+                       path (2^31 <= p < 2^37): 1, 2, 4 the single-term 64-bit kernel;
                        12..18 and 21 other group sizes, shrink intervals and register
                        budgets; 32..36 the default with a quarter to all of its 64-bit
                        table additions as PTX carry chains (32: plain; 33..36: with a

@@ -29,7 +29,7 @@ struct Plan {
   const uint64_t *primes;       // caller's primes (chunk base)
   uint64_t *out_b, *out_e;      // caller's outputs (chunk base), may be null
   PrimeCtx *ctx;                // per slot (M31 slots first, then M64)
-  uint32_t *flag, *pos, *n31;   // flag: p-bucket per prime; n31: slots with p < 2^30
+  uint32_t *flag, *pos, *n31;   // flag: p-bucket per prime; n31: slots with p < 2^31
   uint32_t *bk;                 // 3 x 64 words: bucket counts, offsets, cursors
   uint64_t *seg_lo, *seg_cnt;   // per segment (slot * rows_pp + row)
   uint32_t *seg_tiles, *seg_first;
@@ -64,6 +64,68 @@ __device__ __forceinline__ void warp_merge(const Mont &M, int64_t &a0, int64_t &
     M.combine(a0, a1, b0, b1);
   }
 }
+
+// Unsigned 32-bit words: wide products and word access in PTX.
+__device__ __forceinline__ uint64_t umul_wide(uint32_t a, uint32_t b) {
+  uint64_t d;
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(d) : "r"(a), "r"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t umad_wide(uint32_t a, uint32_t b, uint64_t c) {
+  uint64_t d;
+  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ uint32_t ulo(uint64_t v) {
+  uint32_t lo;
+  asm("{\n\t.reg .b32 t;\n\tmov.b64 {%0, t}, %1;\n\t}" : "=r"(lo) : "l"(v));
+  return lo;
+}
+__device__ __forceinline__ uint32_t uhi(uint64_t v) {
+  uint32_t hi;
+  asm("{\n\t.reg .b32 t;\n\tmov.b64 {t, %0}, %1;\n\t}" : "=r"(hi) : "l"(v));
+  return hi;
+}
+__device__ __forceinline__ uint64_t upack(uint32_t lo, uint32_t hi) {
+  uint64_t v;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(v) : "r"(lo), "r"(hi));
+  return v;
+}
+
+// 2^30 <= p < 2^31: unsigned 32-bit Montgomery with R' = 2^32 and canonical
+// values in [0, p).  A product a b < p^2 < 2^62 plus m p < 2^63 stays below
+// 2^64, and (a b + m p) / 2^32 < 1.5 p, so one conditional subtraction makes
+// it canonical; sums of two products (< 2 p^2) reduce below 2 p the same way.
+// The constants of R' (R' mod p, R'^2 mod p) are formed here, once per chain,
+// since the context of such a prime carries those of R = 2^64.
+struct U31Set {
+  uint32_t up, qn;               // p, -p^-1 mod 2^32
+  uint32_t one, r2, c1, c2, c6;  // R', R'^2 mod p; the plain constants 1, 2, 6
+  __device__ __forceinline__ explicit U31Set(const PrimeCtx &c)
+      : up((uint32_t)c.p), qn(0u - (uint32_t)c.q), c1(1u), c2(2u), c6(6u) {
+    one = (uint32_t)((1ull << 32) % c.p);
+    r2 = (uint32_t)(((uint64_t)one * one) % c.p);
+  }
+  __device__ __forceinline__ uint32_t redc(uint64_t w) const {  // w < 2^63: w R'^-1, < 2 p in, [0, p) out
+    const uint32_t m = ulo(w) * qn;
+    const uint32_t t = uhi(umad_wide(m, up, w));
+    return min(t, t - up);
+  }
+  __device__ __forceinline__ uint32_t mul(uint32_t a, uint32_t b) const {  // a b R'^-1
+    return redc(umul_wide(a, b));
+  }
+  __device__ __forceinline__ uint32_t mulmod(uint32_t a, uint32_t b) const {  // a b
+    return mul(mul(a, b), r2);
+  }
+  __device__ __forceinline__ uint32_t add(uint32_t a, uint32_t b) const {
+    const uint32_t x = a + b;
+    return min(x, x - up);
+  }
+  __device__ __forceinline__ uint32_t sub(uint32_t a, uint32_t b) const {
+    const uint32_t x = a - b;
+    return min(x, x + up);
+  }
+};
 
 // p < 2^30: signed 32-bit Montgomery, R = 2^32.  AR selects the product
 // formulation: 1 = hi(c t) and lo(c tq) with tq = t p^-1 shared by c0 and c1;
@@ -170,7 +232,10 @@ __device__ __forceinline__ void tile_m31(const PrimeCtx &ctx, uint64_t start, ui
   r1 = a1;
 }
 
-// ---- grouped accumulation (p < 2^30) ------------------------------------
+template <bool U> struct SetOf { using T = M31Set; };
+template <> struct SetOf<true> { using T = U31Set; };
+
+// ---- grouped accumulation (p < 2^31) ------------------------------------
 // eqn 3.14 applied to a GROUP of K consecutive terms: the group's factor
 // prod_{i<K} (z + (s+i)^e) = G0(s) + G1(s) z + O(z^2) with
 //   G0(s) = prod_i (s+i)^e,   G1(s) = sum_i prod_{j!=i} (s+j)^e,
@@ -186,9 +251,14 @@ __device__ __forceinline__ void tile_m31(const PrimeCtx &ctx, uint64_t start, ui
 // plain C; the compiler may place their two-input adds on the multiply pipe,
 // which the products already fill.  NF moves work from that pipe to the ALU.
 
-template <int ILP, bool CUBES, int AR, int NF = 0, int KG = 0>
+template <int ILP, bool CUBES, int AR, int NF = 0, int KG = 0, bool U = false>
 __device__ __forceinline__ void tile_m31_grouped(const PrimeCtx &ctx, uint64_t start, uint64_t n,
                                                  int64_t &r0, int64_t &r1) {
+  // U: the unsigned form for 2^30 <= p < 2^31 (U31Set), run by the same
+  // kernel; its chains end with c1 scaled from R' = 2^32 to the context's
+  // R = 2^64 before the lanes merge
+  using SetT = typename SetOf<U>::T;
+  const SetT S(ctx);
   constexpr int K = KG ? KG : (CUBES ? 2 : 3);  // terms per group (default 2 cubes / 3 squares)
   constexpr int EX = CUBES ? 3 : 2;    // t = s^EX
   constexpr int DA = K * EX;           // degree of G0
@@ -222,9 +292,9 @@ __device__ __forceinline__ void tile_m31_grouped(const PrimeCtx &ctx, uint64_t s
     // c1 / c0 unchanged; points from the top down (x^e by backward
     // differences), folded into the diagonals: e_j <- (-1)^j D^j.
     {
-      // 32-bit residues in [0, p) throughout (p < 2^30); s < p, so the top
+      // 32-bit residues in [0, p) throughout (p < 2^31); s < p, so the top
       // point needs at most one subtraction of p
-      const M31Set S(ctx);
+      // 32-bit residues in [0, p) (S: the chain's Montgomery set, above)
       uint64_t x64 = s + (uint64_t)(K * (DA + 1) - 1);
       x64 = x64 >= ctx.p ? (x64 >= 2 * ctx.p ? x64 % ctx.p : x64 - ctx.p) : x64;
       const uint32_t xr = (uint32_t)x64;
@@ -289,7 +359,7 @@ __device__ __forceinline__ void tile_m31_grouped(const PrimeCtx &ctx, uint64_t s
 #pragma unroll
       for (int j = 0; j <= DB; ++j) gb[k][j] = (int32_t)((j & 1) ? S.sub(0, vb[j]) : vb[j]);
     }
-    c0[k] = (int32_t)ctx.one;
+    c0[k] = (int32_t)S.one;
     c1[k] = 0;
   }
   auto modadd = [&](int32_t &a, int32_t b) {
@@ -317,7 +387,14 @@ __device__ __forceinline__ void tile_m31_grouped(const PrimeCtx &ctx, uint64_t s
 #pragma unroll
     for (int k = 0; k < ILP; ++k) {
       const int32_t A = ga[k][0], B = gb[k][0];
-      if (AR >= 7) {
+      if constexpr (U) {
+        // the same with unsigned words: c0 G0 and c1 G0 + c0 G1 stay below
+        // 2 p^2 < 2^63, and one subtraction makes each result canonical
+        const uint64_t w0 = umul_wide((uint32_t)c0[k], (uint32_t)A);
+        const uint64_t w1 = umad_wide((uint32_t)c0[k], (uint32_t)B, umul_wide((uint32_t)c1[k], (uint32_t)A));
+        c0[k] = (int32_t)S.redc(w0);
+        c1[k] = (int32_t)S.redc(w1);
+      } else if (AR >= 7) {
         // one REDC for c1 G0 + c0 G1 R, folded into wide multiply-adds
         const int64_t w0 = mul_wide(c0[k], A);
         const int64_t w1 = mad_wide(c0[k], B, mul_wide(c1[k], A));
@@ -359,6 +436,12 @@ __device__ __forceinline__ void tile_m31_grouped(const PrimeCtx &ctx, uint64_t s
         int64_t tm = M.mul(b, b);
         if (EX == 3) tm = M.mul(tm, b);
         const int32_t t = (int32_t)M.from_mont(tm);
+        if constexpr (U) {  // c1 <- c1 t R'^-1 + c0, c0 <- c0 t R'^-1 (eqn 3.12), canonical
+          const uint32_t n1 = S.add(S.mul((uint32_t)c1[k], (uint32_t)t), (uint32_t)c0[k]);
+          c0[k] = (int32_t)S.mul((uint32_t)c0[k], (uint32_t)t);
+          c1[k] = (int32_t)n1;
+          continue;
+        }
         const int64_t w0 = (int64_t)c0[k] * (int64_t)t;
         const int64_t w1 = (int64_t)c1[k] * (int64_t)t;
         const int32_t m0 = (int32_t)((uint32_t)w0 * q);
@@ -369,9 +452,17 @@ __device__ __forceinline__ void tile_m31_grouped(const PrimeCtx &ctx, uint64_t s
       }
     }
   }
-  int64_t a0 = m31_canon(c0[0], p), a1 = m31_canon(c1[0], p);
+  // canonical pairs whose ratio c1 / c0 is R S (R of the context: for U the
+  // chains carry R' S = 2^32 S, so c1 is multiplied by 2^32 mod p)
+  auto canon = [&](int32_t v) -> int64_t {
+    return U ? (int64_t)(uint32_t)v : m31_canon(v, p);
+  };
+  auto canon1 = [&](int32_t v) -> int64_t {
+    return U ? (int64_t)((((uint64_t)(uint32_t)v) << 32) % ctx.p) : m31_canon(v, p);
+  };
+  int64_t a0 = canon(c0[0]), a1 = canon1(c1[0]);
 #pragma unroll
-  for (int k = 1; k < ILP; ++k) M.combine(a0, a1, m31_canon(c0[k], p), m31_canon(c1[k], p));
+  for (int k = 1; k < ILP; ++k) M.combine(a0, a1, canon(c0[k]), canon1(c1[k]));
   warp_merge(M, a0, a1);
   r0 = a0;
   r1 = a1;
@@ -473,32 +564,6 @@ struct M64K {
   uint32_t p0, p1, q, mhi;  // mhi = floor(2^62 / p)
   uint64_t p;
 };
-
-__device__ __forceinline__ uint64_t umul_wide(uint32_t a, uint32_t b) {
-  uint64_t d;
-  asm("mul.wide.u32 %0, %1, %2;" : "=l"(d) : "r"(a), "r"(b));
-  return d;
-}
-__device__ __forceinline__ uint64_t umad_wide(uint32_t a, uint32_t b, uint64_t c) {
-  uint64_t d;
-  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
-  return d;
-}
-__device__ __forceinline__ uint32_t ulo(uint64_t v) {
-  uint32_t lo;
-  asm("{\n\t.reg .b32 t;\n\tmov.b64 {%0, t}, %1;\n\t}" : "=r"(lo) : "l"(v));
-  return lo;
-}
-__device__ __forceinline__ uint32_t uhi(uint64_t v) {
-  uint32_t hi;
-  asm("{\n\t.reg .b32 t;\n\tmov.b64 {t, %0}, %1;\n\t}" : "=r"(hi) : "l"(v));
-  return hi;
-}
-__device__ __forceinline__ uint64_t upack(uint32_t lo, uint32_t hi) {
-  uint64_t v;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(v) : "r"(lo), "r"(hi));
-  return v;
-}
 
 // (T0 + TY 2^32) 2^-64 mod p for T < 2^96, result below p + 2^32
 __device__ __forceinline__ uint64_t m64_redc2(uint32_t T0, uint64_t TY, const M64K &K) {
@@ -970,6 +1035,16 @@ __device__ __forceinline__ void process_tile(const Plan &P, uint32_t g) {
   } else if (AR == 23) {
     if (j < P.rows_b) tile_paper<true>(ctx, start, n, r0, r1);
     else tile_paper<false>(ctx, start, n, r0, r1);
+  } else if (!WIDE && (ctx.flags & 1u)) {
+    // 2^30 <= p < 2^31 on the 32-bit kernel: the unsigned grouped form with
+    // this formulation's group sizes, single 64-bit terms on short tiles
+    if (AR >= 9 && grp_ok) {
+      if (j < P.rows_b) tile_m31_grouped<ILP, true, 7, NFC, KC, true>(ctx, start, n, r0, r1);
+      else tile_m31_grouped<ILP, false, 7, NFS, KS, true>(ctx, start, n, r0, r1);
+    } else {
+      if (j < P.rows_b) tile_m64<ILP, true>(ctx, start, n, r0, r1);
+      else tile_m64<ILP, false>(ctx, start, n, r0, r1);
+    }
   } else if (!WIDE && AR == 5 && grp_ok) {
     if (j < P.rows_b) tile_m31_grouped<ILP, true, 5>(ctx, start, n, r0, r1);
     else tile_m31_grouped<ILP, false, 5>(ctx, start, n, r0, r1);

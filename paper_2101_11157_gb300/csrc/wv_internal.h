@@ -128,8 +128,8 @@ struct ResidueConfig {
   bool cong_auto_b = true;  // not chosen by the caller: range-aware calls pick by p
   bool cong_auto_e = true;
   int block = 256;
-  int ilp = 2;            // chains per thread, p < 2^30
-  int ilp64 = 1;          // chains per thread, 2^30 <= p < 2^37
+  int ilp = 2;            // chains per thread, p < 2^31
+  int ilp64 = 1;          // chains per thread, 2^31 <= p < 2^37
   int tile_terms = 1 << 20;
   int max_tiles = 8;
   bool tiles_auto = true; // few primes: more, shorter tiles (see tile_shape)
@@ -143,11 +143,11 @@ struct ResidueConfig {
 wv_status resolve_config(const wv_options *opt, bool want_b, bool want_e, ResidueConfig *cfg);
 
 // The hot-loop formulations a caller may select (wv_options.arith):
-//   32-bit path (p < 2^30): 1, 2, 4 single terms; 9 groups of 2 cubes / 3
+//   32-bit path (p < 2^31): 1, 2, 4 single terms; 9 groups of 2 cubes / 3
 //   squares; 25..28 form 9 with other ALU/multiply-pipe splits of the table
 //   additions; 29, 30, 31 groups of 3 cubes, 4 squares, or both (31: the
 //   default); 39 groups of 4 cubes / 5 squares (M31Form in wv_accum.cuh).
-//   64-bit path (2^30 <= p < 2^37): 1, 2, 4 single terms; every
+//   64-bit path (2^31 <= p < 2^37): 1, 2, 4 single terms; every
 //   other value runs the grouped default (8 cubes / 10 squares) except 12..18
 //   and 21, other group sizes and register budgets, 32..36, the default
 //   with its table additions as PTX carry chains, and 37, the default with

@@ -42,8 +42,9 @@ namespace wv {
 // ------------------------------------------------------------------ planner
 // Primes are ordered into slots by p-bucket floor(log2 p), ascending (a
 // counting sort; order inside a bucket is arbitrary and does not affect any
-// result).  Buckets 0..29 are the p < 2^30 slots; the accumulation kernels
-// walk slots from the top, so the largest primes start first.
+// result).  Buckets 0..30 are the p < 2^31 slots of the 32-bit kernel; the
+// accumulation kernels walk slots from the top, so the largest primes start
+// first.
 __device__ __forceinline__ uint32_t p_bucket(uint64_t p) {
   const bool valid = (p >= 11) && (p & 1) && (p < kPMax);
   return valid ? (uint32_t)(63 - __clzll((long long)p)) : 0u;  // special/invalid: no sums
@@ -69,8 +70,10 @@ __global__ void k_plan_buckets(Plan P) {  // one warp: offsets of the 64 buckets
   const uint32_t tot0 = __shfl_sync(0xffffffffu, x0, 31);
   P.bk[64 + lane] = x0 - c0;
   P.bk[96 + lane] = tot0 + x1 - c1;
-  const uint32_t below30 = __shfl_sync(0xffffffffu, x0, 29);  // buckets 0..29
-  if (lane == 0) *P.n31 = below30;
+  // buckets 0..30 (p < 2^31) go to the 32-bit kernel: signed words below
+  // 2^30, unsigned words from 2^30 to 2^31
+  const uint32_t below31 = __shfl_sync(0xffffffffu, x0, 30);
+  if (lane == 0) *P.n31 = below31;
 }
 
 __global__ void k_plan_scatter(Plan P) {

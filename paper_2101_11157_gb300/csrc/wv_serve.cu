@@ -86,7 +86,7 @@ static void terms_host(const uint64_t *ps, size_t n, const ResidueConfig &cfg, d
       const CongView &c = cong_view(id);
       for (int j = 0; j < c.nrows; ++j) t += cong_row_terms(c.row0 + j, p);
     }
-    if (p < (1ull << 30)) a += (double)t;
+    if (p < (1ull << 31)) a += (double)t;  // the 32-bit kernel takes p < 2^31
     else b += (double)t;
   }
   *t31 = a;

@@ -130,10 +130,15 @@ def test_near_miss_tables():
 
 
 def test_wide_path_boundary(orc):
-    """Primes on both sides of the 2^30 switch between 32- and 64-bit words."""
+    """Primes on both sides of the switches between signed 32-bit words (p < 2^30),
+    unsigned 32-bit words (2^30 <= p < 2^31, the largest one 2^31 - 1) and
+    64-bit words (p >= 2^31)."""
     below = [p for p in range(2**30 - 200, 2**30) if W.is_prime(p)][-2:]
     above = [p for p in range(2**30, 2**30 + 200) if W.is_prime(p)][:2]
-    ps = below + above
+    top31 = [p for p in range(2**31 - 200, 2**31) if W.is_prime(p)][-2:]
+    above31 = [p for p in range(2**31, 2**31 + 200) if W.is_prime(p)][:1]
+    assert top31[-1] == 2**31 - 1
+    ps = below + above + top31 + above31
     gb, ge = gpu_residues(ps)
     ob, oe = orc.residues(ps)
     assert np.array_equal(gb, ob) and np.array_equal(ge, oe)
@@ -171,8 +176,8 @@ def test_launch_shapes_agree():
     """Ragged tiles, many tiles per sum, ILP 1/2/4, block sizes, every
     formulation of both arithmetic paths and the single-kind entry points all
     give the identical residues."""
-    ps = np.concatenate([u64(api.sieve(10**6, 10**6 + 3000)), u64(api.sieve(2**31, 2**31 + 400)),
-                         u64(api.sieve(2**36 - 300, 2**36))])
+    ps = np.concatenate([u64(api.sieve(10**6, 10**6 + 3000)), u64(api.sieve(1_500_000_000, 1_500_000_400)),
+                         u64(api.sieve(2**31, 2**31 + 400)), u64(api.sieve(2**36 - 300, 2**36))])
     ref_b, ref_e = gpu_residues(ps)
     for opt in ({"ilp": 1}, {"arith": 9, "ilp": 4}, {"tile_terms": 97, "max_tiles": 4096},
                 {"tile_terms": 1 << 20, "max_tiles": 1}, {"blocks_per_sm": 1},
