@@ -203,7 +203,8 @@ typedef struct {
                        budgets; 32..36 the default with a quarter to all of its 64-bit
                        table additions as PTX carry chains (32: plain; 33..36: with a
                        three-input high word); 37 the default with the earlier, longer
-                       shrink of its difference tables; every other value the grouped default
+                       shrink of its difference tables; 38 the default with its
+                       per-chain set-up unrolled; every other value the grouped default
                        (8 cubes / 10 squares).  23: the paper's own arithmetic on both
                        paths (plain residues, eqn 3.15 split products, remainders from
                        a double-precision quotient, single terms).  Other values:

@@ -358,7 +358,9 @@ def greedy(start: Congruence, rounds: int, D: int = 8, lam: int = 1):
 # left side C_k(2,5,6), which is 14 at 2k = p - 3); the Euler ones from the
 # library's E33 table (integer coefficients relative to its left side).
 GENERATED = [("BB249", "BB30", 40), ("BB476", "BB30", 80), ("BB1115", "BB30", 200),
-             ("EE200", "EE33", 40), ("EE404", "EE33", 80), ("EE967", "EE33", 200)]
+             ("BB2244", "BB30", 400),
+             ("EE200", "EE33", 40), ("EE404", "EE33", 80), ("EE967", "EE33", 200),
+             ("EE2004", "EE33", 400)]
 
 
 def generated(which=None):
@@ -394,7 +396,7 @@ def emit_header(path: str):
         entries.append((name, 0 if cg.kind == "B" else 1, cg.m, lhs, len(rows_all), len(dist_all),
                         len(dist), cg.cost))
         for x, y, c in cg.sums:
-            assert max(x.numerator, x.denominator, y.numerator, y.denominator) < 2**26
+            assert max(x.numerator, x.denominator, y.numerator, y.denominator) < 2**32
             rows_all.append((x.numerator, x.denominator, y.numerator, y.denominator, len(tc_all), len(c)))
             for d in sorted(c):
                 tc_all.append(c[d])

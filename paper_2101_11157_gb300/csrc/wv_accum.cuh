@@ -555,7 +555,8 @@ __device__ __forceinline__ void tile_m64(const PrimeCtx &ctx, uint64_t start, ui
 // The scheme is parametrised by the group sizes (KB terms per group for the
 // cubes of the Bernoulli sums, KE for the squares of the Euler sums), the
 // shrink interval BLK and flags: 4 and 8 write (part of) the table additions
-// as PTX carry chains (M64Split below), 16 selects the four-step shrink.
+// as PTX carry chains (M64Split below), 16 selects the four-step shrink, 32
+// the rolled per-chain set-up.
 // A group costs the same 41 multiply-pipe slots whatever K, so larger groups
 // cut the products per term; the tables cost 2 (D_A + D_B) additions per
 // group and registers, which bound K.
@@ -619,7 +620,7 @@ __device__ __forceinline__ uint64_t m64_shrink_q(uint64_t v, const M64K &K, uint
 
 // group sizes, shrink interval and flags of each 64-bit formulation (arith)
 template <int AR> struct M64Form {  // 9: the default
-  static constexpr int KB = 8, KE = 10, BLK = 16, V = 16;
+  static constexpr int KB = 8, KE = 10, BLK = 16, V = 16 | 32;
 };
 // 32..36: form 9 with its 64-bit table additions written as PTX carry chains
 // (add.cc / addc on the two words) for a share of the entries, in quarters
@@ -628,11 +629,11 @@ template <int AR> struct M64Form {  // 9: the default
 // makes that word's add a three-input add with carry in -- an instruction
 // only the integer ALU has, so the entry stays off the multiply pipe.
 template <int AR> struct M64Split { static constexpr int NFQ = 0; };
-template <> struct M64Form<32> : M64Form<9> { static constexpr int V = 4 | 16; };
-template <> struct M64Form<33> : M64Form<9> { static constexpr int V = 8 | 16; };
-template <> struct M64Form<34> : M64Form<9> { static constexpr int V = 8 | 16; };
-template <> struct M64Form<35> : M64Form<9> { static constexpr int V = 8 | 16; };
-template <> struct M64Form<36> : M64Form<9> { static constexpr int V = 8 | 16; };
+template <> struct M64Form<32> : M64Form<9> { static constexpr int V = 4 | 16 | 32; };
+template <> struct M64Form<33> : M64Form<9> { static constexpr int V = 8 | 16 | 32; };
+template <> struct M64Form<34> : M64Form<9> { static constexpr int V = 8 | 16 | 32; };
+template <> struct M64Form<35> : M64Form<9> { static constexpr int V = 8 | 16 | 32; };
+template <> struct M64Form<36> : M64Form<9> { static constexpr int V = 8 | 16 | 32; };
 template <> struct M64Split<32> { static constexpr int NFQ = 4; };
 template <> struct M64Split<33> { static constexpr int NFQ = 4; };
 template <> struct M64Split<34> { static constexpr int NFQ = 2; };
@@ -640,7 +641,9 @@ template <> struct M64Split<35> { static constexpr int NFQ = 1; };
 template <> struct M64Split<36> { static constexpr int NFQ = 3; };
 // 37: form 9 with the earlier shrink (m64_shrink: a wide quotient, a 64-bit
 // product and a 64-bit subtraction) in place of the four-step one (flag 16)
-template <> struct M64Form<37> : M64Form<9> { static constexpr int V = 0; };
+template <> struct M64Form<37> : M64Form<9> { static constexpr int V = 32; };
+// 38: form 9 with its per-chain set-up loop unrolled, as it was (flag 32 off)
+template <> struct M64Form<38> : M64Form<9> { static constexpr int V = 16; };
 
 // a += b (64-bit) as an explicit carry chain over the two 32-bit words
 __device__ __forceinline__ void add64_cc(uint64_t &a, uint64_t b) {
@@ -665,19 +668,19 @@ __device__ __forceinline__ void add64_cc_z(uint64_t &a, uint64_t b, uint32_t z) 
       : "+l"(a)
       : "l"(b), "r"(z));
 }
-template <> struct M64Form<12> { static constexpr int KB = 2, KE = 3, BLK = 8, V = 16; };
-template <> struct M64Form<13> { static constexpr int KB = 3, KE = 4, BLK = 16, V = 16; };
-template <> struct M64Form<14> { static constexpr int KB = 4, KE = 5, BLK = 16, V = 16; };
-template <> struct M64Form<15> { static constexpr int KB = 5, KE = 6, BLK = 16, V = 16; };
-template <> struct M64Form<16> { static constexpr int KB = 6, KE = 8, BLK = 16, V = 16; };
-template <> struct M64Form<17> { static constexpr int KB = 7, KE = 9, BLK = 16, V = 16; };
+template <> struct M64Form<12> { static constexpr int KB = 2, KE = 3, BLK = 8, V = 16 | 32; };
+template <> struct M64Form<13> { static constexpr int KB = 3, KE = 4, BLK = 16, V = 16 | 32; };
+template <> struct M64Form<14> { static constexpr int KB = 4, KE = 5, BLK = 16, V = 16 | 32; };
+template <> struct M64Form<15> { static constexpr int KB = 5, KE = 6, BLK = 16, V = 16 | 32; };
+template <> struct M64Form<16> { static constexpr int KB = 6, KE = 8, BLK = 16, V = 16 | 32; };
+template <> struct M64Form<17> { static constexpr int KB = 7, KE = 9, BLK = 16, V = 16 | 32; };
 // 18 and 21: the register budget.  Form 9 runs under a cap of kM64MaxReg
 // registers per thread (16 resident warps per SM, a few bytes of spill in
 // the setup); 18 is form 9 without the cap (8 warps), 21 groups of 9 / 11
 // under the cap of 128.
 constexpr int kM64MaxReg = 128;
 template <> struct M64Form<18> : M64Form<9> {};
-template <> struct M64Form<21> { static constexpr int KB = 9, KE = 11, BLK = 16, V = 16; };
+template <> struct M64Form<21> { static constexpr int KB = 9, KE = 11, BLK = 16, V = 16 | 32; };
 
 // a b 2^-64 mod p, below p + 2^12 for a, b < 2^38
 __device__ __forceinline__ uint64_t m64_mm(uint64_t a, uint64_t b, const M64K &K) {
@@ -754,9 +757,10 @@ __device__ __forceinline__ void tile_m64_grouped(const PrimeCtx &ctx, uint64_t s
         d1 = (2 * xr + p - 1) % p;
         d2 = 2;
       }
-#pragma unroll
-      for (int m = DA; m >= 0; --m) {
-        uint64_t P = 0, Q = ctx.one;
+      // one point: the pair (P, Q) of the K consecutive x from the current x down
+      auto point = [&](uint64_t &P, uint64_t &Q) {
+        P = 0;
+        Q = ctx.one;
 #pragma unroll
         for (int i = 0; i < K; ++i) {
           if (i == 0) {
@@ -769,21 +773,61 @@ __device__ __forceinline__ void tile_m64_grouped(const PrimeCtx &ctx, uint64_t s
           d1 = m64_subm(d1, d2, p);
           if (EX == 3) d2 = m64_subm(d2, 6, p);
         }
-        // fold the new point into the diagonals (point DA - m of the sequence)
-        uint64_t nv = m64_once(P, p);
+      };
+      if constexpr ((V & 32) != 0) {
+        // the point loop rolled (flag 32): a few hundred instructions of code
+        // instead of DA + 1 unrolled copies; the table indices stay
+        // compile-time and the diagonal lengths are predicated
 #pragma unroll
-        for (int j = 0; j <= DA - m; ++j) {
-          const uint64_t old = ga[k][j];
-          ga[k][j] = nv;
-          if (j < DA - m) nv = m64_subm(nv, old, p);
+        for (int j = 0; j <= DA; ++j) ga[k][j] = 0;
+#pragma unroll
+        for (int j = 0; j <= DB; ++j) gb[k][j] = 0;
+#pragma unroll 1
+        for (int m = DA; m >= 0; --m) {
+          uint64_t P, Q;
+          point(P, Q);
+          uint64_t nv = m64_once(P, p);
+#pragma unroll
+          for (int j = 0; j <= DA; ++j) {
+            if (j <= DA - m) {
+              const uint64_t old = ga[k][j];
+              ga[k][j] = nv;
+              if (j < DA - m) nv = m64_subm(nv, old, p);
+            }
+          }
+          if (m <= DB) {
+            nv = m64_once(Q, p);
+#pragma unroll
+            for (int j = 0; j <= DB; ++j) {
+              if (j <= DB - m) {
+                const uint64_t old = gb[k][j];
+                gb[k][j] = nv;
+                if (j < DB - m) nv = m64_subm(nv, old, p);
+              }
+            }
+          }
         }
-        if (m <= DB) {
-          nv = m64_once(Q, p);
+      } else {
 #pragma unroll
-          for (int j = 0; j <= DB - m; ++j) {
-            const uint64_t old = gb[k][j];
-            gb[k][j] = nv;
-            if (j < DB - m) nv = m64_subm(nv, old, p);
+        for (int m = DA; m >= 0; --m) {
+          uint64_t P, Q;
+          point(P, Q);
+          // fold the new point into the diagonals (point DA - m of the sequence)
+          uint64_t nv = m64_once(P, p);
+#pragma unroll
+          for (int j = 0; j <= DA - m; ++j) {
+            const uint64_t old = ga[k][j];
+            ga[k][j] = nv;
+            if (j < DA - m) nv = m64_subm(nv, old, p);
+          }
+          if (m <= DB) {
+            nv = m64_once(Q, p);
+#pragma unroll
+            for (int j = 0; j <= DB - m; ++j) {
+              const uint64_t old = gb[k][j];
+              gb[k][j] = nv;
+              if (j < DB - m) nv = m64_subm(nv, old, p);
+            }
           }
         }
       }

@@ -33,6 +33,14 @@ struct PrimeCtx {
 constexpr uint64_t kM31Limit = 1ull << 30;
 constexpr uint64_t kPMax = 1ull << 37;
 
+// floor(n p / d) for n <= d < 2^32 and p < 2^64, in 64-bit words: with
+// p = a d + b, n p / d = n a + n b / d, where n a <= n p / d < 2^64 and
+// n b < 2^64.  The planner uses it for the endpoints x p, y p of every sum.
+__host__ __device__ inline uint64_t floor_frac_times(uint32_t n, uint32_t d, uint64_t p) {
+  const uint64_t a = p / d, b = p % d;
+  return (uint64_t)n * a + ((uint64_t)n * b) / d;
+}
+
 __host__ __device__ inline uint64_t inv_mod_2_64(uint64_t p) {
   uint64_t x = p;  // correct to 3 bits for odd p
   for (int i = 0; i < 5; ++i) x *= 2 - p * x;

@@ -150,13 +150,14 @@ wv_status resolve_config(const wv_options *opt, bool want_b, bool want_e, Residu
 //   64-bit path (2^31 <= p < 2^37): 1, 2, 4 single terms; every
 //   other value runs the grouped default (8 cubes / 10 squares) except 12..18
 //   and 21, other group sizes and register budgets, 32..36, the default
-//   with its table additions as PTX carry chains, and 37, the default with
-//   the earlier, longer shrink of its tables.  23: the paper's own
+//   with its table additions as PTX carry chains, 37, the default with the
+//   earlier, longer shrink of its tables, and 38, the default with its
+//   per-chain set-up unrolled as it was.  23: the paper's own
 //   arithmetic on both paths.
-constexpr const char *kArithList = "1, 2, 4, 9, 12..18, 21, 23, 25..37, 39";
+constexpr const char *kArithList = "1, 2, 4, 9, 12..18, 21, 23, 25..39";
 inline bool arith_selectable(int a) {
   return a == 1 || a == 2 || a == 4 || a == 9 || (a >= 12 && a <= 18) || a == 21 || a == 23 ||
-         (a >= 25 && a <= 37) || a == 39;
+         (a >= 25 && a <= 39);
 }
 
 // Residues for n primes (device array), asynchronous on s.

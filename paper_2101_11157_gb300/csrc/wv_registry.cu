@@ -12,6 +12,7 @@
 #include <string>
 #include <vector>
 
+#include "wv_arith.cuh"
 #include "wv_internal.h"
 #include "wv_tables.h"
 #include "wv_tables_gen.h"
@@ -188,8 +189,8 @@ namespace wv {
 
 uint64_t cong_row_terms(uint32_t r, uint64_t p) {
   const uint32_t *w = cong_row(r);
-  const uint64_t lo = (uint64_t)w[0] * p / w[1] + 1;
-  const uint64_t hi = (uint64_t)w[2] * p / w[3] + 1;
+  const uint64_t lo = floor_frac_times(w[0], w[1], p) + 1;
+  const uint64_t hi = floor_frac_times(w[2], w[3], p) + 1;
   return hi > lo ? hi - lo : 0;
 }
 

@@ -104,10 +104,10 @@ __global__ void k_plan_segments(Plan P) {
   if (!(c.flags & 2u)) {
     const uint64_t p = c.p;
     // open interval (x p, y p): s = floor(xn p / xd) + 1 .. floor(yn p / yd)
-    // (registry endpoints are below 2^26, so xn p < 2^63)
+    // (registry endpoints are 32-bit words with x, y <= 1/2)
     const uint32_t *w = P.cg_rows + 6 * (size_t)(j < P.rows_b ? P.rb0 + j : P.re0 + (j - P.rows_b));
-    lo = (uint64_t)w[0] * p / w[1] + 1;
-    uint64_t hi = (uint64_t)w[2] * p / w[3] + 1;
+    lo = floor_frac_times(w[0], w[1], p) + 1;
+    uint64_t hi = floor_frac_times(w[2], w[3], p) + 1;
     cnt = hi > lo ? hi - lo : 0;
     if (cnt) {
       uint64_t t = (cnt + P.tile_terms - 1) / P.tile_terms;

@@ -39,6 +39,8 @@ GRIDS = {
     "m64cc": [{"arith": a} for a in (9, *range(32, 37))],
     # the 64-bit default (four-step shrink of its tables) against the earlier shrink (37)
     "m64shrink": [{"arith": a} for a in (9, 37)],
+    # the 64-bit default (rolled per-chain set-up) against the unrolled set-up (38)
+    "m64setup": [{"arith": a} for a in (9, 38)],
     # the paper's own arithmetic (eqn 3.15, double-precision quotients) against the default
     "paper": [{"arith": 9}, {"arith": 23}],
     # the 32-bit grouped form 9 with 0 / 4 / 6 / all of its table additions ALU-only (9: 4 and 2)

@@ -93,7 +93,7 @@ def test_top_window_bench_step_equals_oracle():
 
 
 @pytest.mark.parametrize("opt", [None, {"arith": 1}, {"arith": 21}, {"arith": 32}, {"arith": 33},
-                                 {"arith": 37}])
+                                 {"arith": 37}, {"arith": 38}])
 def test_top_window_formulations_equal_oracle(opt):
     """The 8 stored primes below 1e11 on the 64-bit path: the device-list
     default (BB30 + EE33) and the range's congruences, under the default, the

@@ -113,7 +113,7 @@ def test_p1e9_window_cross_congruences():
     # search picks for this window
     for nb, ne in (("BB1", "EE3"), ("BB2", "EE5"), ("BB6", "EE9"), ("BB9", "EE16"),
                    ("BB16", "EE24"), ("BB22", "EE33"), ("BB249", "EE200"), ("BB476", "EE967"),
-                   ("BB1115", "EE404")):
+                   ("BB1115", "EE404"), ("BB2244", "EE2004")):
         gb, ge = gpu_residues(ps, {"cong_b": cong_id(nb), "cong_e": cong_id(ne)})
         assert np.array_equal(gb, ref_b), nb
         assert np.array_equal(ge, ref_e), ne
@@ -184,7 +184,7 @@ def test_launch_shapes_agree():
                 {"arith": 1}, {"arith": 2}, {"arith": 4}, {"arith": 9}, {"arith": 9, "ilp": 1},
                 {"arith": 9, "tile_terms": 5000, "max_tiles": 64},
                 {"block": 32}, {"block": 96, "ilp": 1}, {"block": 128},
-                *({"arith": a} for a in (*range(12, 19), 21, 23, *range(32, 38))),
+                *({"arith": a} for a in (*range(12, 19), 21, 23, *range(32, 39))),
                 *({"arith": a, "ilp": i} for a in (*range(25, 32), 39) for i in (1, 2))):
         gb, ge = gpu_residues(ps, opt)
         assert np.array_equal(gb, ref_b), opt

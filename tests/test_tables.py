@@ -29,7 +29,8 @@ PAPER = {
 
 
 # generated congruences (greedy search over Prop. 2.1 from BB30 / EE33)
-GENERATED = {"BB249": 0, "BB476": 0, "BB1115": 0, "EE200": 1, "EE404": 1, "EE967": 1}
+GENERATED = {"BB249": 0, "BB476": 0, "BB1115": 0, "BB2244": 0,
+             "EE200": 1, "EE404": 1, "EE967": 1, "EE2004": 1}
 
 
 def _interval(cid, j):
@@ -109,7 +110,7 @@ def test_generated_costs_and_intervals(T, name):
     prev = Fraction(0)
     for terms, xn, xd, yn, yd in rows:
         x, y = Fraction(xn, xd), Fraction(yn, yd)
-        assert prev <= x < y <= Fraction(1, 2) and yn < 2**26 and yd < 2**26
+        assert prev <= x < y <= Fraction(1, 2) and yn < 2**32 and yd < 2**32
         prev = y
         for d in (xd, yd) + tuple(d for _, d in terms):  # subdivisions by d <= 8
             for q in (2, 3, 5, 7):
@@ -170,24 +171,33 @@ def _inverse_power_prefix(p, e):
     return pre % np.uint64(p)
 
 
-@pytest.mark.parametrize("p", [12_000_017, 31_000_003])
-def test_generated_congruences_at_primes_where_every_row_has_terms(T, orc, p):
+# every row of every generated congruence holds at least one term at the last of these
+PRIMES_ALL_ROWS = [12_000_017, 31_000_003, 70_000_027]
+
+
+@pytest.mark.parametrize("p", PRIMES_ALL_ROWS)
+def test_generated_congruences_at_large_primes(T, orc, p):
     """The generated congruences' narrowest rows are empty for every p < 700, so
-    the definition test above cannot see a wrong coefficient there.  At these
-    primes every row of every congruence holds at least one term: each one,
-    evaluated with exact integers, must give the oracle's B_{p-3}
-    (Stafford-Vandiver, eqn 2.4) and E_{p-3} (Glaisher, eqn 4.1)."""
+    the definition test above cannot see a wrong coefficient there.  Each
+    congruence, evaluated with exact integers at these primes, must give the
+    oracle's B_{p-3} (Stafford-Vandiver, eqn 2.4) and E_{p-3} (Glaisher, eqn
+    4.1); at the largest of them every row of every congruence holds at least
+    one term, so a wrong coefficient anywhere changes the result."""
     assert is_prime(p)
     want = {0: orc.bernoulli_sv(p), 1: orc.euler_glaisher(p)}
     pre = {3: _inverse_power_prefix(p, 3), 2: _inverse_power_prefix(p, 2)}
     for name in sorted(GENERATED) + ["BB30", "EE33"]:
         cid, kind, lhs, rows = T[name]
         e = 3 if kind == 0 else 2
-        rhs = 0
+        rhs, empty = 0, 0
         for terms, xn, xd, yn, yd in rows:
             lo = xn * p // xd + 1                      # first s above x p
             hi = (yn * p + yd - 1) // yd - 1           # last s below y p
-            assert hi >= lo, (name, p, xn, xd, yn, yd)  # the row is not empty
+            if hi < lo:
+                empty += 1
+                continue
             S = (int(pre[e][hi]) - int(pre[e][lo - 1])) % p
             rhs += _coef(terms, p, e) * S
         assert rhs * pow(lhs, -1, p) % p == want[kind], (name, p)
+        if p == PRIMES_ALL_ROWS[-1]:
+            assert empty == 0, (name, p, empty)
