@@ -50,16 +50,16 @@ IMAD_SLOTS_PER_MODMUL64 = 17
 # run is that busy share scaled by the run's own terms per SM per clock.  Set an entry to None
 # whenever its kernel changes, until it is captured again.
 PIPE_PROFILE = {
-    # k_accumulate<0,2,31>: 492 primes of [1062200000, 1062210000), BB249 + EE404, 3.1220e10 terms,
-    # 15.424 ms at 2.061 GHz; IMAD pipe 76.28 %, ALU 70.79 % of elapsed; 9.1392 MB read, 0 written
-    "accumulate_m31": {"imad_pct": 0.7628, "alu_pct": 0.7079, "terms_per_clk_sm": 6.461,
-                       "dram_bytes_per_prime": 9139200 / 492,
+    # k_accumulate<0,2,31>: 492 primes of [1062200000, 1062210000), BB476 + EE404, 3.0138e10 terms,
+    # 15.592 ms at 2.051 GHz; IMAD pipe 75.20 %, ALU 69.83 % of elapsed; 12.337 MB read, 0 written
+    "accumulate_m31": {"imad_pct": 0.7520, "alu_pct": 0.6983, "terms_per_clk_sm": 6.199,
+                       "dram_bytes_per_prime": 12337152 / 492,
                        "profile": "profiles/accumulate_m31_p1e9_small.md"},
-    # k_accumulate_m64cap<9,128> (four-step shrink): 17 primes of [1e11 - 1e4, 1e11 - 9500),
-    # BB1115 + EE967, 8.4045e10 terms, 61.591 ms at 2.095 GHz; IMAD pipe 83.11 %, ALU 54.49 %;
-    # 1.8906 MB read, 0 written
-    "accumulate_m64": {"imad_pct": 0.8311, "alu_pct": 0.5449, "terms_per_clk_sm": 4.285,
-                       "dram_bytes_per_prime": 1890560 / 17,
+    # k_accumulate_m64cap<9,128> (rolled per-chain set-up): 17 primes of [1e11 - 1e4, 1e11 - 9500),
+    # BB2244 + EE2004, 7.5269e10 terms, 53.149 ms at 2.056 GHz; IMAD pipe 87.85 %, ALU 58.56 %;
+    # 2.4340 MB read, 3.3 KB written
+    "accumulate_m64": {"imad_pct": 0.8785, "alu_pct": 0.5856, "terms_per_clk_sm": 4.531,
+                       "dram_bytes_per_prime": (2434048 + 3328) / 17,
                        "profile": "profiles/accumulate_m64_top_window.md"},
 }
 

@@ -282,7 +282,7 @@ wv_status wv_histogram(uint64_t lo, uint64_t hi, uint32_t bins, unsigned long lo
 /* Number of congruences in the library: ids 0..12 are the paper's (BB1..BB30,
  * EE3..EE33, Sec. 3 and Sec. 5); the ids after them were generated from
  * BB30 and EE33 by the greedy search over Prop. 2.1 (Sec. 2, "Heuristic
- * searches"), named by their number of sums (BB249 ... EE967). */
+ * searches"), named by their number of sums (BB249 ... EE2004). */
 int wv_congruence_count(void);
 
 /* The id of the congruence the residue calls on a device prime list use by
@@ -290,10 +290,13 @@ int wv_congruence_count(void);
 int wv_congruence_default(int kind);
 
 /* The congruences the range-aware calls (wv_search*, wv_histogram, the
- * serving loop) use for primes of [lo, hi) when the caller chose none: by hi,
- * BB9 + EE16 up to 3e7, BB30 + EE33 up to 5e8, BB249 + EE404 up to 2^30,
- * BB30 + EE33 up to 6e9, BB249 + EE404 up to 5e10, then BB1115 + EE967 (the
- * measured fastest on GB300; all give the identical residues). */
+ * serving loop, the batch's per-prime grouping) use for primes of [lo, hi)
+ * when the caller chose none, each kind by hi on its own:
+ *   B: BB9 up to 1e7, BB30 up to 2e8, BB249 up to 1e9, BB476 up to 2^31,
+ *      BB249 up to 5e9, BB476 up to 1.5e10, BB1115 up to 2.5e10, then BB2244;
+ *   E: EE16 up to 3e6, EE33 up to 5e7, EE200 up to 4e8, EE404 up to 5e9,
+ *      EE967 up to 1.5e10, then EE2004
+ * (the measured fastest on GB300; all give the identical residues). */
 void wv_congruence_for_range(uint64_t lo, uint64_t hi, int *cong_b, int *cong_e);
 
 /* Congruence `id`: kind 0 = B_{p-3}, 1 = E_{p-3}; n_rows sums; lhs = the

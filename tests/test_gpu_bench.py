@@ -28,7 +28,7 @@ def test_bench_window_line():
     for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "roofline",
               "e2e", "clocks", "gpu_launches", "cpu_baseline", "config"):
         assert k in d, k
-    assert d["value"] > 0 and d["gpu_launches"] > 0 and d["config"]["congruences"] == "BB249+EE404"
+    assert d["value"] > 0 and d["gpu_launches"] > 0 and d["config"]["congruences"] == "BB476+EE404"
     r = d["roofline"]
     assert r["bound"] == "alu" and r["kernel"] == "accumulate_m31" and r["terms_per_clk_sm"] > 0
     assert r["traffic"] is None  # a partial window: no full-launch traffic figure
@@ -39,4 +39,4 @@ def test_bench_window_line():
 def test_bench_top_line():
     d = _bench("--workload", "top", "--steps", "1", "--warmup", "1", "--width", "400", "--no-extras")
     assert d["roofline"]["kernel"] == "accumulate_m64" and d["value"] > 0
-    assert d["config"]["congruences"] == "BB1115+EE967" and d["hits"] == 0
+    assert d["config"]["congruences"] == "BB2244+EE2004" and d["hits"] == 0

@@ -108,8 +108,8 @@ def test_p1e9_window_cross_congruences():
     """Every congruence, printed or generated, gives the identical residue (Sec. 3, 5)."""
     ps = u64(api.sieve(*W.P1E9_WINDOW))
     ref_b, ref_e = gpu_residues(ps)
-    # the paper's 13 congruences and the 6 generated ones, each against the
-    # default of a device prime list (BB30 + EE33); BB249 + EE404 is what the
+    # the paper's 13 congruences and the 8 generated ones, each against the
+    # default of a device prime list (BB30 + EE33); BB476 + EE404 is what the
     # search picks for this window
     for nb, ne in (("BB1", "EE3"), ("BB2", "EE5"), ("BB6", "EE9"), ("BB9", "EE16"),
                    ("BB16", "EE24"), ("BB22", "EE33"), ("BB249", "EE200"), ("BB476", "EE967"),
