@@ -50,17 +50,8 @@ IMAD_SLOTS_PER_MODMUL64 = 17
 # run is that busy share scaled by the run's own terms per SM per clock.  Set an entry to None
 # whenever its kernel changes, until it is captured again.
 PIPE_PROFILE = {
-    # k_accumulate<0,2,31>: 492 primes of [1062200000, 1062210000), BB476 + EE404, 3.0138e10 terms,
-    # 15.592 ms at 2.051 GHz; IMAD pipe 75.20 %, ALU 69.83 % of elapsed; 12.337 MB read, 0 written
-    "accumulate_m31": {"imad_pct": 0.7520, "alu_pct": 0.6983, "terms_per_clk_sm": 6.199,
-                       "dram_bytes_per_prime": 12337152 / 492,
-                       "profile": "profiles/accumulate_m31_p1e9_small.md"},
-    # k_accumulate_m64cap<9,128> (rolled per-chain set-up): 17 primes of [1e11 - 1e4, 1e11 - 9500),
-    # BB2244 + EE2004, 7.5269e10 terms, 53.149 ms at 2.056 GHz; IMAD pipe 87.85 %, ALU 58.56 %;
-    # 2.4340 MB read, 3.3 KB written
-    "accumulate_m64": {"imad_pct": 0.8785, "alu_pct": 0.5856, "terms_per_clk_sm": 4.531,
-                       "dram_bytes_per_prime": (2434048 + 3328) / 17,
-                       "profile": "profiles/accumulate_m64_top_window.md"},
+    "accumulate_m31": None,  # lane-chain kernel: not yet captured
+    "accumulate_m64": None,
 }
 
 
@@ -365,7 +356,7 @@ def gpu_arm(args):
         "data": "synthetic: every prime of the window, sieved on the device (no dataset)",
         "config": {"workload": f"sieve + B_{{p-3}} ({cong_names[0]}) + E_{{p-3}} ({cong_names[1]}) mod p "
                                f"+ zero/near flags for all primes in [{lo}, {hi}) per GPU"
-                               + (" (64-bit path, 2^30 <= p < 2^37)" if top else ""),
+                               + (" (64-bit path, 2^31 <= p < 2^37)" if top else ""),
                    "primes_per_gpu": int(n_primes), "congruences": "+".join(cong_names),
                    "terms_per_step": int(tb + te), "parallelism": f"range-sharded x{ws}",
                    "range": list(span), "shard": [lo, hi], "primes_all_gpus": int(total_primes),

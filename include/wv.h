@@ -214,7 +214,14 @@ typedef struct {
                        composite gets WV_RESIDUE_INVALID in its slot like an input
                        outside the supported range.  Default 0: primality stays the
                        caller's contract and a composite's slot is unspecified */
-  int reserved[7];
+  int tiling;       /* work unit of the accumulation.  0 (default) or 2: lane chains --
+                       every lane of a warp sums its own piece of one (prime, sum), the
+                       pieces sorted by length so that a warp's lanes finish together;
+                       used with the default formulation (31) and ILP 1 or 2, warp tiles
+                       otherwise.  1: warp tiles -- the 32 lanes of a warp split one piece
+                       and merge by shuffles (the earlier work unit, kept for ablation).
+                       Other values: WV_EINVAL */
+  int reserved[6];
 } wv_options;
 
 /* wv_residues_pm3 with explicit congruence choice and launch shape.
@@ -292,11 +299,12 @@ int wv_congruence_default(int kind);
 /* The congruences the range-aware calls (wv_search*, wv_histogram, the
  * serving loop, the batch's per-prime grouping) use for primes of [lo, hi)
  * when the caller chose none, each kind by hi on its own:
- *   B: BB9 up to 1e7, BB30 up to 2e8, BB249 up to 1e9, BB476 up to 2^31,
- *      BB249 up to 5e9, BB476 up to 1.5e10, BB1115 up to 2.5e10, then BB2244;
- *   E: EE16 up to 3e6, EE33 up to 5e7, EE200 up to 4e8, EE404 up to 5e9,
- *      EE967 up to 1.5e10, then EE2004
- * (the measured fastest on GB300; all give the identical residues). */
+ *   B: BB30 up to 5e6, BB249 up to 2e7, BB476 up to 5e7, BB1115 up to
+ *      1.5e8, then BB2244;
+ *   E: EE33 up to 3e6, EE200 up to 2e7, EE404 up to 5e7, EE967 up to 1e8,
+ *      then EE2004
+ * (the measured fastest on GB300 with the default lane chains; all give the
+ * identical residues). */
 void wv_congruence_for_range(uint64_t lo, uint64_t hi, int *cong_b, int *cong_e);
 
 /* Congruence `id`: kind 0 = B_{p-3}, 1 = E_{p-3}; n_rows sums; lhs = the

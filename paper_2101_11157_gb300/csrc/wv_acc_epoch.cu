@@ -6,7 +6,11 @@
 namespace wv {
 
 // the 64-bit tiles of an epoch run one chain per thread (the fastest grouped form)
-EpochKernel epoch_kernel(bool wide, int ilp) {
+EpochKernel epoch_kernel(bool wide, int ilp, bool lane) {
+  if (lane) {
+    if (wide) return k_epoch<true, 1, 9, true>;
+    return ilp == 1 ? k_epoch<false, 1, 31, true> : k_epoch<false, 2, 31, true>;
+  }
   if (wide) return k_epoch<true, 1, 9>;
   return ilp == 1 ? k_epoch<false, 1, 31> : k_epoch<false, 2, 31>;
 }

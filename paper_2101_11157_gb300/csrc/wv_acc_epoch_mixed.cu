@@ -5,7 +5,8 @@
 
 namespace wv {
 
-EpochKernel epoch_mixed_kernel(int ilp31, int) {
+EpochKernel epoch_mixed_kernel(int ilp31, int, bool lane) {
+  if (lane) return ilp31 == 1 ? k_epoch_mixed<1, 1, true> : k_epoch_mixed<2, 1, true>;
   return ilp31 == 1 ? k_epoch_mixed<1, 1> : k_epoch_mixed<2, 1>;
 }
 

@@ -4,7 +4,8 @@
 
 namespace wv {
 
-EpochTilesKernel epoch_tiles_kernel(int ilp31) {
+EpochTilesKernel epoch_tiles_kernel(int ilp31, bool lane) {
+  if (lane) return ilp31 == 1 ? k_epoch_tiles<1, 1, true> : k_epoch_tiles<2, 1, true>;
   return ilp31 == 1 ? k_epoch_tiles<1, 1> : k_epoch_tiles<2, 1>;
 }
 

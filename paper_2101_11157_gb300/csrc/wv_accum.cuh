@@ -52,7 +52,19 @@ struct Plan {
   // inverse-power sums, and (a, b, c) of C_k(a,b,c) for B
   uint32_t gen_e_b, gen_e_e;
   uint32_t glhs[3];
+  // lane chains (lane != 0): a tile is one lane's piece of a segment, and a
+  // warp runs 32 of them.  perm lists the tiles by class (32-bit signed /
+  // unsigned / 64-bit path, B / E) and, inside a class, by rising length,
+  // each class padded to whole warps with kNoChain; lane_w = {warps of the
+  // 32-bit kernel, all warps}.  Chains per segment come from the path's chain
+  // length (lane_len: terms at most per chain, from lane_sum = terms per path
+  // and the targets below).
+  uint32_t lane;
+  uint32_t *perm, *chain_key, *chain_hist, *lane_w;
+  uint64_t *lane_sum, *lane_len;
+  uint64_t lane_target[2], lane_min[2];  // chains wanted per path, shortest chain length
 };
+constexpr uint32_t kNoChain = 0xffffffffu;
 
 // ------------------------------------------------------------------ tiles
 // Warp-level merge of the per-lane pairs (eqn 3.14) through shuffles.
@@ -130,20 +142,20 @@ struct U31Set {
 // p < 2^30: signed 32-bit Montgomery, R = 2^32.  AR selects the product
 // formulation: 1 = hi(c t) and lo(c tq) with tq = t p^-1 shared by c0 and c1;
 // 2 = the full 64-bit product c t (one wide multiply) and m = lo(c t) p^-1.
-template <int ILP, bool CUBES, int AR>
+template <int ILP, bool CUBES, int AR, bool LANE = false>
 __device__ __forceinline__ void tile_m31(const PrimeCtx &ctx, uint64_t start, uint64_t n,
                                          int64_t &r0, int64_t &r1) {
   const int lane = threadIdx.x & 31;
   const int32_t p = (int32_t)ctx.p;
   const uint32_t up = (uint32_t)ctx.p;
   const uint32_t q = (uint32_t)ctx.q;
-  const uint64_t nch = 32 * ILP;
+  const uint64_t nch = LANE ? ILP : 32 * ILP;  // lane chains: the lane owns the tile
   const uint64_t len = n / nch;
   const uint32_t rem = (uint32_t)(n - len * nch);
   int32_t c0[ILP], c1[ILP], t[ILP], d1[ILP], d2[ILP];
 #pragma unroll
   for (int k = 0; k < ILP; ++k) {
-    const uint32_t ch = k * 32 + lane;
+    const uint32_t ch = LANE ? k : k * 32 + lane;
     const uint64_t s = start + ch * len + (ch < rem ? ch : rem);
     const uint64_t s2 = (s * s) % ctx.p;  // s < 2^30: exact in 64 bits
     if (CUBES) {
@@ -221,13 +233,13 @@ __device__ __forceinline__ void tile_m31(const PrimeCtx &ctx, uint64_t start, ui
   }
 #pragma unroll
   for (int k = 0; k < ILP; ++k)
-    if ((uint32_t)(k * 32 + lane) < rem) step(k, z);
+    if ((uint32_t)(LANE ? k : k * 32 + lane) < rem) step(k, z);
 
   const Mont M(ctx);
   int64_t a0 = m31_canon(c0[0], p), a1 = m31_canon(c1[0], p);
 #pragma unroll
   for (int k = 1; k < ILP; ++k) M.combine(a0, a1, m31_canon(c0[k], p), m31_canon(c1[k], p));
-  warp_merge(M, a0, a1);
+  if (!LANE) warp_merge(M, a0, a1);
   r0 = a0;
   r1 = a1;
 }
@@ -251,7 +263,7 @@ template <> struct SetOf<true> { using T = U31Set; };
 // plain C; the compiler may place their two-input adds on the multiply pipe,
 // which the products already fill.  NF moves work from that pipe to the ALU.
 
-template <int ILP, bool CUBES, int AR, int NF = 0, int KG = 0, bool U = false>
+template <int ILP, bool CUBES, int AR, int NF = 0, int KG = 0, bool U = false, bool LANE = false>
 __device__ __forceinline__ void tile_m31_grouped(const PrimeCtx &ctx, uint64_t start, uint64_t n,
                                                  int64_t &r0, int64_t &r1) {
   // U: the unsigned form for 2^30 <= p < 2^31 (U31Set), run by the same
@@ -270,7 +282,7 @@ __device__ __forceinline__ void tile_m31_grouped(const PrimeCtx &ctx, uint64_t s
   const uint32_t q = (uint32_t)ctx.q;
   const uint32_t uz = (AR >= 7) ? 0u : (ctx.flags >> 16);  // runtime zero (AR 5: three-input adds)
   const int32_t np = -p;
-  const uint64_t nch = 32 * ILP;
+  const uint64_t nch = LANE ? ILP : 32 * ILP;  // lane chains: the lane owns the tile
   const uint64_t len = n / nch;
   const uint32_t rem = (uint32_t)(n - len * nch);
   const uint64_t G = len / K;  // groups per chain, the same for every lane
@@ -279,7 +291,7 @@ __device__ __forceinline__ void tile_m31_grouped(const PrimeCtx &ctx, uint64_t s
   uint32_t n_tail[ILP];
 #pragma unroll
   for (int k = 0; k < ILP; ++k) {
-    const uint32_t ch = k * 32 + lane;
+    const uint32_t ch = LANE ? k : k * 32 + lane;
     const uint64_t s = start + ch * len + (ch < rem ? ch : rem);
     const uint64_t L = len + (ch < rem ? 1 : 0);
     s_tail[k] = s + G * K;
@@ -463,13 +475,13 @@ __device__ __forceinline__ void tile_m31_grouped(const PrimeCtx &ctx, uint64_t s
   int64_t a0 = canon(c0[0]), a1 = canon1(c1[0]);
 #pragma unroll
   for (int k = 1; k < ILP; ++k) M.combine(a0, a1, canon(c0[k]), canon1(c1[k]));
-  warp_merge(M, a0, a1);
+  if (!LANE) warp_merge(M, a0, a1);
   r0 = a0;
   r1 = a1;
 }
 
 // 2^30 <= p < 2^37: signed 64-bit Montgomery, R = 2^64.
-template <int ILP, bool CUBES>
+template <int ILP, bool CUBES, bool LANE = false>
 __device__ __forceinline__ void tile_m64(const PrimeCtx &ctx, uint64_t start, uint64_t n,
                                          int64_t &r0, int64_t &r1) {
   const int lane = threadIdx.x & 31;
@@ -477,13 +489,13 @@ __device__ __forceinline__ void tile_m64(const PrimeCtx &ctx, uint64_t start, ui
   const int64_t p = (int64_t)ctx.p;
   const uint64_t up = ctx.p;
   const uint64_t q = ctx.q;
-  const uint64_t nch = 32 * ILP;
+  const uint64_t nch = LANE ? ILP : 32 * ILP;  // lane chains: the lane owns the tile
   const uint64_t len = n / nch;
   const uint32_t rem = (uint32_t)(n - len * nch);
   int64_t c0[ILP], c1[ILP], t[ILP], d1[ILP], d2[ILP];
 #pragma unroll
   for (int k = 0; k < ILP; ++k) {
-    const uint32_t ch = k * 32 + lane;
+    const uint32_t ch = LANE ? k : k * 32 + lane;
     const uint64_t s = start + ch * len + (ch < rem ? ch : rem);
     const int64_t s2 = M.mulmod((int64_t)s, (int64_t)s);
     if (CUBES) {
@@ -525,12 +537,12 @@ __device__ __forceinline__ void tile_m64(const PrimeCtx &ctx, uint64_t start, ui
   }
 #pragma unroll
   for (int k = 0; k < ILP; ++k)
-    if ((uint32_t)(k * 32 + lane) < rem) step(k);
+    if ((uint32_t)(LANE ? k : k * 32 + lane) < rem) step(k);
 
   int64_t a0 = m64_canon(c0[0], p), a1 = m64_canon(c1[0], p);
 #pragma unroll
   for (int k = 1; k < ILP; ++k) M.combine(a0, a1, m64_canon(c0[k], p), m64_canon(c1[k], p));
-  warp_merge(M, a0, a1);
+  if (!LANE) warp_merge(M, a0, a1);
   r0 = a0;
   r1 = a1;
 }
@@ -698,7 +710,7 @@ __device__ __forceinline__ uint64_t m64_subm(uint64_t a, uint64_t b, uint64_t p)
   return a >= b ? a - b : a + p - b;
 }
 
-template <int ILP, bool CUBES, int AR>
+template <int ILP, bool CUBES, int AR, bool LANE = false>
 __device__ __forceinline__ void tile_m64_grouped(const PrimeCtx &ctx, uint64_t start, uint64_t n,
                                                  int64_t &r0, int64_t &r1) {
   using F = M64Form<AR>;
@@ -720,7 +732,7 @@ __device__ __forceinline__ void tile_m64_grouped(const PrimeCtx &ctx, uint64_t s
   const uint64_t np = 0ull - ctx.p;  // 2^64 - p, for the four-step shrink
   const uint32_t np0 = (uint32_t)np, np1 = (uint32_t)(np >> 32);
   constexpr int NF = (DA + DB) * M64Split<AR>::NFQ / 4;  // carry-chain entries
-  const uint64_t nch = 32 * ILP;
+  const uint64_t nch = LANE ? ILP : 32 * ILP;  // lane chains: the lane owns the tile
   const uint64_t len = n / nch;
   const uint32_t rem = (uint32_t)(n - len * nch);
   const uint64_t G = len / K;
@@ -729,7 +741,7 @@ __device__ __forceinline__ void tile_m64_grouped(const PrimeCtx &ctx, uint64_t s
   uint32_t n_tail[ILP];
 #pragma unroll
   for (int k = 0; k < ILP; ++k) {
-    const uint32_t ch = k * 32 + lane;
+    const uint32_t ch = LANE ? k : k * 32 + lane;
     const uint64_t s = start + ch * len + (ch < rem ? ch : rem);
     const uint64_t L = len + (ch < rem ? 1 : 0);
     s_tail[k] = s + G * K;
@@ -907,7 +919,7 @@ __device__ __forceinline__ void tile_m64_grouped(const PrimeCtx &ctx, uint64_t s
       M.combine(a0, a1, x0, x1);
     }
   }
-  warp_merge(M, a0, a1);
+  if (!LANE) warp_merge(M, a0, a1);
   r0 = a0;
   r1 = a1;
 }
@@ -1056,9 +1068,18 @@ template <> struct M31Form<30> { static constexpr int KC = 0, KS = 4, NFC = 4, N
 template <> struct M31Form<31> { static constexpr int KC = 3, KS = 4, NFC = 6, NFS = 4; };
 template <> struct M31Form<39> { static constexpr int KC = 4, KS = 5, NFC = 6, NFS = 4; };
 
-template <bool WIDE, int ILP, int AR>
+template <bool WIDE, int ILP, int AR, bool LANE = false>
 __device__ __forceinline__ void process_tile(const Plan &P, uint32_t g) {
   const int lane = threadIdx.x & 31;
+  bool live = true;
+  if constexpr (LANE) {
+    // g is a warp of lane chains: this lane's tile from the sorted list; a
+    // padding lane repeats lane 0's tile (same code path, nothing stored)
+    uint32_t t = __ldg(&P.perm[32 * (size_t)g + lane]);
+    const uint32_t t0 = __shfl_sync(0xffffffffu, t, 0);
+    live = t != kNoChain;
+    g = live ? t : t0;
+  }
   // segment owning tile g (the planner's tile -> segment map)
   const uint32_t s = __ldg(&P.tile_seg[g]);
   const uint32_t slot = s / P.rows_pp, j = s - slot * P.rows_pp;
@@ -1073,7 +1094,7 @@ __device__ __forceinline__ void process_tile(const Plan &P, uint32_t g) {
   // group sizes and ALU-only table additions of the grouped 32-bit form
   constexpr int NFC = M31Form<AR>::NFC, NFS = M31Form<AR>::NFS;
   constexpr int KC = M31Form<AR>::KC, KS = M31Form<AR>::KS;
-  const bool grp_ok = n >= 32ull * ILP * kGroupMinChain;
+  const bool grp_ok = n >= (LANE ? 1ull : 32ull) * ILP * kGroupMinChain;
   if (AR == 24) {
     tile_general(ctx, start, n, j < P.rows_b ? P.gen_e_b : P.gen_e_e, r0, r1);
   } else if (AR == 23) {
@@ -1083,35 +1104,51 @@ __device__ __forceinline__ void process_tile(const Plan &P, uint32_t g) {
     // 2^30 <= p < 2^31 on the 32-bit kernel: the unsigned grouped form with
     // this formulation's group sizes, single 64-bit terms on short tiles
     if (AR >= 9 && grp_ok) {
-      if (j < P.rows_b) tile_m31_grouped<ILP, true, 7, NFC, KC, true>(ctx, start, n, r0, r1);
-      else tile_m31_grouped<ILP, false, 7, NFS, KS, true>(ctx, start, n, r0, r1);
+      if (j < P.rows_b) tile_m31_grouped<ILP, true, 7, NFC, KC, true, LANE>(ctx, start, n, r0, r1);
+      else tile_m31_grouped<ILP, false, 7, NFS, KS, true, LANE>(ctx, start, n, r0, r1);
     } else {
-      if (j < P.rows_b) tile_m64<ILP, true>(ctx, start, n, r0, r1);
-      else tile_m64<ILP, false>(ctx, start, n, r0, r1);
+      if (j < P.rows_b) tile_m64<ILP, true, LANE>(ctx, start, n, r0, r1);
+      else tile_m64<ILP, false, LANE>(ctx, start, n, r0, r1);
     }
   } else if (!WIDE && AR == 5 && grp_ok) {
     if (j < P.rows_b) tile_m31_grouped<ILP, true, 5>(ctx, start, n, r0, r1);
     else tile_m31_grouped<ILP, false, 5>(ctx, start, n, r0, r1);
   } else if (!WIDE && AR >= 7 && grp_ok && j >= P.rows_b) {
-    tile_m31_grouped<ILP, false, 7, NFS, KS>(ctx, start, n, r0, r1);
+    tile_m31_grouped<ILP, false, 7, NFS, KS, false, LANE>(ctx, start, n, r0, r1);
   } else if (!WIDE && AR >= 9 && grp_ok) {
-    tile_m31_grouped<ILP, true, 7, NFC, KC>(ctx, start, n, r0, r1);
+    tile_m31_grouped<ILP, true, 7, NFC, KC, false, LANE>(ctx, start, n, r0, r1);
   } else if (!WIDE) {
-    if (j < P.rows_b) tile_m31<ILP, true, AS>(ctx, start, n, r0, r1);
-    else tile_m31<ILP, false, AS>(ctx, start, n, r0, r1);
+    if (j < P.rows_b) tile_m31<ILP, true, AS, LANE>(ctx, start, n, r0, r1);
+    else tile_m31<ILP, false, AS, LANE>(ctx, start, n, r0, r1);
   } else if (AR >= 9 && grp_ok) {
-    if (j < P.rows_b) tile_m64_grouped<ILP, true, AR>(ctx, start, n, r0, r1);
-    else tile_m64_grouped<ILP, false, AR>(ctx, start, n, r0, r1);
+    if (j < P.rows_b) tile_m64_grouped<ILP, true, AR, LANE>(ctx, start, n, r0, r1);
+    else tile_m64_grouped<ILP, false, AR, LANE>(ctx, start, n, r0, r1);
   } else {
-    if (j < P.rows_b) tile_m64<ILP, true>(ctx, start, n, r0, r1);
-    else tile_m64<ILP, false>(ctx, start, n, r0, r1);
+    if (j < P.rows_b) tile_m64<ILP, true, LANE>(ctx, start, n, r0, r1);
+    else tile_m64<ILP, false, LANE>(ctx, start, n, r0, r1);
   }
-  if (lane == 0) P.partials[g] = make_ulonglong2((unsigned long long)r0, (unsigned long long)r1);
+  if (LANE ? live : lane == 0)
+    P.partials[g] = make_ulonglong2((unsigned long long)r0, (unsigned long long)r1);
 }
 
-template <bool WIDE, int ILP, int AR>
+template <bool WIDE, int ILP, int AR, bool LANE = false>
 __device__ __forceinline__ void accumulate_loop(const Plan &P) {
   const int lane = threadIdx.x & 31;
+  if constexpr (LANE) {
+    // warps of lane chains, [0, lane_w[0]) on the 32-bit kernel and
+    // [lane_w[0], lane_w[1]) on the 64-bit one, taken from the top (longest
+    // chains of each class first)
+    const uint32_t w0 = WIDE ? P.lane_w[0] : 0u, w1 = WIDE ? P.lane_w[1] : P.lane_w[0];
+    uint32_t *counter = P.counters + (WIDE ? 1 : 0);
+    for (;;) {
+      uint32_t g = 0;
+      if (lane == 0) g = atomicAdd(counter, 1u);
+      g = __shfl_sync(0xffffffffu, g, 0);
+      if (g >= w1 - w0) break;
+      process_tile<WIDE, ILP, AR, true>(P, w1 - 1 - g);
+    }
+    return;
+  }
   const uint32_t total = *P.total_tiles, split = *P.split_tile;
   const uint32_t t_begin = WIDE ? split : 0u, t_end = WIDE ? total : split;
   const uint32_t ntiles = t_end - t_begin;
@@ -1129,22 +1166,23 @@ __device__ __forceinline__ void accumulate_loop(const Plan &P) {
 // to 85 per thread.  Without the minimum the compiler fits the 32-bit
 // grouped kernel into 64 registers (4 blocks) and schedules its group loop
 // tighter, which measured slower on GB300 than 3 blocks of 70 registers.
-template <bool WIDE, int ILP, int AR>
+template <bool WIDE, int ILP, int AR, bool LANE = false>
 __global__ void __launch_bounds__(kAccThreads, 3) k_accumulate(Plan P) {
-  accumulate_loop<WIDE, ILP, AR>(P);
+  accumulate_loop<WIDE, ILP, AR, LANE>(P);
 }
 
 // The 64-bit path with a register cap (any block size): fewer registers per
 // thread, more resident warps.
-template <int AR, int MAXREG>
+template <int AR, int MAXREG, bool LANE = false>
 __global__ void __maxnreg__(MAXREG) k_accumulate_m64cap(Plan P) {
-  accumulate_loop<true, 1, AR>(P);
+  accumulate_loop<true, 1, AR, LANE>(P);
 }
 
 // Epoch form: tiles of several plans (one per request of a serving loop),
 // given as items {plan, first tile, count, prefix}; the items' tiles are
-// taken from one counter, each item from its top tile down.
-template <bool WIDE, int ILP, int AR>
+// taken from one counter, each item from its top tile down.  LANE: the plans
+// hold lane chains and a "tile" is a warp of their sorted tile list.
+template <bool WIDE, int ILP, int AR, bool LANE = false>
 __global__ void __maxnreg__(kM64MaxReg)
     k_epoch(const EpochItem *items, uint32_t n_items, uint32_t total, const Plan *plans,
             uint32_t *counter) {
@@ -1160,13 +1198,13 @@ __global__ void __maxnreg__(kM64MaxReg)
       if (__ldg(&items[mid].prefix) <= g) lo = mid; else hi = mid;
     }
     const EpochItem it = items[lo];
-    process_tile<WIDE, ILP, AR>(plans[it.plan], it.first + it.count - 1 - (g - it.prefix));
+    process_tile<WIDE, ILP, AR, LANE>(plans[it.plan], it.first + it.count - 1 - (g - it.prefix));
   }
 }
 
 // Epoch form with both arithmetic paths in one launch: items with bit 31 of
 // `plan` set are 64-bit-path tiles.  One launch (and one tail) per epoch.
-template <int I31, int I64>
+template <int I31, int I64, bool LANE = false>
 __global__ void __maxnreg__(kM64MaxReg)
     k_epoch_mixed(const EpochItem *items, uint32_t n_items, uint32_t total, const Plan *plans,
                   uint32_t *counter) {
@@ -1183,8 +1221,8 @@ __global__ void __maxnreg__(kM64MaxReg)
     }
     const EpochItem it = items[lo];
     const uint32_t tile = it.first + it.count - 1 - (g - it.prefix);
-    if (it.plan >> 31) process_tile<true, I64, 9>(plans[it.plan & 0x7fffffffu], tile);
-    else process_tile<false, I31, 31>(plans[it.plan], tile);
+    if (it.plan >> 31) process_tile<true, I64, 9, LANE>(plans[it.plan & 0x7fffffffu], tile);
+    else process_tile<false, I31, 31, LANE>(plans[it.plan], tile);
   }
 }
 
@@ -1192,7 +1230,7 @@ __global__ void __maxnreg__(kM64MaxReg)
 // one-warp blocks), so warps retire tile by tile and the block scheduler
 // hands their slots to whatever is pending -- the next epoch, or admission
 // kernels on a higher-priority stream -- without a persistent grid's tail.
-template <int I31, int I64>
+template <int I31, int I64, bool LANE = false>
 __global__ void __maxnreg__(kM64MaxReg)
     k_epoch_tiles(const EpochItem *items, uint32_t n_items, uint32_t total, const Plan *plans) {
   const uint32_t g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -1204,8 +1242,8 @@ __global__ void __maxnreg__(kM64MaxReg)
   }
   const EpochItem it = items[lo];
   const uint32_t tile = it.first + it.count - 1 - (g - it.prefix);
-  if (it.plan >> 31) process_tile<true, I64, 9>(plans[it.plan & 0x7fffffffu], tile);
-  else process_tile<false, I31, 31>(plans[it.plan], tile);
+  if (it.plan >> 31) process_tile<true, I64, 9, LANE>(plans[it.plan & 0x7fffffffu], tile);
+  else process_tile<false, I31, 31, LANE>(plans[it.plan], tile);
 }
 
 // ------------------------------------------------------------------ getters
@@ -1226,12 +1264,16 @@ AccKernel acc_kernel_m64w(int arith, int ilp);
 AccKernel acc_kernel_m64v(int arith, int ilp);  // forms 32..36 (w falls through to v)
 // 32-bit path: formulation 9 with other ALU-only splits or group sizes (arith 25..31), ILP 1 or 2
 AccKernel acc_kernel_m31x(int arith, int ilp);
+// lane chains: the 32-bit default (formulation 31, ILP 1 or 2) and the
+// 64-bit grouped default (one chain per thread)
+AccKernel acc_kernel_lane31(int ilp);
+AccKernel acc_kernel_lane64();
 AccKernel acc_kernel_m31y(int arith, int ilp);  // form 39 (x falls through to y)
 // serving-loop epoch kernels (the default formulations: 31 on the 32-bit path,
 // 9 with one chain per thread on the 64-bit path)
-EpochKernel epoch_kernel(bool wide, int ilp);
-EpochKernel epoch_mixed_kernel(int ilp31, int ilp64);
+EpochKernel epoch_kernel(bool wide, int ilp, bool lane);
+EpochKernel epoch_mixed_kernel(int ilp31, int ilp64, bool lane);
 using EpochTilesKernel = void (*)(const EpochItem *, uint32_t, uint32_t, const Plan *);
-EpochTilesKernel epoch_tiles_kernel(int ilp31);
+EpochTilesKernel epoch_tiles_kernel(int ilp31, bool lane);
 
 }  // namespace wv

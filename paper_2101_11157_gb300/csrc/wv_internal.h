@@ -139,6 +139,12 @@ struct ResidueConfig {
   uint32_t gen_e_e = 0;   // general index: E_{p-1-e} (e even); 0 = the E_{p-3} forms
   size_t chunk = 0;       // primes per launch sequence (0: library default 16384)
   bool check_primes = false;  // planner verifies primality (composites -> invalid slot)
+  int tiling = 0;         // 0 / 2: lane chains where supported, 1: warp tiles
+  // lane chains apply to the default formulation with ILP 1 or 2 and not to
+  // the general index (its own single-term tiles)
+  bool lane_chains() const {
+    return tiling != 1 && arith == 31 && (ilp == 1 || ilp == 2) && !gen_e_b && !gen_e_e;
+  }
 };
 wv_status resolve_config(const wv_options *opt, bool want_b, bool want_e, ResidueConfig *cfg);
 

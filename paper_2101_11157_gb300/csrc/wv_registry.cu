@@ -127,22 +127,20 @@ int cong_default(int kind) { return kind == 0 ? kWvDefaultB : kWvDefaultE; }
 
 // The congruences for primes below `hi` (the paper also switches congruences
 // with the size of p, Sec. 3 "Method for primes p < 6e10").  Measured on
-// GB300, for each kind alone, over windows of primes from 1e7 to 1e11: the
-// cheapest congruence whose sums stay long enough for their per-chain set-up
-// to pay.  The bands differ by kind and restart at 2^31, where the 64-bit
-// path (with its costlier set-up) takes over from the 32-bit one.
+// GB300 with lane chains, for each kind alone, over windows of primes from
+// 1e5 to 1e11: with lane chains every congruence runs at the kernel's own
+// rate once its sums are a few thousand terms long, so the cheapest one
+// (most sums) wins from p ~ 1e8 on; below, the smaller ones.
 void cong_for_range(uint64_t hi, int *cb, int *ce) {
   struct Band {
     uint64_t hi;
     const char *name;
   };
-  static const Band bands_b[] = {{10000000ull, "BB9"},        {200000000ull, "BB30"},
-                                 {1000000000ull, "BB249"},    {1ull << 31, "BB476"},
-                                 {5000000000ull, "BB249"},    {15000000000ull, "BB476"},
-                                 {25000000000ull, "BB1115"},  {~0ull, "BB2244"}};
-  static const Band bands_e[] = {{3000000ull, "EE16"},        {50000000ull, "EE33"},
-                                 {400000000ull, "EE200"},     {1ull << 31, "EE404"},
-                                 {5000000000ull, "EE404"},    {15000000000ull, "EE967"},
+  static const Band bands_b[] = {{5000000ull, "BB30"},      {20000000ull, "BB249"},
+                                 {50000000ull, "BB476"},    {150000000ull, "BB1115"},
+                                 {~0ull, "BB2244"}};
+  static const Band bands_e[] = {{3000000ull, "EE33"},      {20000000ull, "EE200"},
+                                 {50000000ull, "EE404"},    {100000000ull, "EE967"},
                                  {~0ull, "EE2004"}};
   for (const Band &bd : bands_b)
     if (hi <= bd.hi) {

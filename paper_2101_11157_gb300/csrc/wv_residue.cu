@@ -10,18 +10,28 @@
 // finishes the sum (Sec. 3, the CPU's last step in the paper's GPU method).
 //
 // GB300 design:
-//  * Work unit = a warp tile: a contiguous range of s inside one (prime, row)
-//    sum.  The planner splits every sum into at most `max_tiles` tiles of about
-//    `tile_terms` terms.  A persistent kernel (grid = SMs x occupancy) lets
-//    warps take tiles from an atomic counter, largest primes first.
-//  * Inside a tile, 32 lanes x ILP chains each own a contiguous run of s.  Term
+//  * Work unit (default) = a lane chain: one lane's contiguous range of s
+//    inside one (prime, row) sum.  The planner splits every sum into pieces
+//    of at most L terms (L: the path's terms over 16 times its resident
+//    lanes, at least 4096 / 16384), sorts the pieces by class and length,
+//    and a persistent kernel (grid = SMs x occupancy) lets warps take 32
+//    pieces at a time from an atomic counter, longest first.  The lanes of a
+//    warp then sum different primes and rows side by side, and a sum of any
+//    length keeps one chain per piece, so the per-chain set-up stays small
+//    even for the thousands of short sums of the generated congruences.
+//  * Work unit (wv_options.tiling = 1) = a warp tile: a contiguous range of s
+//    inside one sum, split over the 32 lanes x ILP chains of a warp and merged
+//    by shuffles.  The planner splits every sum into at most `max_tiles`
+//    tiles of about `tile_terms` terms, taken largest primes first.
+//  * Inside a piece, each lane owns ILP contiguous runs of s.  Term
 //    generation is by forward differences (Sec. 3, improvement 1): s^3 from
 //    (s-1)^3 with three modular additions, s^2 with one; no multiplication.
 //  * Accumulation: signed Montgomery arithmetic (see wv_arith.cuh).  For
 //    p < 2^30 a term costs 7 integer multiplies (hi(c0 t), hi(c1 t), t p^-1,
 //    c0 tq, c1 tq, hi(m0 p), hi(m1 p)); 64-bit words for 2^30 <= p < 2^37.
-//  * The chains of a tile are merged with eqn 3.14 in registers and by warp
-//    shuffles; one (c0, c1) pair per tile goes to global memory.  The finalise
+//  * The chains of a lane are merged with eqn 3.14 in registers (of a warp
+//    tile, also by warp shuffles); one (c0, c1) pair per tile goes to global
+//    memory.  The finalise
 //    kernel (one warp per prime and kind) merges the tiles of each sum, forms
 //    sum_j coef_j c1_j / c0_j as one fraction, and inverts once (Fermat).
 //
@@ -132,6 +142,201 @@ __global__ void k_plan_split(Plan P) {
   *P.split_tile = (n31 < P.n) ? P.seg_first[n31 * P.rows_pp] : *P.total_tiles;
   P.counters[0] = 0;
   P.counters[1] = 0;
+}
+
+// ------------------------------------------------------------------ lane chains
+// With lane chains every tile is one lane's piece of a segment.  The planner
+// splits segment s into ceil(cnt_s / L) pieces, where the chain length L of
+// the segment's path (32-bit or 64-bit kernel) is the larger of a floor that
+// keeps the per-chain set-up small and the path's terms over the number of
+// chains that fill the GPU kLaneRounds times over (so that no chain runs
+// longer than about 1/kLaneRounds of the launch, and the longest start
+// first); it then
+// sorts the tiles by class (signed 32-bit, unsigned 32-bit, 64-bit; B or E)
+// and, inside a class, by length (32 steps per octave), so that the
+// lanes of a warp run one code path for about the same number of terms.
+constexpr int kChainClasses = 6;
+constexpr uint32_t kChainBins = 2048;  // length bins per class
+// chains wanted per path: resident threads per SM (3 blocks of 256 on the
+// 32-bit kernel, 2 on the 64-bit one) x SMs x rounds (kLaneRounds for a
+// call, kLaneRoundsEpoch for a serving plan, whose epochs mix many plans);
+// shortest chain lengths (the 64-bit path's set-up costs about 40 groups)
+constexpr uint64_t kLaneThreads31 = 768, kLaneThreads64 = 512;
+constexpr uint64_t kLaneRounds = 16, kLaneRoundsEpoch = 4;
+constexpr uint64_t kLaneMin31 = 4096, kLaneMin64 = 16384;
+
+__global__ void k_lane_sum(Plan P) {  // terms per path
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t ns = (size_t)P.n * P.rows_pp;
+  uint64_t c31 = 0, c64 = 0;
+  if (idx < ns) {
+    const uint64_t c = P.seg_cnt[idx];
+    if (idx / P.rows_pp >= *P.n31) c64 = c; else c31 = c;
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    c31 += __shfl_down_sync(0xffffffffu, c31, o);
+    c64 += __shfl_down_sync(0xffffffffu, c64, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (c31) atomicAdd((unsigned long long *)&P.lane_sum[0], (unsigned long long)c31);
+    if (c64) atomicAdd((unsigned long long *)&P.lane_sum[1], (unsigned long long)c64);
+  }
+}
+
+__device__ __forceinline__ uint64_t lane_chain_len(const Plan &P, int path) {
+  const uint64_t t = P.lane_target[path];
+  const uint64_t L = (P.lane_sum[path] + t - 1) / t;
+  return L > P.lane_min[path] ? L : P.lane_min[path];
+}
+
+__global__ void k_lane_chains(Plan P) {  // pieces per segment
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)P.n * P.rows_pp) return;
+  const uint64_t cnt = P.seg_cnt[idx];
+  uint32_t t = 0;
+  if (cnt) {
+    const uint64_t L = lane_chain_len(P, idx / P.rows_pp >= *P.n31 ? 1 : 0);
+    t = (uint32_t)((cnt + L - 1) / L);  // <= terms / L + 1: within tiles_capacity
+  }
+  P.seg_tiles[idx] = t;
+}
+
+// sort key of tile g: class * kChainBins + length bin (the kernels take warps
+// from the top of their range, so the longest chains of a class start first)
+__device__ __forceinline__ uint32_t chain_key(const Plan &P, uint32_t g) {
+  const uint32_t s = P.tile_seg[g];
+  const uint32_t slot = s / P.rows_pp, j = s - slot * P.rows_pp;
+  const uint32_t k = g - P.seg_first[s], T = P.seg_tiles[s];
+  const uint64_t cnt = P.seg_cnt[s];
+  const uint64_t n = cnt * (k + 1) / T - cnt * k / T;  // >= 1
+  const uint32_t path = slot >= *P.n31 ? 2u : (P.ctx[slot].flags & 1u) ? 1u : 0u;
+  const uint32_t cls = path * 2 + (j >= P.rows_b ? 1u : 0u);
+  const uint32_t e = 63 - __clzll((long long)n);
+  const uint32_t frac = (uint32_t)((e >= 5 ? n >> (e - 5) : n << (5 - e)) & 31u);
+  return cls * kChainBins + (e * 32 + frac);
+}
+
+// counts per key (warp-aggregated atomics); keys kept for the scatter
+__global__ void k_chain_hist(Plan P) {
+  const uint32_t total = *P.total_tiles, lane = threadIdx.x & 31;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t b = (size_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); b < total; b += stride) {
+    const size_t g = b + lane;
+    const uint32_t key = g < total ? chain_key(P, (uint32_t)g) : 0xffffffffu;
+    if (g < total) P.chain_key[g] = key;
+    const uint32_t peers = __match_any_sync(0xffffffffu, key);
+    if (key != 0xffffffffu && lane == (uint32_t)(__ffs(peers) - 1))
+      atomicAdd(&P.chain_hist[key], (uint32_t)__popc(peers));
+  }
+}
+
+// one block: counts -> first positions, each class starting on a whole warp;
+// padding slots get kNoChain; lane_w = {32-bit kernel's warps, all warps}
+constexpr int kOffThreads = 1024;
+__global__ void __launch_bounds__(kOffThreads) k_chain_offsets(Plan P) {
+  __shared__ uint32_t sh[kOffThreads];
+  __shared__ uint32_t base;
+  const uint32_t t = threadIdx.x;
+  constexpr uint32_t per = kChainBins / kOffThreads;  // bins per thread and class
+  if (t == 0) base = 0;
+  __syncthreads();
+  for (int c = 0; c < kChainClasses; ++c) {
+    uint32_t h[per], v = 0;
+#pragma unroll
+    for (uint32_t i = 0; i < per; ++i) {
+      h[i] = P.chain_hist[c * kChainBins + t * per + i];
+      v += h[i];
+    }
+    sh[t] = v;
+    __syncthreads();
+    for (uint32_t o = 1; o < kOffThreads; o <<= 1) {  // inclusive scan (Hillis-Steele)
+      const uint32_t y = t >= o ? sh[t - o] : 0u;
+      __syncthreads();
+      sh[t] += y;
+      __syncthreads();
+    }
+    uint32_t pos = base + sh[t] - v;
+#pragma unroll
+    for (uint32_t i = 0; i < per; ++i) {
+      P.chain_hist[c * kChainBins + t * per + i] = pos;
+      pos += h[i];
+    }
+    __syncthreads();
+    if (t == 0) {
+      const uint32_t end = base + sh[kOffThreads - 1], padded = (end + 31u) & ~31u;
+      for (uint32_t x = end; x < padded; ++x) P.perm[x] = kNoChain;
+      base = padded;
+      if (c == 3) P.lane_w[0] = padded / 32;
+      if (c == kChainClasses - 1) P.lane_w[1] = padded / 32;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_chain_scatter(Plan P) {
+  const uint32_t total = *P.total_tiles, lane = threadIdx.x & 31;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t b = (size_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); b < total; b += stride) {
+    const size_t g = b + lane;
+    const uint32_t key = g < total ? P.chain_key[g] : 0xffffffffu;
+    const uint32_t peers = __match_any_sync(0xffffffffu, key);
+    const uint32_t leader = (uint32_t)(__ffs(peers) - 1);
+    uint32_t pos = 0;
+    if (key != 0xffffffffu && lane == leader) pos = atomicAdd(&P.chain_hist[key], (uint32_t)__popc(peers));
+    pos = __shfl_sync(0xffffffffu, pos, (int)leader);
+    if (key != 0xffffffffu) P.perm[pos + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)g;
+  }
+}
+
+// tiles a plan of ns segments may hold: with lane chains sum_s ceil(cnt_s / L)
+// is at most the chains wanted per path plus the segments (L >= a path's
+// terms / its chains wanted); warp tiles: max_tiles per segment
+static size_t tiles_capacity(const ResidueConfig &cfg, size_t ns, uint32_t max_tiles, int sms,
+                             uint64_t rounds) {
+  if (!cfg.lane_chains()) return ns * max_tiles;
+  return ns + (size_t)sms * (kLaneThreads31 + kLaneThreads64) * rounds;
+}
+
+// the lane-chain fields of a plan whose other buffers are set; `get`
+// allocates device memory
+template <typename Get>
+static wv_status lane_setup(Plan &P, size_t tiles_cap, uint32_t *scal, int sms, uint64_t rounds,
+                            Get get) {
+  P.lane = 1;
+  WV_CHECK(get((void **)&P.perm, (tiles_cap + 32 * kChainClasses) * sizeof(uint32_t)));
+  WV_CHECK(get((void **)&P.chain_key, tiles_cap * sizeof(uint32_t)));
+  WV_CHECK(get((void **)&P.chain_hist, (size_t)kChainClasses * kChainBins * sizeof(uint32_t)));
+  WV_CHECK(get((void **)&P.lane_sum, 2 * sizeof(uint64_t)));
+  P.lane_w = scal + 8;
+  P.lane_target[0] = (uint64_t)sms * kLaneThreads31 * rounds;
+  P.lane_target[1] = (uint64_t)sms * kLaneThreads64 * rounds;
+  P.lane_min[0] = kLaneMin31;
+  P.lane_min[1] = kLaneMin64;
+  return WV_OK;
+}
+
+// the planner's launch sequence after the prime contexts: segments, pieces
+// per segment, the tile map and, with lane chains, the sorted tile list
+static wv_status plan_launches(Plan &P, uint32_t *u32tmp, int sms, cudaStream_t s) {
+  const size_t ns = (size_t)P.n * P.rows_pp;
+  WV_LAUNCH("plan_segments", k_plan_segments, (unsigned)((ns + 255) / 256), 256, 0, s, P);
+  if (P.lane) {
+    WV_CUDA(cudaMemsetAsync(P.lane_sum, 0, 2 * sizeof(uint64_t), s));
+    WV_LAUNCH("lane_sum", k_lane_sum, (unsigned)((ns + 255) / 256), 256, 0, s, P);
+    WV_LAUNCH("lane_chains", k_lane_chains, (unsigned)((ns + 255) / 256), 256, 0, s, P);
+  }
+  WV_CHECK(scan_exclusive_u32(P.seg_tiles, P.seg_first, ns, P.total_tiles, u32tmp, s));
+  WV_LAUNCH("plan_tilemap", k_plan_tilemap, (unsigned)((ns + 255) / 256), 256, 0, s, P);
+  WV_LAUNCH("plan_split", k_plan_split, 1, 1, 0, s, P);
+  if (P.lane) {
+    const unsigned gs = (unsigned)(sms * 8);
+    WV_CUDA(cudaMemsetAsync(P.chain_hist, 0, (size_t)kChainClasses * kChainBins * 4, s));
+    WV_LAUNCH("chain_hist", k_chain_hist, gs, 256, 0, s, P);
+    WV_LAUNCH("chain_offsets", k_chain_offsets, 1, kOffThreads, 0, s, P);
+    WV_LAUNCH("chain_scatter", k_chain_scatter, gs, 256, 0, s, P);
+  }
+  return WV_OK;
 }
 
 // ------------------------------------------------------------------ finalize
@@ -281,7 +486,9 @@ template <bool WIDE>
 static wv_status launch_accumulate(const Plan &P, const ResidueConfig &cfg, int sms, cudaStream_t s) {
   const char *name = WIDE ? "accumulate_m64" : "accumulate_m31";
   AccKernel kern = nullptr;
-  if (WIDE) {
+  if (P.lane) {
+    kern = WIDE ? acc_kernel_lane64() : acc_kernel_lane31(cfg.ilp);
+  } else if (WIDE) {
     // arith 25..28 vary the 32-bit path only; the 64-bit path runs its default
     // the single-term forms (1, 2, 4) run the single-term 64-bit kernel, 12..18,
     // 21, 23..24 and 32..36 their own 64-bit forms, everything else the grouped
@@ -333,8 +540,9 @@ wv_status residues_device(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,
   WV_CHECK(sc.get(&P.seg_cnt, nseg));
   WV_CHECK(sc.get(&P.seg_tiles, nseg));
   WV_CHECK(sc.get(&P.seg_first, nseg));
-  WV_CHECK(sc.get(&P.partials, nseg * P.max_tiles));
-  WV_CHECK(sc.get(&P.tile_seg, nseg * P.max_tiles));
+  const size_t tiles_cap = tiles_capacity(cfg, nseg, P.max_tiles, dev->sms, kLaneRounds);
+  WV_CHECK(sc.get(&P.partials, tiles_cap));
+  WV_CHECK(sc.get(&P.tile_seg, tiles_cap));
   WV_CHECK(sc.get(&u32tmp, scan_tmp_elems(nseg)));
   WV_CHECK(sc.get(&scal, 256));
   P.bk = scal + 64;
@@ -342,6 +550,10 @@ wv_status residues_device(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,
   P.total_tiles = scal + 1;
   P.split_tile = scal + 2;
   P.counters = scal + 4;
+  if (cfg.lane_chains())
+    WV_CHECK(lane_setup(P, tiles_cap, scal, dev->sms, kLaneRounds, [&](void **p, size_t bytes) {
+      return sc.get((unsigned char **)p, bytes);
+    }));
 
   for (size_t base = 0; base < n; base += chunk) {
     P.n = (uint32_t)((n - base) < chunk ? (n - base) : chunk);
@@ -353,11 +565,7 @@ wv_status residues_device(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,
     WV_LAUNCH("plan_prime", k_plan_prime, gp, 256, 0, s, P);
     WV_LAUNCH("plan_buckets", k_plan_buckets, 1, 32, 0, s, P);
     WV_LAUNCH("plan_scatter", k_plan_scatter, gp, 256, 0, s, P);
-    const size_t ns = (size_t)P.n * P.rows_pp;
-    WV_LAUNCH("plan_segments", k_plan_segments, (unsigned)((ns + 255) / 256), 256, 0, s, P);
-    WV_CHECK(scan_exclusive_u32(P.seg_tiles, P.seg_first, ns, P.total_tiles, u32tmp, s));
-    WV_LAUNCH("plan_tilemap", k_plan_tilemap, (unsigned)((ns + 255) / 256), 256, 0, s, P);
-    WV_LAUNCH("plan_split", k_plan_split, 1, 1, 0, s, P);
+    WV_CHECK(plan_launches(P, u32tmp, dev->sms, s));
     WV_CHECK(launch_accumulate<false>(P, cfg, dev->sms, s));
     WV_CHECK(launch_accumulate<true>(P, cfg, dev->sms, s));
     const uint32_t nk = (do_b ? 1 : 0) + (do_e ? 1 : 0);
@@ -427,8 +635,14 @@ size_t plan_bytes(uint32_t n, const ResidueConfig &cfg) {
   const size_t ns = (size_t)n * rows_of(cfg);
   uint32_t tt = 0, mt = 0;
   tile_shape(cfg, n, rows_of(cfg), &tt, &mt);
-  return n * (sizeof(PrimeCtx) + 8) + ns * (8 + 8 + 4 + 4) + ns * mt * (sizeof(ulonglong2) + 4) +
-         scan_tmp_elems(ns) * 4 + 1024 + 16 * 256;
+  DeviceState *dev = nullptr;
+  const int sms = device_state(&dev) == WV_OK ? dev->sms : 160;
+  const size_t tc = tiles_capacity(cfg, ns, mt, sms, kLaneRoundsEpoch);
+  size_t b = n * (sizeof(PrimeCtx) + 8) + ns * (8 + 8 + 4 + 4) + tc * (sizeof(ulonglong2) + 4) +
+             scan_tmp_elems(ns) * 4 + 1024 + 16 * 256;
+  if (cfg.lane_chains())  // sorted tile list, keys, bins, terms per path
+    b += tc * 8 + 32 * kChainClasses * 4 + (size_t)kChainClasses * kChainBins * 4 + 16 + 4 * 256;
+  return b;
 }
 
 size_t plan_struct_bytes() { return sizeof(Plan); }
@@ -458,8 +672,9 @@ wv_status plan_build(const uint64_t *d_primes, uint32_t n, const ResidueConfig &
   WV_CHECK(get((void **)&P.seg_cnt, ns * 8));
   WV_CHECK(get((void **)&P.seg_tiles, ns * 4));
   WV_CHECK(get((void **)&P.seg_first, ns * 4));
-  WV_CHECK(get((void **)&P.partials, ns * P.max_tiles * sizeof(ulonglong2)));
-  WV_CHECK(get((void **)&P.tile_seg, ns * P.max_tiles * sizeof(uint32_t)));
+  const size_t tiles_cap = tiles_capacity(cfg, ns, P.max_tiles, dev->sms, kLaneRoundsEpoch);
+  WV_CHECK(get((void **)&P.partials, tiles_cap * sizeof(ulonglong2)));
+  WV_CHECK(get((void **)&P.tile_seg, tiles_cap * sizeof(uint32_t)));
   WV_CHECK(get((void **)&u32tmp, scan_tmp_elems(ns) * 4));
   WV_CHECK(get((void **)&scal, 1024));
   P.pos = nullptr;
@@ -468,6 +683,7 @@ wv_status plan_build(const uint64_t *d_primes, uint32_t n, const ResidueConfig &
   P.total_tiles = scal + 1;
   P.split_tile = scal + 2;
   P.counters = scal + 4;
+  if (cfg.lane_chains()) WV_CHECK(lane_setup(P, tiles_cap, scal, dev->sms, kLaneRoundsEpoch, get));
   P.n = n;
   P.primes = d_primes;
   ps->n = n;
@@ -476,19 +692,17 @@ wv_status plan_build(const uint64_t *d_primes, uint32_t n, const ResidueConfig &
   WV_LAUNCH("plan_prime", k_plan_prime, gp, 256, 0, s, P);
   WV_LAUNCH("plan_buckets", k_plan_buckets, 1, 32, 0, s, P);
   WV_LAUNCH("plan_scatter", k_plan_scatter, gp, 256, 0, s, P);
-  WV_LAUNCH("plan_segments", k_plan_segments, (unsigned)((ns + 255) / 256), 256, 0, s, P);
-  WV_CHECK(scan_exclusive_u32(P.seg_tiles, P.seg_first, ns, P.total_tiles, u32tmp, s));
-  WV_LAUNCH("plan_tilemap", k_plan_tilemap, (unsigned)((ns + 255) / 256), 256, 0, s, P);
-  WV_LAUNCH("plan_split", k_plan_split, 1, 1, 0, s, P);
-  return WV_OK;
+  return plan_launches(P, u32tmp, dev->sms, s);
 }
 
+// A plan's work units and the first unit of the 64-bit kernel: tiles, or
+// with lane chains warps of the sorted tile list (lane_w at scal + 8).
 wv_status plan_totals(PlanState *ps, cudaStream_t s) {
-  uint32_t v[3] = {0, 0, 0};
-  WV_CUDA(cudaMemcpyAsync(v, ps->host->n31, 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  uint32_t v[10] = {};
+  WV_CUDA(cudaMemcpyAsync(v, ps->host->n31, 10 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   WV_CUDA(cudaStreamSynchronize(s));
-  ps->total = v[1];
-  ps->split = v[2];
+  ps->total = ps->host->lane ? v[9] : v[1];
+  ps->split = ps->host->lane ? v[8] : v[2];
   return WV_OK;
 }
 
@@ -501,7 +715,7 @@ wv_status epoch_launch(bool wide, const EpochItem *d_items, uint32_t n_items, ui
                        const Plan *d_plans, uint32_t *d_counter, const ResidueConfig &cfg, int sms,
                        int reserve_blocks, cudaStream_t s) {
   if (total == 0) return WV_OK;
-  EpochKernel kern = epoch_kernel(wide, wide ? cfg.ilp64 : cfg.ilp);
+  EpochKernel kern = epoch_kernel(wide, wide ? cfg.ilp64 : cfg.ilp, cfg.lane_chains());
   int occ = 0;
   WV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, cfg.block, 0));
   if (occ < 1) occ = 1;
@@ -518,7 +732,7 @@ wv_status epoch_launch_mixed(const EpochItem *d_items, uint32_t n_items, uint32_
                              const Plan *d_plans, uint32_t *d_counter, const ResidueConfig &cfg,
                              int sms, int reserve_blocks, cudaStream_t s) {
   if (total == 0) return WV_OK;
-  EpochKernel kern = epoch_mixed_kernel(cfg.ilp, cfg.ilp64);
+  EpochKernel kern = epoch_mixed_kernel(cfg.ilp, cfg.ilp64, cfg.lane_chains());
   int occ = 0;
   WV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, cfg.block, 0));
   if (occ < 1) occ = 1;
@@ -535,7 +749,7 @@ wv_status epoch_launch_tiles(const EpochItem *d_items, uint32_t n_items, uint32_
                              const Plan *d_plans, const ResidueConfig &cfg, cudaStream_t s) {
   if (total == 0) return WV_OK;
   const uint32_t wpb = (uint32_t)(cfg.block / 32);
-  WV_LAUNCH("epoch", epoch_tiles_kernel(cfg.ilp), (total + wpb - 1) / wpb, cfg.block, 0, s, d_items,
+  WV_LAUNCH("epoch", epoch_tiles_kernel(cfg.ilp, cfg.lane_chains()), (total + wpb - 1) / wpb, cfg.block, 0, s, d_items,
             n_items, total, d_plans);
   return WV_OK;
 }

@@ -292,7 +292,10 @@ wv_status resolve_config(const wv_options *opt, bool want_b, bool want_e, Residu
     if (opt->blocks_per_sm > 0) c.blocks_per_sm = opt->blocks_per_sm;
     if (opt->arith > 0) c.arith = opt->arith;
     c.check_primes = opt->check_primes != 0;
+    c.tiling = opt->tiling;
   }
+  if (c.tiling < 0 || c.tiling > 2)
+    return set_error(WV_EINVAL, "tiling=%d must be 0, 1 or 2", c.tiling);
   if (c.cong_b >= 0 && (c.cong_b >= cong_count() || cong_view(c.cong_b).kind != 0))
     return set_error(WV_EINVAL, "cong_b=%d is not a Bernoulli congruence", c.cong_b);
   if (c.cong_e >= 0 && (c.cong_e >= cong_count() || cong_view(c.cong_e).kind != 1))

@@ -58,7 +58,8 @@ class wv_options(ctypes.Structure):
     _fields_ = [("cong_b", ctypes.c_int), ("cong_e", ctypes.c_int), ("block", ctypes.c_int),
                 ("ilp", ctypes.c_int), ("tile_terms", ctypes.c_int), ("max_tiles", ctypes.c_int),
                 ("blocks_per_sm", ctypes.c_int), ("arith", ctypes.c_int),
-                ("check_primes", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+                ("check_primes", ctypes.c_int), ("tiling", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
 
 
 _lock = threading.Lock()

@@ -59,11 +59,11 @@ def test_host_validation_without_gpu():
     # the formulation and launch options are checked before any device work
     for bad in ({"arith": 24}, {"arith": 40}, {"arith": 3}, {"arith": 10}, {"arith": 19},
                 {"arith": 25, "ilp": 4}, {"arith": 31, "ilp": 4}, {"arith": 2, "ilp": 4},
-                {"ilp": 4}, {"ilp": 3}, {"block": 48}):
+                {"ilp": 4}, {"ilp": 3}, {"block": 48}, {"tiling": 3}, {"tiling": -1}):
         assert lib.wv_residues_ex(None, 0, None, None, wv._options(bad), None) == wv.WV_EINVAL, bad
     for good in ({"arith": 23}, {"arith": 25}, {"arith": 28, "ilp": 1}, {"arith": 9, "ilp": 4},
                  {"arith": 32}, {"arith": 37}, {"arith": 38}, {"arith": 39, "ilp": 1}, {"arith": 21, "ilp": 4},
-                 {"check_primes": 1}):
+                 {"check_primes": 1}, {"tiling": 1}, {"tiling": 2, "ilp": 1}):
         assert lib.wv_residues_ex(None, 0, None, None, wv._options(good), None) == wv.WV_OK, good
 
 

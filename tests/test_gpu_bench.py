@@ -28,7 +28,7 @@ def test_bench_window_line():
     for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "roofline",
               "e2e", "clocks", "gpu_launches", "cpu_baseline", "config"):
         assert k in d, k
-    assert d["value"] > 0 and d["gpu_launches"] > 0 and d["config"]["congruences"] == "BB476+EE404"
+    assert d["value"] > 0 and d["gpu_launches"] > 0 and d["config"]["congruences"] == "BB2244+EE2004"
     r = d["roofline"]
     assert r["bound"] == "alu" and r["kernel"] == "accumulate_m31" and r["terms_per_clk_sm"] > 0
     assert r["traffic"] is None  # a partial window: no full-launch traffic figure

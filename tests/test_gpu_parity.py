@@ -109,7 +109,7 @@ def test_p1e9_window_cross_congruences():
     ps = u64(api.sieve(*W.P1E9_WINDOW))
     ref_b, ref_e = gpu_residues(ps)
     # the paper's 13 congruences and the 8 generated ones, each against the
-    # default of a device prime list (BB30 + EE33); BB476 + EE404 is what the
+    # default of a device prime list (BB30 + EE33); BB2244 + EE2004 is what the
     # search picks for this window
     for nb, ne in (("BB1", "EE3"), ("BB2", "EE5"), ("BB6", "EE9"), ("BB9", "EE16"),
                    ("BB16", "EE24"), ("BB22", "EE33"), ("BB249", "EE200"), ("BB476", "EE967"),
@@ -184,6 +184,7 @@ def test_launch_shapes_agree():
                 {"arith": 1}, {"arith": 2}, {"arith": 4}, {"arith": 9}, {"arith": 9, "ilp": 1},
                 {"arith": 9, "tile_terms": 5000, "max_tiles": 64},
                 {"block": 32}, {"block": 96, "ilp": 1}, {"block": 128},
+                {"tiling": 1}, {"tiling": 1, "ilp": 1}, {"tiling": 2, "ilp": 1},
                 *({"arith": a} for a in (*range(12, 19), 21, 23, *range(32, 39))),
                 *({"arith": a, "ilp": i} for a in (*range(25, 32), 39) for i in (1, 2))):
         gb, ge = gpu_residues(ps, opt)
