@@ -50,8 +50,19 @@ IMAD_SLOTS_PER_MODMUL64 = 17
 # run is that busy share scaled by the run's own terms per SM per clock.  Set an entry to None
 # whenever its kernel changes, until it is captured again.
 PIPE_PROFILE = {
-    "accumulate_m31": None,  # lane-chain kernel: not yet captured
-    "accumulate_m64": None,
+    # k_accumulate<0,1,39,1> (form 39, lane chains): 492 primes of [1062200000, 1062210000),
+    # BB2244 + EE2004, 2.3139e10 terms, 9.892 ms at 2.067 GHz; IMAD pipe 81.34 %, ALU 73.78 % of
+    # elapsed.  Traffic: one launch of the full window (--metrics dram__bytes_read.sum,
+    # dram__bytes_write.sum, the second launch): 10.545 GB read + 0.659 GB written
+    "accumulate_m31": {"imad_pct": 0.8134, "alu_pct": 0.7378, "terms_per_clk_sm": 7.446,
+                       "traffic_bytes": 10545422080 + 659143680,
+                       "profile": "profiles/accumulate_m31_p1e9_small.md"},
+    # k_accumulate_m64cap<9,128,1> (lane chains): 17 primes of [1e11 - 1e4, 1e11 - 9500),
+    # BB2244 + EE2004, 7.5269e10 terms, 51.147 ms at 2.069 GHz; IMAD pipe 90.52 %, ALU 58.59 %
+    # Traffic: one launch of the full 391-prime window (second launch): 69.4 MB read + 22.4 MB written
+    "accumulate_m64": {"imad_pct": 0.9052, "alu_pct": 0.5859, "terms_per_clk_sm": 4.678,
+                       "traffic_bytes": 69445632 + 22405120,
+                       "profile": "profiles/accumulate_m64_top_window.md"},
 }
 
 
@@ -320,9 +331,10 @@ def gpu_arm(args):
         frac = prof_k["imad_pct"] * tpcs / prof_k["terms_per_clk_sm"]
         roof = {"bound": "alu", "achieved": frac * pipe_peak, "peak": pipe_peak,
                 "unit": "IMAD-pipe cycles/s", "frac": frac,
-                "traffic": prof_k["dram_bytes_per_prime"] * n_primes if full_launch else None,
-                "traffic_basis": f"ncu dram__bytes_read.sum + dram__bytes_write.sum of {prof_k['profile']}, "
-                                 "scaled by primes to this launch",
+                "traffic": prof_k["traffic_bytes"] if full_launch else None,
+                "traffic_basis": (f"ncu dram__bytes_read.sum + dram__bytes_write.sum of one full launch "
+                                  f"({prof_k['profile']})" if prof_k["traffic_bytes"] else
+                                  "not captured for the current kernel at this size"),
                 "frac_basis": f"IMAD-pipe busy {prof_k['imad_pct']:.3f} at {prof_k['terms_per_clk_sm']:.3f} "
                               f"terms/clk/SM ({prof_k['profile']}); this run {tpcs:.3f} terms/clk/SM at "
                               f"{clk_mhz:.0f} MHz",

@@ -179,7 +179,7 @@ typedef struct {
                        default 256.  Smaller blocks release their registers warp by
                        warp at the end of a launch and round occupancy differently */
   int ilp;          /* independent accumulator chains per thread for p < 2^31: 1, 2 or 4
-                       (4 only with arith 9, 12..18, 21 or 23; default 2).  The grouped 64-bit forms
+                       (4 only with arith 9, 12..18, 21 or 23; default 1).  The grouped 64-bit forms
                        (arith >= 9) run one chain per thread; the single-term 64-bit
                        form takes this value too */
   int tile_terms;   /* target terms per warp tile (default 2^20) */
@@ -187,7 +187,7 @@ typedef struct {
                        call with few primes gets more and shorter tiles (up to 64 per
                        sum) so that one launch still holds ~1e5 tiles */
   int blocks_per_sm;/* persistent grid = SMs x this */
-  int arith;        /* hot-loop formulation (default 31).  Every value gives the same
+  int arith;        /* hot-loop formulation (default 39).  Every value gives the same
                        residues; the others exist for ablation.  32-bit path (p < 2^31;
                        signed words below 2^30, unsigned from 2^30 to 2^31):
                        1, 2, 4 single terms (1: shared t p^-1; 2: one wide product and
@@ -197,7 +197,7 @@ typedef struct {
                        group's difference-table additions as ALU-only three-input adds
                        (9 itself: 4 of a Bernoulli group's 9 and 2 of an Euler group's
                        10); 29, 30, 31 groups of 3 cubes, of 4 squares, or both; 39
-                       groups of 4 cubes / 5 squares.  64-bit
+                       (default) groups of 4 cubes / 5 squares.  64-bit
                        path (2^31 <= p < 2^37): 1, 2, 4 the single-term 64-bit kernel;
                        12..18 and 21 other group sizes, shrink intervals and register
                        budgets; 32..36 the default with a quarter to all of its 64-bit
@@ -217,8 +217,8 @@ typedef struct {
   int tiling;       /* work unit of the accumulation.  0 (default) or 2: lane chains --
                        every lane of a warp sums its own piece of one (prime, sum), the
                        pieces sorted by length so that a warp's lanes finish together;
-                       used with the default formulation (31) and ILP 1 or 2, warp tiles
-                       otherwise.  1: warp tiles -- the 32 lanes of a warp split one piece
+                       used with the grouped formulations 39 (default) and 31 and ILP 1 or
+                       2, warp tiles otherwise.  1: warp tiles -- the 32 lanes of a warp split one piece
                        and merge by shuffles (the earlier work unit, kept for ablation).
                        Other values: WV_EINVAL */
   int reserved[6];

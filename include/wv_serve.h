@@ -27,7 +27,7 @@ extern "C" {
 typedef struct wv_server_s *wv_server;
 
 typedef struct {
-  size_t mem_budget;     /* device bytes for admitted queries (0: 16 GiB)           */
+  size_t mem_budget;     /* device bytes for admitted queries (0: 64 GiB)           */
   uint32_t max_active;   /* queries admitted at once (0: 256)                        */
   double epoch_terms;    /* summed terms per epoch, bounds its duration (0: 4e10)    */
   int device;            /* CUDA device (-1: current device at creation)              */

@@ -63,6 +63,7 @@ struct Plan {
   uint32_t *perm, *chain_key, *chain_hist, *lane_w;
   uint64_t *lane_sum, *lane_len;
   uint64_t lane_target[2], lane_min[2];  // chains wanted per path, shortest chain length
+  uint64_t lane_fix[2];  // nonzero: the chain length per path, fixed by the host
 };
 constexpr uint32_t kNoChain = 0xffffffffu;
 
@@ -1055,9 +1056,10 @@ __device__ __forceinline__ void tile_general(const PrimeCtx &ctx, uint64_t start
 // fastest on GB300 of 0, 2..6 and all); 25: none, 26: 4 and 4, 27: 6 and 6,
 // 28: all (ablation).  29..31 are 9 with larger groups: 3 cubes (15
 // additions, 6 ALU-only), 4 squares (14 additions, 4 ALU-only), or both (31,
-// the default).  39: larger groups still, 4 cubes / 5 squares (21 and 18
-// additions, 6 and 4 ALU-only); of 4 / 5 with 8 / 6 ALU-only, 3 / 5 and 4 / 4
-// it was the fastest, and faster than 31 on long sums only.
+// the default with warp tiles).  39: larger groups still, 4 cubes / 5 squares
+// (21 and 18 additions, 6 and 4 ALU-only); of 4 / 5 with 8 / 6 ALU-only,
+// 3 / 5 and 4 / 4 it was the fastest, and faster than 31 on long sums: with
+// lane chains (where every chain is long) it is the default, at ILP 1.
 template <int AR> struct M31Form { static constexpr int KC = 0, KS = 0, NFC = 4, NFS = 2; };
 template <> struct M31Form<25> { static constexpr int KC = 0, KS = 0, NFC = 0, NFS = 0; };
 template <> struct M31Form<26> { static constexpr int KC = 0, KS = 0, NFC = 4, NFS = 4; };
@@ -1222,7 +1224,7 @@ __global__ void __maxnreg__(kM64MaxReg)
     const EpochItem it = items[lo];
     const uint32_t tile = it.first + it.count - 1 - (g - it.prefix);
     if (it.plan >> 31) process_tile<true, I64, 9, LANE>(plans[it.plan & 0x7fffffffu], tile);
-    else process_tile<false, I31, 31, LANE>(plans[it.plan], tile);
+    else process_tile<false, I31, 39, LANE>(plans[it.plan], tile);
   }
 }
 
@@ -1243,7 +1245,7 @@ __global__ void __maxnreg__(kM64MaxReg)
   const EpochItem it = items[lo];
   const uint32_t tile = it.first + it.count - 1 - (g - it.prefix);
   if (it.plan >> 31) process_tile<true, I64, 9, LANE>(plans[it.plan & 0x7fffffffu], tile);
-  else process_tile<false, I31, 31, LANE>(plans[it.plan], tile);
+  else process_tile<false, I31, 39, LANE>(plans[it.plan], tile);
 }
 
 // ------------------------------------------------------------------ getters
@@ -1264,9 +1266,9 @@ AccKernel acc_kernel_m64w(int arith, int ilp);
 AccKernel acc_kernel_m64v(int arith, int ilp);  // forms 32..36 (w falls through to v)
 // 32-bit path: formulation 9 with other ALU-only splits or group sizes (arith 25..31), ILP 1 or 2
 AccKernel acc_kernel_m31x(int arith, int ilp);
-// lane chains: the 32-bit default (formulation 31, ILP 1 or 2) and the
-// 64-bit grouped default (one chain per thread)
-AccKernel acc_kernel_lane31(int ilp);
+// lane chains: the 32-bit grouped formulations 39 (default) and 31, ILP 1 or
+// 2, and the 64-bit grouped default (one chain per thread)
+AccKernel acc_kernel_lane31(int arith, int ilp);
 AccKernel acc_kernel_lane64();
 AccKernel acc_kernel_m31y(int arith, int ilp);  // form 39 (x falls through to y)
 // serving-loop epoch kernels (the default formulations: 31 on the 32-bit path,

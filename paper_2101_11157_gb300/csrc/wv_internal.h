@@ -128,22 +128,23 @@ struct ResidueConfig {
   bool cong_auto_b = true;  // not chosen by the caller: range-aware calls pick by p
   bool cong_auto_e = true;
   int block = 256;
-  int ilp = 2;            // chains per thread, p < 2^31
+  int ilp = 1;            // chains per thread, p < 2^31
   int ilp64 = 1;          // chains per thread, 2^31 <= p < 2^37
   int tile_terms = 1 << 20;
   int max_tiles = 8;
   bool tiles_auto = true; // few primes: more, shorter tiles (see tile_shape)
   int blocks_per_sm = 0;  // 0 = occupancy
-  int arith = 31;         // hot-loop formulation (see wv_accum.cuh)
+  int arith = 39;         // hot-loop formulation (see wv_accum.cuh)
   uint32_t gen_e_b = 0;   // general index: B_{p-e} (e odd); 0 = the B_{p-3} forms
   uint32_t gen_e_e = 0;   // general index: E_{p-1-e} (e even); 0 = the E_{p-3} forms
   size_t chunk = 0;       // primes per launch sequence (0: library default 16384)
   bool check_primes = false;  // planner verifies primality (composites -> invalid slot)
   int tiling = 0;         // 0 / 2: lane chains where supported, 1: warp tiles
-  // lane chains apply to the default formulation with ILP 1 or 2 and not to
-  // the general index (its own single-term tiles)
+  // lane chains apply to the grouped formulations 39 (the default) and 31
+  // with ILP 1 or 2, and not to the general index (its own single-term tiles)
   bool lane_chains() const {
-    return tiling != 1 && arith == 31 && (ilp == 1 || ilp == 2) && !gen_e_b && !gen_e_e;
+    return tiling != 1 && (arith == 31 || arith == 39) && (ilp == 1 || ilp == 2) && !gen_e_b &&
+           !gen_e_e;
   }
 };
 wv_status resolve_config(const wv_options *opt, bool want_b, bool want_e, ResidueConfig *cfg);
@@ -151,8 +152,8 @@ wv_status resolve_config(const wv_options *opt, bool want_b, bool want_e, Residu
 // The hot-loop formulations a caller may select (wv_options.arith):
 //   32-bit path (p < 2^31): 1, 2, 4 single terms; 9 groups of 2 cubes / 3
 //   squares; 25..28 form 9 with other ALU/multiply-pipe splits of the table
-//   additions; 29, 30, 31 groups of 3 cubes, 4 squares, or both (31: the
-//   default); 39 groups of 4 cubes / 5 squares (M31Form in wv_accum.cuh).
+//   additions; 29, 30, 31 groups of 3 cubes, 4 squares, or both; 39 groups
+//   of 4 cubes / 5 squares (the default; M31Form in wv_accum.cuh).
 //   64-bit path (2^31 <= p < 2^37): 1, 2, 4 single terms; every
 //   other value runs the grouped default (8 cubes / 10 squares) except 12..18
 //   and 21, other group sizes and register budgets, 32..36, the default
@@ -184,13 +185,18 @@ struct PlanState {
   int nblocks = 0;
   size_t bytes = 0;         // device bytes held
   uint32_t n = 0, total = 0, split = 0;  // primes, tiles, first 64-bit tile
+  double terms[2] = {-1, -1};  // with lane chains: terms on the 32-bit / 64-bit kernel
 };
-// Allocate (stream-ordered) and plan n <= 65536 primes; asynchronous.
+// Allocate (stream-ordered) and plan n <= 65536 primes; asynchronous.  With
+// lane chains and `terms` (upper bounds on the plan's terms on the 32-bit and
+// the 64-bit kernel), the chain lengths are fixed on the host and bounded
+// for epochs; without, they follow the device's term counts.
 wv_status plan_build(const uint64_t *d_primes, uint32_t n, const ResidueConfig &cfg,
-                     PlanState *ps, cudaStream_t s);
-// Device bytes plan_build will hold for n primes.
-size_t plan_bytes(uint32_t n, const ResidueConfig &cfg);
-// Synchronise s and read the plan's tile totals into ps.
+                     PlanState *ps, cudaStream_t s, const double *terms = nullptr);
+// Device bytes plan_build will hold for n primes (the same `terms`).
+size_t plan_bytes(uint32_t n, const ResidueConfig &cfg, const double *terms = nullptr);
+// Synchronise s and read the plan's tile totals (and, with lane chains, its
+// exact terms per kernel) into ps.
 wv_status plan_totals(PlanState *ps, cudaStream_t s);
 // Copy the plan struct to device memory at d_plan (asynchronous).
 wv_status plan_upload(const PlanState *ps, Plan *d_plan, cudaStream_t s);

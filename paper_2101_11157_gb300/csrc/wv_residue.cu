@@ -163,24 +163,35 @@ constexpr uint32_t kChainBins = 2048;  // length bins per class
 // shortest chain lengths (the 64-bit path's set-up costs about 40 groups)
 constexpr uint64_t kLaneThreads31 = 768, kLaneThreads64 = 512;
 constexpr uint64_t kLaneRounds = 16, kLaneRoundsEpoch = 4;
+// a serving plan's chains are at most kLaneMaxEpoch terms long, so that an
+// epoch is never held up by one long chain (about 2 ms of one lane on the
+// 32-bit kernel, 3.5 ms on the 64-bit one) and the shortest epochs still
+// hold enough warps to fill the GPU
+constexpr uint64_t kLaneMaxEpoch = 1ull << 15;
 constexpr uint64_t kLaneMin31 = 4096, kLaneMin64 = 16384;
 
-__global__ void k_lane_sum(Plan P) {  // terms per path
-  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const size_t ns = (size_t)P.n * P.rows_pp;
+__global__ void k_lane_sum(Plan P) {  // terms per path: one atomic per block and path
+  __shared__ unsigned long long sh[2][8];
+  const size_t ns = (size_t)P.n * P.rows_pp, stride = (size_t)gridDim.x * blockDim.x;
+  const uint32_t n31 = *P.n31;
   uint64_t c31 = 0, c64 = 0;
-  if (idx < ns) {
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < ns; idx += stride) {
     const uint64_t c = P.seg_cnt[idx];
-    if (idx / P.rows_pp >= *P.n31) c64 = c; else c31 = c;
+    if (idx / P.rows_pp >= n31) c64 += c; else c31 += c;
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
     c31 += __shfl_down_sync(0xffffffffu, c31, o);
     c64 += __shfl_down_sync(0xffffffffu, c64, o);
   }
-  if ((threadIdx.x & 31) == 0) {
-    if (c31) atomicAdd((unsigned long long *)&P.lane_sum[0], (unsigned long long)c31);
-    if (c64) atomicAdd((unsigned long long *)&P.lane_sum[1], (unsigned long long)c64);
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) sh[0][w] = c31, sh[1][w] = c64;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long a = 0, b = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) a += sh[0][i], b += sh[1][i];
+    if (a) atomicAdd((unsigned long long *)&P.lane_sum[0], a);
+    if (b) atomicAdd((unsigned long long *)&P.lane_sum[1], b);
   }
 }
 
@@ -196,20 +207,28 @@ __global__ void k_lane_chains(Plan P) {  // pieces per segment
   const uint64_t cnt = P.seg_cnt[idx];
   uint32_t t = 0;
   if (cnt) {
-    const uint64_t L = lane_chain_len(P, idx / P.rows_pp >= *P.n31 ? 1 : 0);
-    t = (uint32_t)((cnt + L - 1) / L);  // <= terms / L + 1: within tiles_capacity
+    const int path = idx / P.rows_pp >= *P.n31 ? 1 : 0;
+    const uint64_t L = P.lane_fix[path] ? P.lane_fix[path] : lane_chain_len(P, path);
+    t = (uint32_t)((cnt + L - 1) / L);  // <= terms / L + 1: within the tile capacity
   }
   P.seg_tiles[idx] = t;
 }
 
-// sort key of tile g: class * kChainBins + length bin (the kernels take warps
-// from the top of their range, so the longest chains of a class start first)
-__device__ __forceinline__ uint32_t chain_key(const Plan &P, uint32_t g) {
-  const uint32_t s = P.tile_seg[g];
+// Segments in row-major order (row j, then slot): the lanes of a warp take
+// one row of 32 consecutive primes, whose pieces mostly share a length bin,
+// so that one atomic serves the warp.
+__device__ __forceinline__ uint32_t seg_rowmajor(const Plan &P, size_t idx) {
+  const uint32_t j = (uint32_t)(idx / P.n), slot = (uint32_t)(idx - (size_t)j * P.n);
+  return slot * P.rows_pp + j;
+}
+
+// Sort key of the T pieces of segment s: class * kChainBins + length bin of
+// the longest piece (the others are one term shorter at most).  The kernels
+// take warps from the top of their range, so the longest pieces start first.
+__device__ __forceinline__ uint32_t seg_key(const Plan &P, uint32_t s, uint32_t T) {
   const uint32_t slot = s / P.rows_pp, j = s - slot * P.rows_pp;
-  const uint32_t k = g - P.seg_first[s], T = P.seg_tiles[s];
   const uint64_t cnt = P.seg_cnt[s];
-  const uint64_t n = cnt * (k + 1) / T - cnt * k / T;  // >= 1
+  const uint64_t n = (cnt + T - 1) / T;  // >= 1
   const uint32_t path = slot >= *P.n31 ? 2u : (P.ctx[slot].flags & 1u) ? 1u : 0u;
   const uint32_t cls = path * 2 + (j >= P.rows_b ? 1u : 0u);
   const uint32_t e = 63 - __clzll((long long)n);
@@ -217,17 +236,25 @@ __device__ __forceinline__ uint32_t chain_key(const Plan &P, uint32_t g) {
   return cls * kChainBins + (e * 32 + frac);
 }
 
-// counts per key (warp-aggregated atomics); keys kept for the scatter
+// counts per key: segments of one piece add through one atomic per key and
+// warp, longer segments their piece count each; keys kept for the scatter
 __global__ void k_chain_hist(Plan P) {
-  const uint32_t total = *P.total_tiles, lane = threadIdx.x & 31;
-  const size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t b = (size_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); b < total; b += stride) {
-    const size_t g = b + lane;
-    const uint32_t key = g < total ? chain_key(P, (uint32_t)g) : 0xffffffffu;
-    if (g < total) P.chain_key[g] = key;
-    const uint32_t peers = __match_any_sync(0xffffffffu, key);
-    if (key != 0xffffffffu && lane == (uint32_t)(__ffs(peers) - 1))
-      atomicAdd(&P.chain_hist[key], (uint32_t)__popc(peers));
+  const size_t ns = (size_t)P.n * P.rows_pp, stride = (size_t)gridDim.x * blockDim.x;
+  const uint32_t lane = threadIdx.x & 31;
+  for (size_t b = (size_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); b < ns; b += stride) {
+    const size_t idx = b + lane;
+    uint32_t T = 0, key = 0;
+    if (idx < ns) {
+      const uint32_t s = seg_rowmajor(P, idx);
+      T = P.seg_tiles[s];
+      if (T) {
+        key = seg_key(P, s, T);
+        P.chain_key[s] = key;
+      }
+    }
+    const uint32_t peers = __match_any_sync(0xffffffffu, T == 1 ? key : 0xffff0000u | lane);
+    if (T == 1 && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&P.chain_hist[key], (uint32_t)__popc(peers));
+    if (T > 1) atomicAdd(&P.chain_hist[key], T);
   }
 }
 
@@ -275,17 +302,27 @@ __global__ void __launch_bounds__(kOffThreads) k_chain_offsets(Plan P) {
 }
 
 __global__ void k_chain_scatter(Plan P) {
-  const uint32_t total = *P.total_tiles, lane = threadIdx.x & 31;
-  const size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t b = (size_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); b < total; b += stride) {
-    const size_t g = b + lane;
-    const uint32_t key = g < total ? P.chain_key[g] : 0xffffffffu;
-    const uint32_t peers = __match_any_sync(0xffffffffu, key);
+  const size_t ns = (size_t)P.n * P.rows_pp, stride = (size_t)gridDim.x * blockDim.x;
+  const uint32_t lane = threadIdx.x & 31;
+  for (size_t b = (size_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); b < ns; b += stride) {
+    const size_t idx = b + lane;
+    uint32_t T = 0, key = 0, s = 0;
+    if (idx < ns) {
+      s = seg_rowmajor(P, idx);
+      T = P.seg_tiles[s];
+      if (T) key = P.chain_key[s];
+    }
+    const uint32_t peers = __match_any_sync(0xffffffffu, T == 1 ? key : 0xffff0000u | lane);
     const uint32_t leader = (uint32_t)(__ffs(peers) - 1);
     uint32_t pos = 0;
-    if (key != 0xffffffffu && lane == leader) pos = atomicAdd(&P.chain_hist[key], (uint32_t)__popc(peers));
+    if (T == 1 && lane == leader) pos = atomicAdd(&P.chain_hist[key], (uint32_t)__popc(peers));
     pos = __shfl_sync(0xffffffffu, pos, (int)leader);
-    if (key != 0xffffffffu) P.perm[pos + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)g;
+    if (T == 1) {
+      P.perm[pos + __popc(peers & ((1u << lane) - 1u))] = P.seg_first[s];
+    } else if (T > 1) {
+      const uint32_t f = P.seg_first[s], at = atomicAdd(&P.chain_hist[key], T);
+      for (uint32_t k = 0; k < T; ++k) P.perm[at + k] = f + k;
+    }
   }
 }
 
@@ -296,6 +333,21 @@ static size_t tiles_capacity(const ResidueConfig &cfg, size_t ns, uint32_t max_t
                              uint64_t rounds) {
   if (!cfg.lane_chains()) return ns * max_tiles;
   return ns + (size_t)sms * (kLaneThreads31 + kLaneThreads64) * rounds;
+}
+
+// Chain lengths of a serving plan from upper bounds t[path] on its terms:
+// t / (kLaneRoundsEpoch x the path's resident lanes), within [floor,
+// kLaneMaxEpoch]; the plan then holds at most segments + sum t / L tiles.
+static void epoch_chain_lengths(const double *t, int sms, uint64_t *L, size_t *extra_tiles) {
+  const uint64_t lanes[2] = {(uint64_t)sms * kLaneThreads31, (uint64_t)sms * kLaneThreads64};
+  const uint64_t lmin[2] = {kLaneMin31, kLaneMin64};
+  *extra_tiles = 0;
+  for (int i = 0; i < 2; ++i) {
+    const double want = t[i] / (double)(kLaneRoundsEpoch * lanes[i]);
+    uint64_t l = want > (double)kLaneMaxEpoch ? kLaneMaxEpoch : (uint64_t)want + 1;
+    L[i] = l < lmin[i] ? lmin[i] : l;
+    *extra_tiles += (size_t)(t[i] / (double)L[i]) + 1;
+  }
 }
 
 // the lane-chain fields of a plan whose other buffers are set; `get`
@@ -323,7 +375,7 @@ static wv_status plan_launches(Plan &P, uint32_t *u32tmp, int sms, cudaStream_t 
   WV_LAUNCH("plan_segments", k_plan_segments, (unsigned)((ns + 255) / 256), 256, 0, s, P);
   if (P.lane) {
     WV_CUDA(cudaMemsetAsync(P.lane_sum, 0, 2 * sizeof(uint64_t), s));
-    WV_LAUNCH("lane_sum", k_lane_sum, (unsigned)((ns + 255) / 256), 256, 0, s, P);
+    WV_LAUNCH("lane_sum", k_lane_sum, (unsigned)(sms * 8), 256, 0, s, P);
     WV_LAUNCH("lane_chains", k_lane_chains, (unsigned)((ns + 255) / 256), 256, 0, s, P);
   }
   WV_CHECK(scan_exclusive_u32(P.seg_tiles, P.seg_first, ns, P.total_tiles, u32tmp, s));
@@ -401,8 +453,19 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(Plan P) {
     // coefficient sum_k c_k d_k^-ex, in Montgomery form
     const uint32_t *w = P.cg_rows + 6 * (size_t)(reg0 + j);
     int64_t aM = 0;
-    for (uint32_t t = w[4]; t < w[4] + w[5]; ++t)
-      aM = M.add(aM, M.mul(M.to_mont(smod64(P.cg_tc[t], p)), dpow[P.cg_td[t]]));
+    for (uint32_t t = w[4]; t < w[4] + w[5]; ++t) {
+      // most coefficients are +-1 (every one of the generated Bernoulli
+      // congruences'), and all are far below p except at tiny p
+      const int64_t c = P.cg_tc[t], dp = dpow[P.cg_td[t]];
+      if (c == 1) {
+        aM = M.add(aM, dp);
+      } else if (c == -1) {
+        aM = M.sub(aM, dp);
+      } else {
+        const int64_t cm = (c >= 0 && c < p) ? c : (c < 0 && -c < p) ? c + p : smod64(c, p);
+        aM = M.add(aM, M.mul(M.to_mont(cm), dp));
+      }
+    }
     const int64_t X = M.mul(aM, C1);  // coef * C1 at C1's scale
     N = M.add(M.mul(N, C0), M.mul(X, D));
     D = M.mul(D, C0);
@@ -487,7 +550,7 @@ static wv_status launch_accumulate(const Plan &P, const ResidueConfig &cfg, int 
   const char *name = WIDE ? "accumulate_m64" : "accumulate_m31";
   AccKernel kern = nullptr;
   if (P.lane) {
-    kern = WIDE ? acc_kernel_lane64() : acc_kernel_lane31(cfg.ilp);
+    kern = WIDE ? acc_kernel_lane64() : acc_kernel_lane31(cfg.arith, cfg.ilp);
   } else if (WIDE) {
     // arith 25..28 vary the 32-bit path only; the 64-bit path runs its default
     // the single-term forms (1, 2, 4) run the single-term 64-bit kernel, 12..18,
@@ -631,13 +694,19 @@ static size_t rows_of(const ResidueConfig &cfg) {
   return r;
 }
 
-size_t plan_bytes(uint32_t n, const ResidueConfig &cfg) {
+size_t plan_bytes(uint32_t n, const ResidueConfig &cfg, const double *terms) {
   const size_t ns = (size_t)n * rows_of(cfg);
   uint32_t tt = 0, mt = 0;
   tile_shape(cfg, n, rows_of(cfg), &tt, &mt);
   DeviceState *dev = nullptr;
   const int sms = device_state(&dev) == WV_OK ? dev->sms : 160;
-  const size_t tc = tiles_capacity(cfg, ns, mt, sms, kLaneRoundsEpoch);
+  size_t tc = tiles_capacity(cfg, ns, mt, sms, kLaneRoundsEpoch);
+  if (cfg.lane_chains() && terms) {
+    uint64_t L[2];
+    size_t extra = 0;
+    epoch_chain_lengths(terms, sms, L, &extra);
+    tc = ns + extra;
+  }
   size_t b = n * (sizeof(PrimeCtx) + 8) + ns * (8 + 8 + 4 + 4) + tc * (sizeof(ulonglong2) + 4) +
              scan_tmp_elems(ns) * 4 + 1024 + 16 * 256;
   if (cfg.lane_chains())  // sorted tile list, keys, bins, terms per path
@@ -648,7 +717,7 @@ size_t plan_bytes(uint32_t n, const ResidueConfig &cfg) {
 size_t plan_struct_bytes() { return sizeof(Plan); }
 
 wv_status plan_build(const uint64_t *d_primes, uint32_t n, const ResidueConfig &cfg, PlanState *ps,
-                     cudaStream_t s) {
+                     cudaStream_t s, const double *terms) {
   if (n == 0 || n > 65536) return set_error(WV_EINVAL, "plan_build: n=%u not in [1, 65536]", n);
   DeviceState *dev = nullptr;
   WV_CHECK(device_state(&dev));
@@ -672,7 +741,12 @@ wv_status plan_build(const uint64_t *d_primes, uint32_t n, const ResidueConfig &
   WV_CHECK(get((void **)&P.seg_cnt, ns * 8));
   WV_CHECK(get((void **)&P.seg_tiles, ns * 4));
   WV_CHECK(get((void **)&P.seg_first, ns * 4));
-  const size_t tiles_cap = tiles_capacity(cfg, ns, P.max_tiles, dev->sms, kLaneRoundsEpoch);
+  size_t tiles_cap = tiles_capacity(cfg, ns, P.max_tiles, dev->sms, kLaneRoundsEpoch);
+  if (cfg.lane_chains() && terms) {
+    size_t extra = 0;
+    epoch_chain_lengths(terms, dev->sms, P.lane_fix, &extra);
+    tiles_cap = ns + extra;
+  }
   WV_CHECK(get((void **)&P.partials, tiles_cap * sizeof(ulonglong2)));
   WV_CHECK(get((void **)&P.tile_seg, tiles_cap * sizeof(uint32_t)));
   WV_CHECK(get((void **)&u32tmp, scan_tmp_elems(ns) * 4));
@@ -699,10 +773,14 @@ wv_status plan_build(const uint64_t *d_primes, uint32_t n, const ResidueConfig &
 // with lane chains warps of the sorted tile list (lane_w at scal + 8).
 wv_status plan_totals(PlanState *ps, cudaStream_t s) {
   uint32_t v[10] = {};
+  uint64_t t[2] = {0, 0};
   WV_CUDA(cudaMemcpyAsync(v, ps->host->n31, 10 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  if (ps->host->lane)
+    WV_CUDA(cudaMemcpyAsync(t, ps->host->lane_sum, 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
   WV_CUDA(cudaStreamSynchronize(s));
   ps->total = ps->host->lane ? v[9] : v[1];
   ps->split = ps->host->lane ? v[8] : v[2];
+  if (ps->host->lane) ps->terms[0] = (double)t[0], ps->terms[1] = (double)t[1];
   return WV_OK;
 }
 

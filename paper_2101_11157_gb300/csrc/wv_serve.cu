@@ -168,12 +168,58 @@ ResidueConfig query_cfg(const wv_server_s *S, const SQuery *q) {
   return qc;
 }
 
+// Upper bounds on the terms of the n primes ps per kernel, in O(n): with
+// W = the summed widths y - x of the congruences' rows, a prime holds at
+// most W p + rows terms.
+static void congruence_width(const ResidueConfig &cfg, double *w, double *rows);
+static void terms_linear(const uint64_t *ps, size_t n, const ResidueConfig &cfg, double t[2]) {
+  double w = 0, rows = 0, s31 = 0, s64 = 0, n31 = 0, n64 = 0;
+  congruence_width(cfg, &w, &rows);
+  for (size_t i = 0; i < n; ++i) {
+    const uint64_t p = ps[i];
+    if (p < (1ull << 31)) s31 += (double)p, n31 += 1;
+    else s64 += (double)p, n64 += 1;
+  }
+  t[0] = w * s31 + rows * n31;
+  t[1] = w * s64 + rows * n64;
+}
+
+// Upper bounds on the terms of m primes below pmax, per kernel (32-bit for
+// p < 2^31, 64-bit above): a row (x, y) holds at most (y - x) p + 1 terms.
+static void congruence_width(const ResidueConfig &cfg, double *w, double *rows) {
+  *w = 0;
+  *rows = 0;
+  for (int kind = 0; kind < 2; ++kind) {
+    const int id = kind ? cfg.cong_e : cfg.cong_b;
+    if (id < 0) continue;
+    const CongView &c = cong_view(id);
+    for (int j = 0; j < c.nrows; ++j) {
+      const uint32_t *r = cong_row(c.row0 + j);
+      *w += (double)r[2] / r[3] - (double)r[0] / r[1];
+    }
+    *rows += c.nrows;
+  }
+}
+
+static void terms_bound(const ResidueConfig &cfg, uint64_t m, uint64_t pmax, double t[2]) {
+  double w = 0, rows = 0;
+  congruence_width(cfg, &w, &rows);
+  const double lo31 = std::min<double>((double)pmax, 2147483648.0);
+  t[0] = (double)m * (w * lo31 + rows);
+  t[1] = pmax > (1ull << 31) ? (double)m * (w * (double)pmax + rows) : 0.0;
+}
+
 // Device bytes a query of n primes holds while active.
 size_t query_bytes(const wv_server_s *S, const SQuery *q, uint64_t n) {
   const ResidueConfig qc = query_cfg(S, q);
+  const uint64_t pmax = q->kind == 0 ? q->hi : q->lo + 1;
   size_t need = n * 24;
-  for (uint64_t off = 0; off < n; off += kPlanPrimes)
-    need += plan_bytes((uint32_t)std::min<uint64_t>(kPlanPrimes, n - off), qc);
+  for (uint64_t off = 0; off < n; off += kPlanPrimes) {
+    const uint32_t m = (uint32_t)std::min<uint64_t>(kPlanPrimes, n - off);
+    double t[2];
+    terms_bound(qc, m, pmax, t);
+    need += plan_bytes(m, qc, t);
+  }
   return need;
 }
 
@@ -211,14 +257,18 @@ wv_status build_query(wv_server_s *S, SQuery *q, const std::vector<uint32_t> &sl
     c.slot = slots[i];
     q->chunks.push_back(c);
     SChunk &cc = q->chunks.back();
-    WV_CHECK(plan_build(q->d_primes + cc.off, cc.n, qc, &cc.plan, S->sa));
+    // upper bounds on the plan's terms per kernel, O(n): a row holds at most
+    // (y - x) p + 1 terms; the planner's exact counts replace them below
+    double tb[2] = {0, 0};
+    terms_linear(q->h_primes.data() + cc.off, cc.n, qc, tb);
+    WV_CHECK(plan_build(q->d_primes + cc.off, cc.n, qc, &cc.plan, S->sa, tb));
     WV_CHECK(plan_totals(&cc.plan, S->sa));
     Plan *dst = (Plan *)((char *)S->d_plans + (size_t)cc.slot * plan_struct_bytes());
     WV_CHECK(plan_upload(&cc.plan, dst, S->sa));
     cc.hi31 = cc.plan.split;
     cc.hi64 = cc.plan.total;
-    double t31 = 0, t64 = 0;
-    terms_host(q->h_primes.data() + cc.off, cc.n, qc, &t31, &t64);
+    double t31 = cc.plan.terms[0], t64 = cc.plan.terms[1];
+    if (t31 < 0) terms_host(q->h_primes.data() + cc.off, cc.n, qc, &t31, &t64);  // warp tiles
     cc.tpt31 = cc.plan.split ? t31 / cc.plan.split : 1.0;
     cc.tpt64 = (cc.plan.total > cc.plan.split) ? t64 / (cc.plan.total - cc.plan.split) : 1.0;
     q->remaining += t31 + kWideWeight * t64;
@@ -549,7 +599,7 @@ wv_status wv_server_create(const wv_server_config *cfg, wv_server *out) {
   *out = nullptr;
   wv_server_s *S = new wv_server_s();
   if (cfg) S->cfg = *cfg;
-  if (S->cfg.mem_budget == 0) S->cfg.mem_budget = (size_t)16 << 30;
+  if (S->cfg.mem_budget == 0) S->cfg.mem_budget = (size_t)64 << 30;
   if (S->cfg.max_active == 0) S->cfg.max_active = 256;
   if (S->cfg.epoch_terms <= 0) S->cfg.epoch_terms = 4e10;
   int dev = S->cfg.device;
