@@ -50,18 +50,19 @@ IMAD_SLOTS_PER_MODMUL64 = 17
 # run is that busy share scaled by the run's own terms per SM per clock.  Set an entry to None
 # whenever its kernel changes, until it is captured again.
 PIPE_PROFILE = {
-    # k_accumulate<0,1,39,1> (form 39, lane chains): 492 primes of [1062200000, 1062210000),
-    # BB2244 + EE2004, 2.3139e10 terms, 9.892 ms at 2.067 GHz; IMAD pipe 81.34 %, ALU 73.78 % of
-    # elapsed.  Traffic: one launch of the full window (--metrics dram__bytes_read.sum,
-    # dram__bytes_write.sum, the second launch): 10.545 GB read + 0.659 GB written
-    "accumulate_m31": {"imad_pct": 0.8134, "alu_pct": 0.7378, "terms_per_clk_sm": 7.446,
-                       "traffic_bytes": 10545422080 + 659143680,
+    # k_accumulate<0,1,41,1> (form 41, lane chains, piece records): 492 primes of
+    # [1062200000, 1062210000), BB2244 + EE2004, 2.3139e10 terms, 9.566 ms at 2.068 GHz; IMAD pipe
+    # 80.98 %, ALU 76.78 % of elapsed.  Traffic: one launch of the full window (--metrics
+    # dram__bytes_read.sum,dram__bytes_write.sum, the second launch): 1.044 GB read + 0.637 GB written
+    "accumulate_m31": {"imad_pct": 0.8098, "alu_pct": 0.7678, "terms_per_clk_sm": 7.694,
+                       "traffic_bytes": 1044203264 + 637376512,
                        "profile": "profiles/accumulate_m31_p1e9_small.md"},
-    # k_accumulate_m64cap<9,128,1> (lane chains): 17 primes of [1e11 - 1e4, 1e11 - 9500),
-    # BB2244 + EE2004, 7.5269e10 terms, 51.147 ms at 2.069 GHz; IMAD pipe 90.52 %, ALU 58.59 %
-    # Traffic: one launch of the full 391-prime window (second launch): 69.4 MB read + 22.4 MB written
-    "accumulate_m64": {"imad_pct": 0.9052, "alu_pct": 0.5859, "terms_per_clk_sm": 4.678,
-                       "traffic_bytes": 69445632 + 22405120,
+    # k_accumulate_m64cap<9,128,1> (8 cubes / 12 squares, lane chains, piece records): 17 primes
+    # of [1e11 - 1e4, 1e11 - 9500), BB2244 + EE2004, 7.5269e10 terms, 50.112 ms at 2.069 GHz;
+    # IMAD pipe 89.27 %, ALU 58.50 %.  Traffic: one launch of the full 391-prime window: 60.2 MB
+    # read + 12.3 MB written
+    "accumulate_m64": {"imad_pct": 0.8927, "alu_pct": 0.5850, "terms_per_clk_sm": 4.776,
+                       "traffic_bytes": 60184064 + 12273664,
                        "profile": "profiles/accumulate_m64_top_window.md"},
 }
 
@@ -642,7 +643,8 @@ def main():
     ap.add_argument("--max-range", type=int, default=0, help="serve: cap on range length (0: none)")
     ap.add_argument("--epoch-terms", type=float, default=4e10, help="serve: terms per epoch")
     ap.add_argument("--epoch-form", type=int, default=0,
-                    help="serve: 0 persistent per path, 1 persistent over both paths, 2 one warp per tile")
+                    help="serve: 0 default (1), 1 persistent over both paths, 2 one warp per tile, "
+                         "3 persistent per path")
     ap.add_argument("--epoch-block", type=int, default=0, help="serve: epoch block size (0: 32)")
     ap.add_argument("--plain-block", type=int, default=0,
                     help="serve: accumulation block size of the one-query-at-a-time form (0: default)")

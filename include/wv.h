@@ -187,7 +187,7 @@ typedef struct {
                        call with few primes gets more and shorter tiles (up to 64 per
                        sum) so that one launch still holds ~1e5 tiles */
   int blocks_per_sm;/* persistent grid = SMs x this */
-  int arith;        /* hot-loop formulation (default 39).  Every value gives the same
+  int arith;        /* hot-loop formulation (default 41).  Every value gives the same
                        residues; the others exist for ablation.  32-bit path (p < 2^31;
                        signed words below 2^30, unsigned from 2^30 to 2^31):
                        1, 2, 4 single terms (1: shared t p^-1; 2: one wide product and
@@ -197,15 +197,18 @@ typedef struct {
                        group's difference-table additions as ALU-only three-input adds
                        (9 itself: 4 of a Bernoulli group's 9 and 2 of an Euler group's
                        10); 29, 30, 31 groups of 3 cubes, of 4 squares, or both; 39
-                       (default) groups of 4 cubes / 5 squares.  64-bit
+                       groups of 4 cubes / 5 squares; 40, 41 (default), 44 (lane chains
+                       only; 39 with warp tiles) groups of 5 cubes / 6 squares, 4 cubes /
+                       6 squares, 4 cubes / 7 squares.  64-bit
                        path (2^31 <= p < 2^37): 1, 2, 4 the single-term 64-bit kernel;
                        12..18 and 21 other group sizes, shrink intervals and register
                        budgets; 32..36 the default with a quarter to all of its 64-bit
                        table additions as PTX carry chains (32: plain; 33..36: with a
                        three-input high word); 37 the default with the earlier, longer
                        shrink of its difference tables; 38 the default with its
-                       per-chain set-up unrolled; every other value the grouped default
-                       (8 cubes / 10 squares).  23: the paper's own arithmetic on both
+                       per-chain set-up unrolled; 42, 43 (lane chains only) the default
+                       with Euler groups of 10 or 11 squares; every other value the grouped
+                       default (8 cubes / 12 squares).  23: the paper's own arithmetic on both
                        paths (plain residues, eqn 3.15 split products, remainders from
                        a double-precision quotient, single terms).  Other values:
                        WV_EINVAL */
@@ -217,8 +220,8 @@ typedef struct {
   int tiling;       /* work unit of the accumulation.  0 (default) or 2: lane chains --
                        every lane of a warp sums its own piece of one (prime, sum), the
                        pieces sorted by length so that a warp's lanes finish together;
-                       used with the grouped formulations 39 (default) and 31 and ILP 1 or
-                       2, warp tiles otherwise.  1: warp tiles -- the 32 lanes of a warp split one piece
+                       used with the grouped formulations 41 (default), 31, 39, 40 and
+                       42..44 and ILP 1 or 2, warp tiles otherwise.  1: warp tiles -- the 32 lanes of a warp split one piece
                        and merge by shuffles (the earlier work unit, kept for ablation).
                        Other values: WV_EINVAL */
   int reserved[6];

@@ -31,9 +31,10 @@ typedef struct {
   uint32_t max_active;   /* queries admitted at once (0: 256)                        */
   double epoch_terms;    /* summed terms per epoch, bounds its duration (0: 4e10)    */
   int device;            /* CUDA device (-1: current device at creation)              */
-  int epoch_form;        /* epoch launch: 0 one persistent launch per arithmetic path
-                            (default), 1 one persistent launch over both paths,
-                            2 one warp per tile (non-persistent, both paths)          */
+  int epoch_form;        /* epoch launch: 0 or 1 one persistent launch over both
+                            arithmetic paths (default), 2 one warp per tile
+                            (non-persistent, both paths), 3 one persistent launch
+                            per arithmetic path                                       */
   int epoch_block;       /* threads per block of an epoch launch, 32..256 (0: 32)     */
   int reserved[5];
 } wv_server_config;

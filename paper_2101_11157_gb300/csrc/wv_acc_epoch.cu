@@ -9,10 +9,10 @@ namespace wv {
 EpochKernel epoch_kernel(bool wide, int ilp, bool lane) {
   if (lane) {
     if (wide) return k_epoch<true, 1, 9, true>;
-    return ilp == 1 ? k_epoch<false, 1, 39, true> : k_epoch<false, 2, 39, true>;
+    return ilp == 1 ? k_epoch<false, 1, 41, true> : k_epoch<false, 2, 41, true>;
   }
   if (wide) return k_epoch<true, 1, 9>;
-  return ilp == 1 ? k_epoch<false, 1, 39> : k_epoch<false, 2, 39>;
+  return ilp == 1 ? k_epoch<false, 1, 41> : k_epoch<false, 2, 41>;
 }
 
 }  // namespace wv

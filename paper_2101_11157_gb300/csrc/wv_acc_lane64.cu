@@ -5,6 +5,9 @@
 
 namespace wv {
 
-AccKernel acc_kernel_lane64() { return k_accumulate_m64cap<9, kM64MaxReg, true>; }
+AccKernel acc_kernel_lane64(int arith) {
+  if (arith == 42 || arith == 43) return acc_kernel_lane64x(arith);
+  return k_accumulate_m64cap<9, kM64MaxReg, true>;
+}
 
 }  // namespace wv

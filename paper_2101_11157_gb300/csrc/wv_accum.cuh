@@ -53,19 +53,28 @@ struct Plan {
   uint32_t gen_e_b, gen_e_e;
   uint32_t glhs[3];
   // lane chains (lane != 0): a tile is one lane's piece of a segment, and a
-  // warp runs 32 of them.  perm lists the tiles by class (32-bit signed /
+  // warp runs 32 of them.  rec lists the pieces by class (32-bit signed /
   // unsigned / 64-bit path, B / E) and, inside a class, by rising length,
-  // each class padded to whole warps with kNoChain; lane_w = {warps of the
-  // 32-bit kernel, all warps}.  Chains per segment come from the path's chain
-  // length (lane_len: terms at most per chain, from lane_sum = terms per path
-  // and the targets below).
+  // each class padded to whole warps; lane_w = {warps of the 32-bit kernel,
+  // all warps}.  Pieces per segment come from the path's chain length
+  // (terms at most per piece: from lane_sum = terms per path and the
+  // targets below, or fixed by the host in lane_fix).
   uint32_t lane;
-  uint32_t *perm, *chain_key, *chain_hist, *lane_w;
-  uint64_t *lane_sum, *lane_len;
+  struct PieceRec *rec;  // the sorted pieces (padding: tile = kNoChain)
+  uint32_t *chain_key, *chain_hist, *lane_w;
+  uint64_t *lane_sum;
   uint64_t lane_target[2], lane_min[2];  // chains wanted per path, shortest chain length
   uint64_t lane_fix[2];  // nonzero: the chain length per path, fixed by the host
 };
 constexpr uint32_t kNoChain = 0xffffffffu;
+// One lane chain as the planner lists it, in sorted order, so that a warp's
+// 32 lanes read their pieces with one coalesced load: the first term s, the
+// number of terms, the tile (the slot of its partial), the prime's slot and
+// the row (B rows first).
+struct PieceRec {
+  uint64_t start;
+  uint32_t n, tile, slot, row;
+};
 
 // ------------------------------------------------------------------ tiles
 // Warp-level merge of the per-lane pairs (eqn 3.14) through shuffles.
@@ -556,7 +565,8 @@ __device__ __forceinline__ void tile_m64(const PrimeCtx &ctx, uint64_t start, ui
 // c < p + 2^31 and g < 2^57 every intermediate fits its word and the result
 // is below p + 2^31 (one conditional subtraction makes it canonical).
 //
-// The grouped scheme of the 32-bit path is used with larger groups here: the
+// The grouped scheme of the 32-bit path is used with larger groups here (8
+// cubes, 12 squares): the
 // group polynomials G0, G1 are stepped with plain 64-bit additions and no
 // reduction, and every BLK groups the tables are brought back below 6 p by an
 // approximate Barrett step (quotient from the high word times floor(2^62 / p),
@@ -633,7 +643,7 @@ __device__ __forceinline__ uint64_t m64_shrink_q(uint64_t v, const M64K &K, uint
 
 // group sizes, shrink interval and flags of each 64-bit formulation (arith)
 template <int AR> struct M64Form {  // 9: the default
-  static constexpr int KB = 8, KE = 10, BLK = 16, V = 16 | 32;
+  static constexpr int KB = 8, KE = 12, BLK = 16, V = 16 | 32;
 };
 // 32..36: form 9 with its 64-bit table additions written as PTX carry chains
 // (add.cc / addc on the two words) for a share of the entries, in quarters
@@ -694,6 +704,11 @@ template <> struct M64Form<17> { static constexpr int KB = 7, KE = 9, BLK = 16, 
 constexpr int kM64MaxReg = 128;
 template <> struct M64Form<18> : M64Form<9> {};
 template <> struct M64Form<21> { static constexpr int KB = 9, KE = 11, BLK = 16, V = 16 | 32; };
+// 42, 43: form 9 with smaller Euler groups, 10 squares (the default until
+// lane chains) and 11; the default's 12 squares step tables of degree 24 and
+// 22, no more registers than the 8-cube tables
+template <> struct M64Form<42> { static constexpr int KB = 8, KE = 10, BLK = 16, V = 16 | 32; };
+template <> struct M64Form<43> { static constexpr int KB = 8, KE = 11, BLK = 16, V = 16 | 32; };
 
 // a b 2^-64 mod p, below p + 2^12 for a, b < 2^38
 __device__ __forceinline__ uint64_t m64_mm(uint64_t a, uint64_t b, const M64K &K) {
@@ -1069,27 +1084,46 @@ template <> struct M31Form<29> { static constexpr int KC = 3, KS = 0, NFC = 6, N
 template <> struct M31Form<30> { static constexpr int KC = 0, KS = 4, NFC = 4, NFS = 4; };
 template <> struct M31Form<31> { static constexpr int KC = 3, KS = 4, NFC = 6, NFS = 4; };
 template <> struct M31Form<39> { static constexpr int KC = 4, KS = 5, NFC = 6, NFS = 4; };
+// 40, 41, 44: larger groups still, for lane chains (every chain long): 5
+// cubes / 6 squares (27 and 22 additions, 8 and 5 ALU-only), 4 cubes / 6
+// squares (41, the default with lane chains), 4 cubes / 7 squares
+template <> struct M31Form<40> { static constexpr int KC = 5, KS = 6, NFC = 8, NFS = 5; };
+template <> struct M31Form<41> { static constexpr int KC = 4, KS = 6, NFC = 6, NFS = 5; };
+template <> struct M31Form<44> { static constexpr int KC = 4, KS = 7, NFC = 6, NFS = 6; };
 
 template <bool WIDE, int ILP, int AR, bool LANE = false>
 __device__ __forceinline__ void process_tile(const Plan &P, uint32_t g) {
   const int lane = threadIdx.x & 31;
   bool live = true;
+  uint32_t slot, j;
+  uint64_t start, n;
   if constexpr (LANE) {
-    // g is a warp of lane chains: this lane's tile from the sorted list; a
-    // padding lane repeats lane 0's tile (same code path, nothing stored)
-    uint32_t t = __ldg(&P.perm[32 * (size_t)g + lane]);
-    const uint32_t t0 = __shfl_sync(0xffffffffu, t, 0);
+    // g is a warp of lane chains: this lane's piece from the sorted list; a
+    // padding lane repeats lane 0's piece (same code path, nothing stored)
+    const PieceRec *rp = P.rec + 32 * (size_t)g + lane;
+    uint64_t st = __ldg(&rp->start);
+    uint32_t nn = __ldg(&rp->n), t = __ldg(&rp->tile), sl = __ldg(&rp->slot), rw = __ldg(&rp->row);
     live = t != kNoChain;
+    const uint64_t st0 = __shfl_sync(0xffffffffu, st, 0);
+    const uint32_t nn0 = __shfl_sync(0xffffffffu, nn, 0), t0 = __shfl_sync(0xffffffffu, t, 0);
+    const uint32_t sl0 = __shfl_sync(0xffffffffu, sl, 0), rw0 = __shfl_sync(0xffffffffu, rw, 0);
     g = live ? t : t0;
+    start = live ? st : st0;
+    n = live ? nn : nn0;
+    slot = live ? sl : sl0;
+    j = live ? rw : rw0;
+  } else {
+    // segment owning tile g (the planner's tile -> segment map)
+    const uint32_t s = __ldg(&P.tile_seg[g]);
+    slot = s / P.rows_pp;
+    j = s - slot * P.rows_pp;
+    const uint32_t k = g - P.seg_first[s], T = P.seg_tiles[s];
+    const uint64_t cnt = P.seg_cnt[s];
+    const uint64_t b0 = cnt * k / T, b1 = cnt * (k + 1) / T;
+    start = P.seg_lo[s] + b0;
+    n = b1 - b0;
   }
-  // segment owning tile g (the planner's tile -> segment map)
-  const uint32_t s = __ldg(&P.tile_seg[g]);
-  const uint32_t slot = s / P.rows_pp, j = s - slot * P.rows_pp;
   const PrimeCtx ctx = P.ctx[slot];
-  const uint32_t k = g - P.seg_first[s], T = P.seg_tiles[s];
-  const uint64_t cnt = P.seg_cnt[s];
-  const uint64_t b0 = cnt * k / T, b1 = cnt * (k + 1) / T;
-  const uint64_t start = P.seg_lo[s] + b0, n = b1 - b0;
   int64_t r0, r1;
   // single-term form used beside the grouped one
   constexpr int AS = (AR == 5 || AR >= 8) ? 4 : AR;
@@ -1224,7 +1258,7 @@ __global__ void __maxnreg__(kM64MaxReg)
     const EpochItem it = items[lo];
     const uint32_t tile = it.first + it.count - 1 - (g - it.prefix);
     if (it.plan >> 31) process_tile<true, I64, 9, LANE>(plans[it.plan & 0x7fffffffu], tile);
-    else process_tile<false, I31, 39, LANE>(plans[it.plan], tile);
+    else process_tile<false, I31, 41, LANE>(plans[it.plan], tile);
   }
 }
 
@@ -1245,7 +1279,7 @@ __global__ void __maxnreg__(kM64MaxReg)
   const EpochItem it = items[lo];
   const uint32_t tile = it.first + it.count - 1 - (g - it.prefix);
   if (it.plan >> 31) process_tile<true, I64, 9, LANE>(plans[it.plan & 0x7fffffffu], tile);
-  else process_tile<false, I31, 39, LANE>(plans[it.plan], tile);
+  else process_tile<false, I31, 41, LANE>(plans[it.plan], tile);
 }
 
 // ------------------------------------------------------------------ getters
@@ -1269,7 +1303,11 @@ AccKernel acc_kernel_m31x(int arith, int ilp);
 // lane chains: the 32-bit grouped formulations 39 (default) and 31, ILP 1 or
 // 2, and the 64-bit grouped default (one chain per thread)
 AccKernel acc_kernel_lane31(int arith, int ilp);
-AccKernel acc_kernel_lane64();
+AccKernel acc_kernel_lane64(int arith);
+// lane-chain forms 40, 41 (the default), 44 (32-bit groups) and 42, 43
+// (64-bit groups)
+AccKernel acc_kernel_lane31x(int arith, int ilp);
+AccKernel acc_kernel_lane64x(int arith);
 AccKernel acc_kernel_m31y(int arith, int ilp);  // form 39 (x falls through to y)
 // serving-loop epoch kernels (the default formulations: 31 on the 32-bit path,
 // 9 with one chain per thread on the 64-bit path)

@@ -163,11 +163,11 @@ constexpr uint32_t kChainBins = 2048;  // length bins per class
 // shortest chain lengths (the 64-bit path's set-up costs about 40 groups)
 constexpr uint64_t kLaneThreads31 = 768, kLaneThreads64 = 512;
 constexpr uint64_t kLaneRounds = 16, kLaneRoundsEpoch = 4;
-// a serving plan's chains are at most kLaneMaxEpoch terms long, so that an
-// epoch is never held up by one long chain (about 2 ms of one lane on the
-// 32-bit kernel, 3.5 ms on the 64-bit one) and the shortest epochs still
-// hold enough warps to fill the GPU
-constexpr uint64_t kLaneMaxEpoch = 1ull << 15;
+// a serving plan's chains are at most kLaneMaxEpoch[path] terms long, so that
+// an epoch is never held up by one long chain (about 4 ms of one lane on the
+// 32-bit kernel, 7 ms on the 64-bit one, whose per-chain set-up is costlier)
+// and the shortest epochs still hold enough warps to fill the GPU
+constexpr uint64_t kLaneMaxEpoch[2] = {1ull << 16, 1ull << 16};
 constexpr uint64_t kLaneMin31 = 4096, kLaneMin64 = 16384;
 
 __global__ void k_lane_sum(Plan P) {  // terms per path: one atomic per block and path
@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(kOffThreads) k_chain_offsets(Plan P) {
     __syncthreads();
     if (t == 0) {
       const uint32_t end = base + sh[kOffThreads - 1], padded = (end + 31u) & ~31u;
-      for (uint32_t x = end; x < padded; ++x) P.perm[x] = kNoChain;
+      for (uint32_t x = end; x < padded; ++x) P.rec[x].tile = kNoChain;
       base = padded;
       if (c == 3) P.lane_w[0] = padded / 32;
       if (c == kChainClasses - 1) P.lane_w[1] = padded / 32;
@@ -317,11 +317,18 @@ __global__ void k_chain_scatter(Plan P) {
     uint32_t pos = 0;
     if (T == 1 && lane == leader) pos = atomicAdd(&P.chain_hist[key], (uint32_t)__popc(peers));
     pos = __shfl_sync(0xffffffffu, pos, (int)leader);
-    if (T == 1) {
-      P.perm[pos + __popc(peers & ((1u << lane) - 1u))] = P.seg_first[s];
-    } else if (T > 1) {
-      const uint32_t f = P.seg_first[s], at = atomicAdd(&P.chain_hist[key], T);
-      for (uint32_t k = 0; k < T; ++k) P.perm[at + k] = f + k;
+    if (T) {
+      const uint32_t slot = s / P.rows_pp, row = s - slot * P.rows_pp, f = P.seg_first[s];
+      const uint64_t lo = P.seg_lo[s], cnt = P.seg_cnt[s];
+      if (T == 1) {
+        P.rec[pos + __popc(peers & ((1u << lane) - 1u))] = PieceRec{lo, (uint32_t)cnt, f, slot, row};
+      } else {
+        const uint32_t at = atomicAdd(&P.chain_hist[key], T);
+        for (uint32_t k = 0; k < T; ++k) {
+          const uint64_t b0 = cnt * k / T, b1 = cnt * (k + 1) / T;
+          P.rec[at + k] = PieceRec{lo + b0, (uint32_t)(b1 - b0), f + k, slot, row};
+        }
+      }
     }
   }
 }
@@ -344,7 +351,7 @@ static void epoch_chain_lengths(const double *t, int sms, uint64_t *L, size_t *e
   *extra_tiles = 0;
   for (int i = 0; i < 2; ++i) {
     const double want = t[i] / (double)(kLaneRoundsEpoch * lanes[i]);
-    uint64_t l = want > (double)kLaneMaxEpoch ? kLaneMaxEpoch : (uint64_t)want + 1;
+    uint64_t l = want > (double)kLaneMaxEpoch[i] ? kLaneMaxEpoch[i] : (uint64_t)want + 1;
     L[i] = l < lmin[i] ? lmin[i] : l;
     *extra_tiles += (size_t)(t[i] / (double)L[i]) + 1;
   }
@@ -356,7 +363,7 @@ template <typename Get>
 static wv_status lane_setup(Plan &P, size_t tiles_cap, uint32_t *scal, int sms, uint64_t rounds,
                             Get get) {
   P.lane = 1;
-  WV_CHECK(get((void **)&P.perm, (tiles_cap + 32 * kChainClasses) * sizeof(uint32_t)));
+  WV_CHECK(get((void **)&P.rec, (tiles_cap + 32 * kChainClasses) * sizeof(PieceRec)));
   WV_CHECK(get((void **)&P.chain_key, tiles_cap * sizeof(uint32_t)));
   WV_CHECK(get((void **)&P.chain_hist, (size_t)kChainClasses * kChainBins * sizeof(uint32_t)));
   WV_CHECK(get((void **)&P.lane_sum, 2 * sizeof(uint64_t)));
@@ -379,7 +386,9 @@ static wv_status plan_launches(Plan &P, uint32_t *u32tmp, int sms, cudaStream_t 
     WV_LAUNCH("lane_chains", k_lane_chains, (unsigned)((ns + 255) / 256), 256, 0, s, P);
   }
   WV_CHECK(scan_exclusive_u32(P.seg_tiles, P.seg_first, ns, P.total_tiles, u32tmp, s));
-  WV_LAUNCH("plan_tilemap", k_plan_tilemap, (unsigned)((ns + 255) / 256), 256, 0, s, P);
+  // the tile -> segment map serves warp tiles; lane chains read piece records
+  if (!P.lane)
+    WV_LAUNCH("plan_tilemap", k_plan_tilemap, (unsigned)((ns + 255) / 256), 256, 0, s, P);
   WV_LAUNCH("plan_split", k_plan_split, 1, 1, 0, s, P);
   if (P.lane) {
     const unsigned gs = (unsigned)(sms * 8);
@@ -550,7 +559,7 @@ static wv_status launch_accumulate(const Plan &P, const ResidueConfig &cfg, int 
   const char *name = WIDE ? "accumulate_m64" : "accumulate_m31";
   AccKernel kern = nullptr;
   if (P.lane) {
-    kern = WIDE ? acc_kernel_lane64() : acc_kernel_lane31(cfg.arith, cfg.ilp);
+    kern = WIDE ? acc_kernel_lane64(cfg.arith) : acc_kernel_lane31(cfg.arith, cfg.ilp);
   } else if (WIDE) {
     // arith 25..28 vary the 32-bit path only; the 64-bit path runs its default
     // the single-term forms (1, 2, 4) run the single-term 64-bit kernel, 12..18,

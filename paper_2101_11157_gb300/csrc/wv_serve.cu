@@ -421,10 +421,10 @@ wv_status launch_epoch(wv_server_s *S, int b, const std::vector<EpochItem> &item
                        EpochItem *d, uint32_t tot, cudaStream_t es) {
   const int form = S->cfg.epoch_form;
   if (form == 2) return epoch_launch_tiles(d, (uint32_t)items.size(), tot, S->d_plans, S->rcfg, es);
-  if (form == 1)
+  if (form <= 1)  // the default: one launch (and one tail) per epoch
     return epoch_launch_mixed(d, (uint32_t)items.size(), tot, S->d_plans, S->d_counter + 2 * b,
                               S->rcfg, S->sms, kReserveBlocks, es);
-  // form 0: the items of each path as their own list (h is pinned host memory
+  // form 3: the items of each path as their own list (h is pinned host memory
   // of 2 kMaxPlans items; the 32-bit items first, then the 64-bit ones)
   uint32_t n31 = 0, t31 = 0, t64 = 0;
   for (const EpochItem &it : items)
@@ -621,7 +621,7 @@ wv_status wv_server_create(const wv_server_config *cfg, wv_server *out) {
     // frees its registers at once for the next epoch, not after its block
     S->rcfg.block = S->cfg.epoch_block > 0 ? S->cfg.epoch_block : kEpochBlock;
     if (S->rcfg.block % 32 || S->rcfg.block > 256) st = set_error(WV_EINVAL, "epoch_block must be 32..256, a multiple of 32");
-    if (S->cfg.epoch_form < 0 || S->cfg.epoch_form > 2) st = set_error(WV_EINVAL, "epoch_form must be 0, 1 or 2");
+    if (S->cfg.epoch_form < 0 || S->cfg.epoch_form > 3) st = set_error(WV_EINVAL, "epoch_form must be 0..3");
     int lo_prio = 0, hi_prio = 0;
     cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
     // admission and finalisation go first whenever SMs free up

@@ -104,3 +104,35 @@ def test_top_window_formulations_equal_oracle(opt):
         cb, ce = wv.wv_congruence_for_range(*W.TOP_WINDOW)
         rb, re = _residues(gp, {**(opt or {}), "cong_b": cb, "cong_e": ce})
         assert np.array_equal(rb, gb) and np.array_equal(re, ge)
+
+
+@pytest.mark.parametrize("opt", [None, {"arith": 40}, {"arith": 41}, {"arith": 31, "ilp": 2},
+                                 {"tiling": 1}, {"tiling": 1, "arith": 31, "ilp": 2}])
+def test_p1e9_window_work_units_equal_oracle(opt):
+    """The window under lane chains (the default: each lane sums its own piece
+    of a sum, pieces sorted by length) with the lane formulations, and under
+    warp tiles, against the stored oracle residues."""
+    gp, gb, ge = _gold("p1e9_window_residues.txt")
+    cb, ce = wv.wv_congruence_for_range(*W.P1E9_WINDOW)
+    rb, re = _residues(gp, {**(opt or {}), "cong_b": cb, "cong_e": ce})
+    assert np.array_equal(rb, gb) and np.array_equal(re, ge)
+
+
+@pytest.mark.parametrize("opt", [None, {"arith": 42}, {"arith": 43}, {"tiling": 1}])
+def test_lane_chains_few_primes_equal_oracle(opt):
+    """Lists of 1 to 8 stored primes below 1e11 and the first 33 of the window at
+    1.06e9: most lanes of the last warp of a class are padding, the sums split
+    into many pieces (few primes, many lanes), and the paths mix."""
+    tp, tb, te = _gold("top_window_subset_residues.txt")
+    wp, wb, we = _gold("p1e9_window_residues.txt")
+    cb, ce = wv.wv_congruence_for_range(*W.TOP_WINDOW)
+    for k in (1, 2, 5, 8):
+        rb, re = _residues(tp[:k], {**(opt or {}), "cong_b": cb, "cong_e": ce})
+        assert np.array_equal(rb, tb[:k]) and np.array_equal(re, te[:k]), k
+    for k in (1, 31, 32, 33):
+        rb, re = _residues(wp[:k], {**(opt or {}), "cong_b": cb, "cong_e": ce})
+        assert np.array_equal(rb, wb[:k]) and np.array_equal(re, we[:k]), k
+    mix = np.concatenate([wp[:33], tp[:3]])
+    rb, re = _residues(mix, opt)
+    assert np.array_equal(rb, np.concatenate([wb[:33], tb[:3]]))
+    assert np.array_equal(re, np.concatenate([we[:33], te[:3]]))
