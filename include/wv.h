@@ -187,7 +187,7 @@ typedef struct {
                        call with few primes gets more and shorter tiles (up to 64 per
                        sum) so that one launch still holds ~1e5 tiles */
   int blocks_per_sm;/* persistent grid = SMs x this */
-  int arith;        /* hot-loop formulation (default 41).  Every value gives the same
+  int arith;        /* hot-loop formulation (default 48).  Every value gives the same
                        residues; the others exist for ablation.  32-bit path (p < 2^31;
                        signed words below 2^30, unsigned from 2^30 to 2^31):
                        1, 2, 4 single terms (1: shared t p^-1; 2: one wide product and
@@ -197,9 +197,12 @@ typedef struct {
                        group's difference-table additions as ALU-only three-input adds
                        (9 itself: 4 of a Bernoulli group's 9 and 2 of an Euler group's
                        10); 29, 30, 31 groups of 3 cubes, of 4 squares, or both; 39
-                       groups of 4 cubes / 5 squares; 40, 41 (default), 44 (lane chains
-                       only; 39 with warp tiles) groups of 5 cubes / 6 squares, 4 cubes /
-                       6 squares, 4 cubes / 7 squares.  64-bit
+                       groups of 4 cubes / 5 squares; lane chains only (39 with warp
+                       tiles): 40, 41, 44 groups of 5 cubes / 6 squares, 4 / 6, 4 / 7;
+                       45, 46, 47 the u form (G0 = u^e from a table of u = prod (s+i),
+                       K + e(K-1) table additions per group instead of 2eK - e) with
+                       groups of 8 / 10, 6 / 8, 10 / 12; 48 (default) per warp 45 on
+                       pieces of at least 6144 terms and 41 on shorter ones.  64-bit
                        path (2^31 <= p < 2^37): 1, 2, 4 the single-term 64-bit kernel;
                        12..18 and 21 other group sizes, shrink intervals and register
                        budgets; 32..36 the default with a quarter to all of its 64-bit
@@ -220,8 +223,8 @@ typedef struct {
   int tiling;       /* work unit of the accumulation.  0 (default) or 2: lane chains --
                        every lane of a warp sums its own piece of one (prime, sum), the
                        pieces sorted by length so that a warp's lanes finish together;
-                       used with the grouped formulations 41 (default), 31, 39, 40 and
-                       42..44 and ILP 1 or 2, warp tiles otherwise.  1: warp tiles -- the 32 lanes of a warp split one piece
+                       used with the grouped formulations 48 (default), 31 and 39..47
+                       and ILP 1 or 2, warp tiles otherwise.  1: warp tiles -- the 32 lanes of a warp split one piece
                        and merge by shuffles (the earlier work unit, kept for ablation).
                        Other values: WV_EINVAL */
   int reserved[6];

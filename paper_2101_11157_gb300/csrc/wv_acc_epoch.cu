@@ -9,10 +9,10 @@ namespace wv {
 EpochKernel epoch_kernel(bool wide, int ilp, bool lane) {
   if (lane) {
     if (wide) return k_epoch<true, 1, 9, true>;
-    return ilp == 1 ? k_epoch<false, 1, 41, true> : k_epoch<false, 2, 41, true>;
+    return ilp == 1 ? k_epoch<false, 1, 48, true> : k_epoch<false, 2, 48, true>;
   }
   if (wide) return k_epoch<true, 1, 9>;
-  return ilp == 1 ? k_epoch<false, 1, 41> : k_epoch<false, 2, 41>;
+  return ilp == 1 ? k_epoch<false, 1, 48> : k_epoch<false, 2, 48>;
 }
 
 }  // namespace wv

@@ -5,7 +5,7 @@
 namespace wv {
 
 AccKernel acc_kernel_lane31(int arith, int ilp) {
-  if (arith == 40 || arith == 44) return acc_kernel_lane31x(arith, ilp);
+  if (arith == 40 || arith >= 44) return acc_kernel_lane31x(arith, ilp);  // 48 (default) too
   if (arith == 39) return ilp == 1 ? k_accumulate<false, 1, 39, true> : k_accumulate<false, 2, 39, true>;
   if (arith >= 41) return ilp == 1 ? k_accumulate<false, 1, 41, true> : k_accumulate<false, 2, 41, true>;
   return ilp == 1 ? k_accumulate<false, 1, 31, true> : k_accumulate<false, 2, 31, true>;

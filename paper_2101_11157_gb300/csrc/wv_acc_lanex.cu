@@ -7,7 +7,8 @@ namespace wv {
 
 AccKernel acc_kernel_lane31x(int arith, int ilp) {
   if (arith == 40) return ilp == 1 ? k_accumulate<false, 1, 40, true> : k_accumulate<false, 2, 40, true>;
-  return ilp == 1 ? k_accumulate<false, 1, 44, true> : k_accumulate<false, 2, 44, true>;
+  if (arith == 44) return ilp == 1 ? k_accumulate<false, 1, 44, true> : k_accumulate<false, 2, 44, true>;
+  return acc_kernel_lane31u(arith, ilp);
 }
 
 AccKernel acc_kernel_lane64x(int arith) {

@@ -273,7 +273,8 @@ template <> struct SetOf<true> { using T = U31Set; };
 // plain C; the compiler may place their two-input adds on the multiply pipe,
 // which the products already fill.  NF moves work from that pipe to the ALU.
 
-template <int ILP, bool CUBES, int AR, int NF = 0, int KG = 0, bool U = false, bool LANE = false>
+template <int ILP, bool CUBES, int AR, int NF = 0, int KG = 0, bool U = false, bool LANE = false,
+          bool UF = false>
 __device__ __forceinline__ void tile_m31_grouped(const PrimeCtx &ctx, uint64_t start, uint64_t n,
                                                  int64_t &r0, int64_t &r1) {
   // U: the unsigned form for 2^30 <= p < 2^31 (U31Set), run by the same
@@ -285,6 +286,10 @@ __device__ __forceinline__ void tile_m31_grouped(const PrimeCtx &ctx, uint64_t s
   constexpr int EX = CUBES ? 3 : 2;    // t = s^EX
   constexpr int DA = K * EX;           // degree of G0
   constexpr int DB = (K - 1) * EX;     // degree of G1
+  // UF: G0 = u^EX with u = prod_{i<K} (s+i), so the first table is u's, of
+  // degree K, and each group forms G0 with EX - 1 products from it
+  constexpr int DT = UF ? K : DA;            // degree of the first table
+  constexpr int DTOP = DT > DB ? DT : DB;    // points of the set-up: 0 .. DTOP
   const int lane = threadIdx.x & 31;
   const Mont M(ctx);
   const int32_t p = (int32_t)ctx.p;
@@ -296,7 +301,7 @@ __device__ __forceinline__ void tile_m31_grouped(const PrimeCtx &ctx, uint64_t s
   const uint64_t len = n / nch;
   const uint32_t rem = (uint32_t)(n - len * nch);
   const uint64_t G = len / K;  // groups per chain, the same for every lane
-  int32_t c0[ILP], c1[ILP], ga[ILP][DA + 1], gb[ILP][DB + 1];
+  int32_t c0[ILP], c1[ILP], ga[ILP][DT + 1], gb[ILP][DB + 1];
   uint64_t s_tail[ILP];
   uint32_t n_tail[ILP];
 #pragma unroll
@@ -317,7 +322,7 @@ __device__ __forceinline__ void tile_m31_grouped(const PrimeCtx &ctx, uint64_t s
       // 32-bit residues in [0, p) throughout (p < 2^31); s < p, so the top
       // point needs at most one subtraction of p
       // 32-bit residues in [0, p) (S: the chain's Montgomery set, above)
-      uint64_t x64 = s + (uint64_t)(K * (DA + 1) - 1);
+      uint64_t x64 = s + (uint64_t)(K * (DTOP + 1) - 1);
       x64 = x64 >= ctx.p ? (x64 >= 2 * ctx.p ? x64 % ctx.p : x64 - ctx.p) : x64;
       const uint32_t xr = (uint32_t)x64;
       const uint32_t sq = S.mulmod(xr, xr);
@@ -332,38 +337,45 @@ __device__ __forceinline__ void tile_m31_grouped(const PrimeCtx &ctx, uint64_t s
         d1 = S.sub(x2, S.c1);
         d2 = S.c2;
       }
-      uint32_t va[DA + 1], vb[DB + 1];
+      uint32_t va[DT + 1], vb[DB + 1];
+      uint32_t xc = xr;  // the plain x of the current term (UF: u's factors)
 #pragma unroll
-      for (int i = 0; i <= DA; ++i) va[i] = 0;
+      for (int i = 0; i <= DT; ++i) va[i] = 0;
 #pragma unroll
       for (int i = 0; i <= DB; ++i) vb[i] = 0;
       // the point loop stays rolled (it runs once per chain; unrolled it is
       // kilobytes of code that short tiles fetch again and again); the table
       // indices stay compile-time, the diagonal lengths are predicated
 #pragma unroll 1
-      for (int m = DA; m >= 0; --m) {
-        uint32_t P = 0, Q = S.one;
+      for (int m = DTOP; m >= 0; --m) {
+        uint32_t P = 0, Q = S.one, Pu = 0;
 #pragma unroll
         for (int i = 0; i < K; ++i) {
           if (i == 0) {
             P = t;
+            if (UF) Pu = xc;
           } else {
             Q = S.add(S.mul(Q, t), P);
             P = S.mul(P, t);
+            if (UF) Pu = S.mul(Pu, xc);
           }
           t = S.sub(t, d1);
           d1 = S.sub(d1, d2);
           if (EX == 3) d2 = S.sub(d2, S.c6);
+          if (UF) xc = S.sub(xc, S.c1);
         }
-        uint32_t nv = P;
+        if (m <= DT) {
+          uint32_t nv = UF ? Pu : P;
 #pragma unroll
-        for (int j = 0; j <= DA; ++j) {
-          if (j <= DA - m) {
-            const uint32_t old = va[j];
-            va[j] = nv;
-            nv = S.sub(nv, old);
+          for (int j = 0; j <= DT; ++j) {
+            if (j <= DT - m) {
+              const uint32_t old = va[j];
+              va[j] = nv;
+              nv = S.sub(nv, old);
+            }
           }
         }
+        uint32_t nv;
         if (m <= DB) {
           nv = Q;
 #pragma unroll
@@ -377,7 +389,7 @@ __device__ __forceinline__ void tile_m31_grouped(const PrimeCtx &ctx, uint64_t s
         }
       }
 #pragma unroll
-      for (int j = 0; j <= DA; ++j) ga[k][j] = (int32_t)((j & 1) ? S.sub(0, va[j]) : va[j]);
+      for (int j = 0; j <= DT; ++j) ga[k][j] = (int32_t)((j & 1) ? S.sub(0, va[j]) : va[j]);
 #pragma unroll
       for (int j = 0; j <= DB; ++j) gb[k][j] = (int32_t)((j & 1) ? S.sub(0, vb[j]) : vb[j]);
     }
@@ -408,7 +420,28 @@ __device__ __forceinline__ void tile_m31_grouped(const PrimeCtx &ctx, uint64_t s
   for (uint32_t g = 0; g < G32; ++g) {
 #pragma unroll
     for (int k = 0; k < ILP; ++k) {
-      const int32_t A = ga[k][0], B = gb[k][0];
+      int32_t A;
+      if constexpr (UF && U) {
+        // G0 = u^EX from the u table's value, canonical
+        const uint32_t Uv = (uint32_t)ga[k][0], U2 = S.mul(Uv, Uv);
+        A = (int32_t)(EX == 3 ? S.mul(U2, Uv) : U2);
+      } else if constexpr (UF) {
+        // the same on signed words, REDC folded into a wide multiply-add: from
+        // u in [0, p) the square lies in (-3p/4, 3p/4) and the cube in (-p, p),
+        // inside the accumulator's operand range
+        const int32_t Uv = ga[k][0];
+        const int64_t w2 = mul_wide(Uv, Uv);
+        const int32_t U2 = hi32(mad_wide((int32_t)((uint32_t)lo32(w2) * q), np, w2));
+        if (EX == 3) {
+          const int64_t w3 = mul_wide(U2, Uv);
+          A = hi32(mad_wide((int32_t)((uint32_t)lo32(w3) * q), np, w3));
+        } else {
+          A = U2;
+        }
+      } else {
+        A = ga[k][0];
+      }
+      const int32_t B = gb[k][0];
       if constexpr (U) {
         // the same with unsigned words: c0 G0 and c1 G0 + c0 G1 stay below
         // 2 p^2 < 2^63, and one subtraction makes each result canonical
@@ -437,15 +470,28 @@ __device__ __forceinline__ void tile_m31_grouped(const PrimeCtx &ctx, uint64_t s
       }
       // step both difference tables by one group (low order first)
 #pragma unroll
-      for (int j = 0; j < DA; ++j) {
+      for (int j = 0; j < DT; ++j) {
         if (j < NF) modadd_alu(ga[k][j], ga[k][j + 1]);
         else modadd(ga[k][j], ga[k][j + 1]);
       }
 #pragma unroll
       for (int j = 0; j < DB; ++j) {
-        if (DA + j < NF) modadd_alu(gb[k][j], gb[k][j + 1]);
+        if (DT + j < NF) modadd_alu(gb[k][j], gb[k][j + 1]);
         else modadd(gb[k][j], gb[k][j + 1]);
       }
+    }
+  }
+  if constexpr (UF) {
+    // u^EX carries R^-(EX-1)K more than the G0 of the pair tables, so the
+    // groups' ratio c1 / c0 is R^((EX-1)K) too large: scale c1 back once,
+    // by a product with R^(1-(EX-1)K), before the single-term tail
+    uint32_t f = S.one;
+#pragma unroll 1
+    for (int i = 0; i < (EX - 1) * K; ++i) f = S.mul(f, S.c1);
+#pragma unroll
+    for (int k = 0; k < ILP; ++k) {
+      const uint32_t c = U ? (uint32_t)c1[k] : (uint32_t)m31_canon(c1[k], p);
+      c1[k] = (int32_t)S.mul(c, f);
     }
   }
   // the last (at most K) terms of each chain one at a time (eqn 3.12)
@@ -1090,6 +1136,22 @@ template <> struct M31Form<39> { static constexpr int KC = 4, KS = 5, NFC = 6, N
 template <> struct M31Form<40> { static constexpr int KC = 5, KS = 6, NFC = 8, NFS = 5; };
 template <> struct M31Form<41> { static constexpr int KC = 4, KS = 6, NFC = 6, NFS = 5; };
 template <> struct M31Form<44> { static constexpr int KC = 4, KS = 7, NFC = 6, NFS = 6; };
+// 45..47: the u form (tile_m31_grouped, UF): G0 = u^e from a table of
+// u = prod (s+i) of degree K, so a group steps K + e(K-1) table entries
+// instead of 2eK - e, for e - 1 more products per group; groups of 8 cubes
+// / 10 squares (45), 6 / 8 (46) and 10 / 12 (47)
+template <int AR> struct M31UF { static constexpr bool on = false; };
+template <> struct M31UF<45> { static constexpr bool on = true; };
+template <> struct M31UF<46> { static constexpr bool on = true; };
+template <> struct M31UF<47> { static constexpr bool on = true; };
+template <> struct M31Form<45> { static constexpr int KC = 8, KS = 10, NFC = 8, NFS = 8; };
+template <> struct M31Form<46> { static constexpr int KC = 6, KS = 8, NFC = 6, NFS = 6; };
+template <> struct M31Form<47> { static constexpr int KC = 10, KS = 12, NFC = 10, NFS = 10; };
+// 48 (lane chains): per warp, the u form of 45 for pieces of at least
+// kUFormMinChain terms (its set-up visits e(K-1) + 1 points of K terms, about
+// three times form 41's, and pays on long pieces only) and form 41 below
+template <> struct M31Form<48> : M31Form<41> {};
+constexpr uint64_t kUFormMinChain = 6144;
 
 template <bool WIDE, int ILP, int AR, bool LANE = false>
 __device__ __forceinline__ void process_tile(const Plan &P, uint32_t g) {
@@ -1130,7 +1192,12 @@ __device__ __forceinline__ void process_tile(const Plan &P, uint32_t g) {
   // group sizes and ALU-only table additions of the grouped 32-bit form
   constexpr int NFC = M31Form<AR>::NFC, NFS = M31Form<AR>::NFS;
   constexpr int KC = M31Form<AR>::KC, KS = M31Form<AR>::KS;
+  constexpr bool UFM = M31UF<AR>::on;
   const bool grp_ok = n >= (LANE ? 1ull : 32ull) * ILP * kGroupMinChain;
+  // form 48: the warp's pieces are sorted by length, so lane 0's decides
+  bool ufw = false;
+  if constexpr (AR == 48 && !WIDE) ufw = __shfl_sync(0xffffffffu, n, 0) >= kUFormMinChain;
+  using F45 = M31Form<45>;
   if (AR == 24) {
     tile_general(ctx, start, n, j < P.rows_b ? P.gen_e_b : P.gen_e_e, r0, r1);
   } else if (AR == 23) {
@@ -1139,9 +1206,12 @@ __device__ __forceinline__ void process_tile(const Plan &P, uint32_t g) {
   } else if (!WIDE && (ctx.flags & 1u)) {
     // 2^30 <= p < 2^31 on the 32-bit kernel: the unsigned grouped form with
     // this formulation's group sizes, single 64-bit terms on short tiles
-    if (AR >= 9 && grp_ok) {
-      if (j < P.rows_b) tile_m31_grouped<ILP, true, 7, NFC, KC, true, LANE>(ctx, start, n, r0, r1);
-      else tile_m31_grouped<ILP, false, 7, NFS, KS, true, LANE>(ctx, start, n, r0, r1);
+    if (AR == 48 && ufw && grp_ok) {
+      if (j < P.rows_b) tile_m31_grouped<ILP, true, 7, F45::NFC, F45::KC, true, LANE, true>(ctx, start, n, r0, r1);
+      else tile_m31_grouped<ILP, false, 7, F45::NFS, F45::KS, true, LANE, true>(ctx, start, n, r0, r1);
+    } else if (AR >= 9 && grp_ok) {
+      if (j < P.rows_b) tile_m31_grouped<ILP, true, 7, NFC, KC, true, LANE, UFM>(ctx, start, n, r0, r1);
+      else tile_m31_grouped<ILP, false, 7, NFS, KS, true, LANE, UFM>(ctx, start, n, r0, r1);
     } else {
       if (j < P.rows_b) tile_m64<ILP, true, LANE>(ctx, start, n, r0, r1);
       else tile_m64<ILP, false, LANE>(ctx, start, n, r0, r1);
@@ -1149,10 +1219,13 @@ __device__ __forceinline__ void process_tile(const Plan &P, uint32_t g) {
   } else if (!WIDE && AR == 5 && grp_ok) {
     if (j < P.rows_b) tile_m31_grouped<ILP, true, 5>(ctx, start, n, r0, r1);
     else tile_m31_grouped<ILP, false, 5>(ctx, start, n, r0, r1);
+  } else if (!WIDE && AR == 48 && ufw && grp_ok) {
+    if (j < P.rows_b) tile_m31_grouped<ILP, true, 7, F45::NFC, F45::KC, false, LANE, true>(ctx, start, n, r0, r1);
+    else tile_m31_grouped<ILP, false, 7, F45::NFS, F45::KS, false, LANE, true>(ctx, start, n, r0, r1);
   } else if (!WIDE && AR >= 7 && grp_ok && j >= P.rows_b) {
-    tile_m31_grouped<ILP, false, 7, NFS, KS, false, LANE>(ctx, start, n, r0, r1);
+    tile_m31_grouped<ILP, false, 7, NFS, KS, false, LANE, UFM>(ctx, start, n, r0, r1);
   } else if (!WIDE && AR >= 9 && grp_ok) {
-    tile_m31_grouped<ILP, true, 7, NFC, KC, false, LANE>(ctx, start, n, r0, r1);
+    tile_m31_grouped<ILP, true, 7, NFC, KC, false, LANE, UFM>(ctx, start, n, r0, r1);
   } else if (!WIDE) {
     if (j < P.rows_b) tile_m31<ILP, true, AS, LANE>(ctx, start, n, r0, r1);
     else tile_m31<ILP, false, AS, LANE>(ctx, start, n, r0, r1);
@@ -1258,7 +1331,7 @@ __global__ void __maxnreg__(kM64MaxReg)
     const EpochItem it = items[lo];
     const uint32_t tile = it.first + it.count - 1 - (g - it.prefix);
     if (it.plan >> 31) process_tile<true, I64, 9, LANE>(plans[it.plan & 0x7fffffffu], tile);
-    else process_tile<false, I31, 41, LANE>(plans[it.plan], tile);
+    else process_tile<false, I31, 48, LANE>(plans[it.plan], tile);
   }
 }
 
@@ -1279,7 +1352,7 @@ __global__ void __maxnreg__(kM64MaxReg)
   const EpochItem it = items[lo];
   const uint32_t tile = it.first + it.count - 1 - (g - it.prefix);
   if (it.plan >> 31) process_tile<true, I64, 9, LANE>(plans[it.plan & 0x7fffffffu], tile);
-  else process_tile<false, I31, 41, LANE>(plans[it.plan], tile);
+  else process_tile<false, I31, 48, LANE>(plans[it.plan], tile);
 }
 
 // ------------------------------------------------------------------ getters
@@ -1307,6 +1380,7 @@ AccKernel acc_kernel_lane64(int arith);
 // lane-chain forms 40, 41 (the default), 44 (32-bit groups) and 42, 43
 // (64-bit groups)
 AccKernel acc_kernel_lane31x(int arith, int ilp);
+AccKernel acc_kernel_lane31u(int arith, int ilp);  // the u form, 45..47
 AccKernel acc_kernel_lane64x(int arith);
 AccKernel acc_kernel_m31y(int arith, int ilp);  // form 39 (x falls through to y)
 // serving-loop epoch kernels (the default formulations: 31 on the 32-bit path,

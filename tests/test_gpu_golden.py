@@ -106,8 +106,10 @@ def test_top_window_formulations_equal_oracle(opt):
         assert np.array_equal(rb, gb) and np.array_equal(re, ge)
 
 
-@pytest.mark.parametrize("opt", [None, {"arith": 40}, {"arith": 41}, {"arith": 31, "ilp": 2},
-                                 {"tiling": 1}, {"tiling": 1, "arith": 31, "ilp": 2}])
+@pytest.mark.parametrize("opt", [None, {"arith": 40}, {"arith": 39}, {"arith": 31, "ilp": 2},
+                                 {"arith": 44}, {"arith": 45}, {"arith": 46}, {"arith": 47},
+                                 {"arith": 45, "ilp": 2}, {"arith": 48}, {"tiling": 1},
+                                 {"tiling": 1, "arith": 31, "ilp": 2}])
 def test_p1e9_window_work_units_equal_oracle(opt):
     """The window under lane chains (the default: each lane sums its own piece
     of a sum, pieces sorted by length) with the lane formulations, and under
