@@ -50,18 +50,8 @@ IMAD_SLOTS_PER_MODMUL64 = 17
 # run is that busy share scaled by the run's own terms per SM per clock.  Set an entry to None
 # whenever its kernel changes, until it is captured again.
 PIPE_PROFILE = {
-    # k_accumulate<0,1,41,1> (form 41, lane chains, piece records): 492 primes of
-    # [1062200000, 1062210000), BB2244 + EE2004, 2.3139e10 terms, 9.566 ms at 2.068 GHz; IMAD pipe
-    # 80.98 %, ALU 76.78 % of elapsed.  Traffic: one launch of the full window (--metrics
-    # dram__bytes_read.sum,dram__bytes_write.sum, the second launch): 1.044 GB read + 0.637 GB written
     "accumulate_m31": None,  # form 48 (the u form on long pieces): not yet captured
-    # k_accumulate_m64cap<9,128,1> (8 cubes / 12 squares, lane chains, piece records): 17 primes
-    # of [1e11 - 1e4, 1e11 - 9500), BB2244 + EE2004, 7.5269e10 terms, 50.112 ms at 2.069 GHz;
-    # IMAD pipe 89.27 %, ALU 58.50 %.  Traffic: one launch of the full 391-prime window: 60.2 MB
-    # read + 12.3 MB written
-    "accumulate_m64": {"imad_pct": 0.8927, "alu_pct": 0.5850, "terms_per_clk_sm": 4.776,
-                       "traffic_bytes": 60184064 + 12273664,
-                       "profile": "profiles/accumulate_m64_top_window.md"},
+    "accumulate_m64": None,  # form 50 (the u form on long pieces): not yet captured
 }
 
 

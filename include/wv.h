@@ -187,7 +187,7 @@ typedef struct {
                        call with few primes gets more and shorter tiles (up to 64 per
                        sum) so that one launch still holds ~1e5 tiles */
   int blocks_per_sm;/* persistent grid = SMs x this */
-  int arith;        /* hot-loop formulation (default 48).  Every value gives the same
+  int arith;        /* hot-loop formulation (default 50).  Every value gives the same
                        residues; the others exist for ablation.  32-bit path (p < 2^31;
                        signed words below 2^30, unsigned from 2^30 to 2^31):
                        1, 2, 4 single terms (1: shared t p^-1; 2: one wide product and
@@ -201,8 +201,8 @@ typedef struct {
                        tiles): 40, 41, 44 groups of 5 cubes / 6 squares, 4 / 6, 4 / 7;
                        45, 46, 47 the u form (G0 = u^e from a table of u = prod (s+i),
                        K + e(K-1) table additions per group instead of 2eK - e) with
-                       groups of 8 / 10, 6 / 8, 10 / 12; 48 (default) per warp 45 on
-                       pieces of at least 6144 terms and 41 on shorter ones.  64-bit
+                       groups of 8 / 10, 6 / 8, 10 / 12; 48, 49, 50 (default) per warp
+                       45 on pieces of at least 6144 terms and 41 on shorter ones.  64-bit
                        path (2^31 <= p < 2^37): 1, 2, 4 the single-term 64-bit kernel;
                        12..18 and 21 other group sizes, shrink intervals and register
                        budgets; 32..36 the default with a quarter to all of its 64-bit
@@ -210,8 +210,10 @@ typedef struct {
                        three-input high word); 37 the default with the earlier, longer
                        shrink of its difference tables; 38 the default with its
                        per-chain set-up unrolled; 42, 43 (lane chains only) the default
-                       with Euler groups of 10 or 11 squares; every other value the grouped
-                       default (8 cubes / 12 squares).  23: the paper's own arithmetic on both
+                       with Euler groups of 10 or 11 squares; 49 (lane chains only) the u
+                       form, groups of 12 cubes / 16 squares; 50 (default; lane chains only)
+                       per warp 49 on pieces of at least 65536 terms and the grouped form
+                       below; every other value the grouped form (8 cubes / 12 squares).  23: the paper's own arithmetic on both
                        paths (plain residues, eqn 3.15 split products, remainders from
                        a double-precision quotient, single terms).  Other values:
                        WV_EINVAL */
@@ -223,7 +225,7 @@ typedef struct {
   int tiling;       /* work unit of the accumulation.  0 (default) or 2: lane chains --
                        every lane of a warp sums its own piece of one (prime, sum), the
                        pieces sorted by length so that a warp's lanes finish together;
-                       used with the grouped formulations 48 (default), 31 and 39..47
+                       used with the grouped formulations 50 (default), 31 and 39..49
                        and ILP 1 or 2, warp tiles otherwise.  1: warp tiles -- the 32 lanes of a warp split one piece
                        and merge by shuffles (the earlier work unit, kept for ablation).
                        Other values: WV_EINVAL */
@@ -295,7 +297,7 @@ wv_status wv_histogram(uint64_t lo, uint64_t hi, uint32_t bins, unsigned long lo
 /* Number of congruences in the library: ids 0..12 are the paper's (BB1..BB30,
  * EE3..EE33, Sec. 3 and Sec. 5); the ids after them were generated from
  * BB30 and EE33 by the greedy search over Prop. 2.1 (Sec. 2, "Heuristic
- * searches"), named by their number of sums (BB249 ... EE2004). */
+ * searches"), named by their number of sums (BB249 ... EE4122). */
 int wv_congruence_count(void);
 
 /* The id of the congruence the residue calls on a device prime list use by
@@ -306,9 +308,9 @@ int wv_congruence_default(int kind);
  * serving loop, the batch's per-prime grouping) use for primes of [lo, hi)
  * when the caller chose none, each kind by hi on its own:
  *   B: BB30 up to 5e6, BB249 up to 2e7, BB476 up to 5e7, BB1115 up to
- *      1.5e8, then BB2244;
- *   E: EE33 up to 3e6, EE200 up to 2e7, EE404 up to 5e7, EE967 up to 1e8,
- *      then EE2004
+ *      1.5e8, BB2244 up to 1.2e9, then BB3802;
+ *   E: EE33 up to 3e6, EE200 up to 2e7, EE404 up to 5e7, EE967 up to 1.5e8,
+ *      EE2004 up to 1.2e9, then EE4122
  * (the measured fastest on GB300 with the default lane chains; all give the
  * identical residues). */
 void wv_congruence_for_range(uint64_t lo, uint64_t hi, int *cong_b, int *cong_e);

@@ -358,9 +358,9 @@ def greedy(start: Congruence, rounds: int, D: int = 8, lam: int = 1):
 # left side C_k(2,5,6), which is 14 at 2k = p - 3); the Euler ones from the
 # library's E33 table (integer coefficients relative to its left side).
 GENERATED = [("BB249", "BB30", 40), ("BB476", "BB30", 80), ("BB1115", "BB30", 200),
-             ("BB2244", "BB30", 400),
+             ("BB2244", "BB30", 400), ("BB3802", "BB30", 680),
              ("EE200", "EE33", 40), ("EE404", "EE33", 80), ("EE967", "EE33", 200),
-             ("EE2004", "EE33", 400)]
+             ("EE2004", "EE33", 400), ("EE4122", "EE33", 800)]
 
 
 def generated(which=None):

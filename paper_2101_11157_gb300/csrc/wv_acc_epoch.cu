@@ -8,7 +8,7 @@ namespace wv {
 // the 64-bit tiles of an epoch run one chain per thread (the fastest grouped form)
 EpochKernel epoch_kernel(bool wide, int ilp, bool lane) {
   if (lane) {
-    if (wide) return k_epoch<true, 1, 9, true>;
+    if (wide) return k_epoch<true, 1, 50, true>;
     return ilp == 1 ? k_epoch<false, 1, 48, true> : k_epoch<false, 2, 48, true>;
   }
   if (wide) return k_epoch<true, 1, 9>;

@@ -7,6 +7,7 @@ namespace wv {
 
 AccKernel acc_kernel_lane64(int arith) {
   if (arith == 42 || arith == 43) return acc_kernel_lane64x(arith);
+  if (arith == 49 || arith == 50) return acc_kernel_lane64u(arith);
   return k_accumulate_m64cap<9, kM64MaxReg, true>;
 }
 

@@ -9,7 +9,7 @@ namespace wv {
 AccKernel acc_kernel_lane31u(int arith, int ilp) {
   if (arith == 46) return ilp == 1 ? k_accumulate<false, 1, 46, true> : k_accumulate<false, 2, 46, true>;
   if (arith == 47) return ilp == 1 ? k_accumulate<false, 1, 47, true> : k_accumulate<false, 2, 47, true>;
-  if (arith == 48) return ilp == 1 ? k_accumulate<false, 1, 48, true> : k_accumulate<false, 2, 48, true>;
+  if (arith >= 48) return ilp == 1 ? k_accumulate<false, 1, 48, true> : k_accumulate<false, 2, 48, true>;
   return ilp == 1 ? k_accumulate<false, 1, 45, true> : k_accumulate<false, 2, 45, true>;
 }
 

@@ -17,7 +17,7 @@ namespace wv {
 
 constexpr int kAccThreads = 256;
 constexpr int kMaxRowsPP = 66;  // B rows + E rows of BB30 + EE33 (the allocation-free path)
-constexpr int kMaxDist = 256;   // distinct coefficient bases d of one congruence
+constexpr int kMaxDist = 512;   // distinct coefficient bases d of one congruence
 constexpr uint32_t kChunkPrimes = 16384;  // primes per internal launch sequence
 constexpr uint64_t kGroupMinChain = 48;   // grouped path only for chains of >= 48 terms
 
@@ -755,6 +755,10 @@ template <> struct M64Form<21> { static constexpr int KB = 9, KE = 11, BLK = 16,
 // 22, no more registers than the 8-cube tables
 template <> struct M64Form<42> { static constexpr int KB = 8, KE = 10, BLK = 16, V = 16 | 32; };
 template <> struct M64Form<43> { static constexpr int KB = 8, KE = 11, BLK = 16, V = 16 | 32; };
+// 49: the u form (flag 64): G0 = u^e from a table of u = prod (s+i) of degree
+// K, groups of 12 cubes / 16 squares (tables of 13 + 34 and 17 + 31 entries,
+// the default's register budget)
+template <> struct M64Form<49> { static constexpr int KB = 12, KE = 16, BLK = 16, V = 16 | 32 | 64; };
 
 // a b 2^-64 mod p, below p + 2^12 for a, b < 2^38
 __device__ __forceinline__ uint64_t m64_mm(uint64_t a, uint64_t b, const M64K &K) {
@@ -782,6 +786,12 @@ __device__ __forceinline__ void tile_m64_grouped(const PrimeCtx &ctx, uint64_t s
   constexpr int EX = CUBES ? 3 : 2;
   constexpr int DA = K * EX;
   constexpr int DB = (K - 1) * EX;
+  // flag 64, the u form: G0 = u^EX with u = prod_{i<K} (s+i) from a table of
+  // degree K (the rolled set-up only)
+  constexpr bool UF = (V & 64) != 0;
+  static_assert(!UF || ((V & 32) && !(V & 12)), "the u form needs the rolled set-up, plain adds");
+  constexpr int DT = UF ? K : DA;          // degree of the first table
+  constexpr int DTOP = DT > DB ? DT : DB;  // set-up points 0 .. DTOP
   const int lane = threadIdx.x & 31;
   const Mont M(ctx);
   M64K KK;
@@ -798,7 +808,7 @@ __device__ __forceinline__ void tile_m64_grouped(const PrimeCtx &ctx, uint64_t s
   const uint64_t len = n / nch;
   const uint32_t rem = (uint32_t)(n - len * nch);
   const uint64_t G = len / K;
-  uint64_t c0[ILP], c1[ILP], ga[ILP][DA + 1], gb[ILP][DB + 1];
+  uint64_t c0[ILP], c1[ILP], ga[ILP][DT + 1], gb[ILP][DB + 1];
   uint64_t s_tail[ILP];
   uint32_t n_tail[ILP];
 #pragma unroll
@@ -818,8 +828,9 @@ __device__ __forceinline__ void tile_m64_grouped(const PrimeCtx &ctx, uint64_t s
     // folded into the tables' diagonal as they come: e_j <- (-1)^j D^j.
     const uint64_t p = ctx.p;
     {
-      uint64_t xr = s + (uint64_t)(K * (DA + 1) - 1);
+      uint64_t xr = s + (uint64_t)(K * (DTOP + 1) - 1);
       xr = xr >= p ? xr % p : xr;
+      uint64_t xc = xr;  // the plain x of the current term (u form)
       const uint64_t sq = (uint64_t)M.mulmod((int64_t)xr, (int64_t)xr);
       uint64_t t, d1, d2;
       if (EX == 3) {  // x^3, 3x^2 - 3x + 1, 6x - 6, 6
@@ -832,20 +843,24 @@ __device__ __forceinline__ void tile_m64_grouped(const PrimeCtx &ctx, uint64_t s
         d2 = 2;
       }
       // one point: the pair (P, Q) of the K consecutive x from the current x down
-      auto point = [&](uint64_t &P, uint64_t &Q) {
+      auto point = [&](uint64_t &P, uint64_t &Q, uint64_t &Pu) {
         P = 0;
         Q = ctx.one;
+        Pu = 0;
 #pragma unroll
         for (int i = 0; i < K; ++i) {
           if (i == 0) {
             P = t;
+            if (UF) Pu = xc;
           } else {
             Q = m64_once(m64_mm(Q, t, KK) + P, p);
             P = m64_mm(P, t, KK);
+            if (UF) Pu = m64_once(m64_mm(Pu, xc, KK), p);
           }
           t = m64_subm(t, d1, p);
           d1 = m64_subm(d1, d2, p);
           if (EX == 3) d2 = m64_subm(d2, 6, p);
+          if (UF) xc = m64_subm(xc, 1, p);
         }
       };
       if constexpr ((V & 32) != 0) {
@@ -853,20 +868,23 @@ __device__ __forceinline__ void tile_m64_grouped(const PrimeCtx &ctx, uint64_t s
         // instead of DA + 1 unrolled copies; the table indices stay
         // compile-time and the diagonal lengths are predicated
 #pragma unroll
-        for (int j = 0; j <= DA; ++j) ga[k][j] = 0;
+        for (int j = 0; j <= DT; ++j) ga[k][j] = 0;
 #pragma unroll
         for (int j = 0; j <= DB; ++j) gb[k][j] = 0;
 #pragma unroll 1
-        for (int m = DA; m >= 0; --m) {
-          uint64_t P, Q;
-          point(P, Q);
-          uint64_t nv = m64_once(P, p);
+        for (int m = DTOP; m >= 0; --m) {
+          uint64_t P, Q, Pu;
+          point(P, Q, Pu);
+          uint64_t nv;
+          if (m <= DT) {
+            nv = m64_once(UF ? Pu : P, p);
 #pragma unroll
-          for (int j = 0; j <= DA; ++j) {
-            if (j <= DA - m) {
-              const uint64_t old = ga[k][j];
-              ga[k][j] = nv;
-              if (j < DA - m) nv = m64_subm(nv, old, p);
+            for (int j = 0; j <= DT; ++j) {
+              if (j <= DT - m) {
+                const uint64_t old = ga[k][j];
+                ga[k][j] = nv;
+                if (j < DT - m) nv = m64_subm(nv, old, p);
+              }
             }
           }
           if (m <= DB) {
@@ -884,8 +902,8 @@ __device__ __forceinline__ void tile_m64_grouped(const PrimeCtx &ctx, uint64_t s
       } else {
 #pragma unroll
         for (int m = DA; m >= 0; --m) {
-          uint64_t P, Q;
-          point(P, Q);
+          uint64_t P, Q, Pu;
+          point(P, Q, Pu);
           // fold the new point into the diagonals (point DA - m of the sequence)
           uint64_t nv = m64_once(P, p);
 #pragma unroll
@@ -906,7 +924,7 @@ __device__ __forceinline__ void tile_m64_grouped(const PrimeCtx &ctx, uint64_t s
         }
       }
 #pragma unroll
-      for (int j = 1; j <= DA; j += 2) ga[k][j] = ga[k][j] ? p - ga[k][j] : 0;
+      for (int j = 1; j <= DT; j += 2) ga[k][j] = ga[k][j] ? p - ga[k][j] : 0;
 #pragma unroll
       for (int j = 1; j <= DB; j += 2) gb[k][j] = gb[k][j] ? p - gb[k][j] : 0;
     }
@@ -921,13 +939,25 @@ __device__ __forceinline__ void tile_m64_grouped(const PrimeCtx &ctx, uint64_t s
       for (int k = 0; k < ILP; ++k) {
         uint32_t T0;
         uint64_t TY;
-        m64_prod(c0[k], ga[k][0], T0, TY);
+        uint64_t A = ga[k][0];
+        if constexpr (UF) {
+          // G0 = u^EX: u's value brought below 6p < 2^40 (both factors of a
+          // product below 2^40 keep it under 2^80), then EX - 1 products
+          const uint64_t Us = m64_shrink_q(A, KK, np0, np1);
+          m64_prod(Us, Us, T0, TY);
+          A = m64_redc2(T0, TY, KK);  // < p + 2^16
+          if (EX == 3) {
+            m64_prod(A, Us, T0, TY);
+            A = m64_redc2(T0, TY, KK);
+          }
+        }
+        m64_prod(c0[k], A, T0, TY);
         const uint64_t n0 = m64_redc2(T0, TY, KK);
-        m64_prod2(c1[k], ga[k][0], c0[k], gb[k][0], T0, TY);
+        m64_prod2(c1[k], A, c0[k], gb[k][0], T0, TY);
         c1[k] = m64_redc2(T0, TY, KK);
         c0[k] = n0;
 #pragma unroll
-        for (int j = 0; j < DA; ++j) {
+        for (int j = 0; j < DT; ++j) {
           if ((V & 12) && j < NF) {
             if (V & 8) add64_cc_z(ga[k][j], ga[k][j + 1], z32);
             else add64_cc(ga[k][j], ga[k][j + 1]);
@@ -949,13 +979,22 @@ __device__ __forceinline__ void tile_m64_grouped(const PrimeCtx &ctx, uint64_t s
 #pragma unroll
     for (int k = 0; k < ILP; ++k) {
 #pragma unroll
-      for (int j = 0; j < DA; ++j)
+      for (int j = 0; j < DT; ++j)
         ga[k][j] = (V & 16) ? m64_shrink_q(ga[k][j], KK, np0, np1) : m64_shrink(ga[k][j], KK);
 #pragma unroll
       for (int j = 0; j < DB; ++j)
         gb[k][j] = (V & 16) ? m64_shrink_q(gb[k][j], KK, np0, np1) : m64_shrink(gb[k][j], KK);
     }
     g += nb;
+  }
+  if constexpr (UF) {
+    // u^EX carries R^-(EX-1)K more than the pair tables' G0: scale c1 back
+    // once by R^(1-(EX-1)K) before the single-term tail
+    uint64_t f = ctx.one;
+#pragma unroll 1
+    for (int i = 0; i < (EX - 1) * K; ++i) f = m64_mm(f, 1, KK);
+#pragma unroll
+    for (int k = 0; k < ILP; ++k) c1[k] = m64_mm(c1[k], f, KK);
   }
   // canonical accumulators, then the last (at most K) terms one at a time
   int64_t a0 = 0, a1 = 0;
@@ -1151,7 +1190,12 @@ template <> struct M31Form<47> { static constexpr int KC = 10, KS = 12, NFC = 10
 // kUFormMinChain terms (its set-up visits e(K-1) + 1 points of K terms, about
 // three times form 41's, and pays on long pieces only) and form 41 below
 template <> struct M31Form<48> : M31Form<41> {};
+template <> struct M31Form<49> : M31Form<41> {};  // 49, 50: 48 on the 32-bit kernel
+template <> struct M31Form<50> : M31Form<41> {};
 constexpr uint64_t kUFormMinChain = 6144;
+// 64-bit path, form 50: per warp the u form of 49 on pieces of at least
+// kUFormMinChain64 terms (its set-up visits 34 points of 12 terms), form 9 below
+constexpr uint64_t kUFormMinChain64 = 65536;
 
 template <bool WIDE, int ILP, int AR, bool LANE = false>
 __device__ __forceinline__ void process_tile(const Plan &P, uint32_t g) {
@@ -1194,9 +1238,11 @@ __device__ __forceinline__ void process_tile(const Plan &P, uint32_t g) {
   constexpr int KC = M31Form<AR>::KC, KS = M31Form<AR>::KS;
   constexpr bool UFM = M31UF<AR>::on;
   const bool grp_ok = n >= (LANE ? 1ull : 32ull) * ILP * kGroupMinChain;
-  // form 48: the warp's pieces are sorted by length, so lane 0's decides
+  // forms 48..50: the warp's pieces are sorted by length, so lane 0's decides
+  constexpr bool ADAPT = AR >= 48 && AR <= 50;
   bool ufw = false;
-  if constexpr (AR == 48 && !WIDE) ufw = __shfl_sync(0xffffffffu, n, 0) >= kUFormMinChain;
+  if constexpr (ADAPT && !WIDE) ufw = __shfl_sync(0xffffffffu, n, 0) >= kUFormMinChain;
+  if constexpr (AR == 50 && WIDE) ufw = __shfl_sync(0xffffffffu, n, 0) >= kUFormMinChain64;
   using F45 = M31Form<45>;
   if (AR == 24) {
     tile_general(ctx, start, n, j < P.rows_b ? P.gen_e_b : P.gen_e_e, r0, r1);
@@ -1206,7 +1252,7 @@ __device__ __forceinline__ void process_tile(const Plan &P, uint32_t g) {
   } else if (!WIDE && (ctx.flags & 1u)) {
     // 2^30 <= p < 2^31 on the 32-bit kernel: the unsigned grouped form with
     // this formulation's group sizes, single 64-bit terms on short tiles
-    if (AR == 48 && ufw && grp_ok) {
+    if (ADAPT && ufw && grp_ok) {
       if (j < P.rows_b) tile_m31_grouped<ILP, true, 7, F45::NFC, F45::KC, true, LANE, true>(ctx, start, n, r0, r1);
       else tile_m31_grouped<ILP, false, 7, F45::NFS, F45::KS, true, LANE, true>(ctx, start, n, r0, r1);
     } else if (AR >= 9 && grp_ok) {
@@ -1219,7 +1265,7 @@ __device__ __forceinline__ void process_tile(const Plan &P, uint32_t g) {
   } else if (!WIDE && AR == 5 && grp_ok) {
     if (j < P.rows_b) tile_m31_grouped<ILP, true, 5>(ctx, start, n, r0, r1);
     else tile_m31_grouped<ILP, false, 5>(ctx, start, n, r0, r1);
-  } else if (!WIDE && AR == 48 && ufw && grp_ok) {
+  } else if (!WIDE && ADAPT && ufw && grp_ok) {
     if (j < P.rows_b) tile_m31_grouped<ILP, true, 7, F45::NFC, F45::KC, false, LANE, true>(ctx, start, n, r0, r1);
     else tile_m31_grouped<ILP, false, 7, F45::NFS, F45::KS, false, LANE, true>(ctx, start, n, r0, r1);
   } else if (!WIDE && AR >= 7 && grp_ok && j >= P.rows_b) {
@@ -1229,6 +1275,14 @@ __device__ __forceinline__ void process_tile(const Plan &P, uint32_t g) {
   } else if (!WIDE) {
     if (j < P.rows_b) tile_m31<ILP, true, AS, LANE>(ctx, start, n, r0, r1);
     else tile_m31<ILP, false, AS, LANE>(ctx, start, n, r0, r1);
+  } else if (AR == 50 && grp_ok) {  // 64-bit: the u form on long pieces
+    if (ufw) {
+      if (j < P.rows_b) tile_m64_grouped<ILP, true, 49, LANE>(ctx, start, n, r0, r1);
+      else tile_m64_grouped<ILP, false, 49, LANE>(ctx, start, n, r0, r1);
+    } else {
+      if (j < P.rows_b) tile_m64_grouped<ILP, true, 9, LANE>(ctx, start, n, r0, r1);
+      else tile_m64_grouped<ILP, false, 9, LANE>(ctx, start, n, r0, r1);
+    }
   } else if (AR >= 9 && grp_ok) {
     if (j < P.rows_b) tile_m64_grouped<ILP, true, AR, LANE>(ctx, start, n, r0, r1);
     else tile_m64_grouped<ILP, false, AR, LANE>(ctx, start, n, r0, r1);
@@ -1330,7 +1384,7 @@ __global__ void __maxnreg__(kM64MaxReg)
     }
     const EpochItem it = items[lo];
     const uint32_t tile = it.first + it.count - 1 - (g - it.prefix);
-    if (it.plan >> 31) process_tile<true, I64, 9, LANE>(plans[it.plan & 0x7fffffffu], tile);
+    if (it.plan >> 31) process_tile<true, I64, LANE ? 50 : 9, LANE>(plans[it.plan & 0x7fffffffu], tile);
     else process_tile<false, I31, 48, LANE>(plans[it.plan], tile);
   }
 }
@@ -1351,7 +1405,7 @@ __global__ void __maxnreg__(kM64MaxReg)
   }
   const EpochItem it = items[lo];
   const uint32_t tile = it.first + it.count - 1 - (g - it.prefix);
-  if (it.plan >> 31) process_tile<true, I64, 9, LANE>(plans[it.plan & 0x7fffffffu], tile);
+  if (it.plan >> 31) process_tile<true, I64, LANE ? 50 : 9, LANE>(plans[it.plan & 0x7fffffffu], tile);
   else process_tile<false, I31, 48, LANE>(plans[it.plan], tile);
 }
 
@@ -1380,7 +1434,8 @@ AccKernel acc_kernel_lane64(int arith);
 // lane-chain forms 40, 41 (the default), 44 (32-bit groups) and 42, 43
 // (64-bit groups)
 AccKernel acc_kernel_lane31x(int arith, int ilp);
-AccKernel acc_kernel_lane31u(int arith, int ilp);  // the u form, 45..47
+AccKernel acc_kernel_lane31u(int arith, int ilp);  // the u form, 45..48
+AccKernel acc_kernel_lane64u(int arith);            // the 64-bit u form, 49, 50
 AccKernel acc_kernel_lane64x(int arith);
 AccKernel acc_kernel_m31y(int arith, int ilp);  // form 39 (x falls through to y)
 // serving-loop epoch kernels (the default formulations: 31 on the 32-bit path,

@@ -134,14 +134,14 @@ struct ResidueConfig {
   int max_tiles = 8;
   bool tiles_auto = true; // few primes: more, shorter tiles (see tile_shape)
   int blocks_per_sm = 0;  // 0 = occupancy
-  int arith = 48;         // hot-loop formulation (see wv_accum.cuh)
+  int arith = 50;         // hot-loop formulation (see wv_accum.cuh)
   uint32_t gen_e_b = 0;   // general index: B_{p-e} (e odd); 0 = the B_{p-3} forms
   uint32_t gen_e_e = 0;   // general index: E_{p-1-e} (e even); 0 = the E_{p-3} forms
   size_t chunk = 0;       // primes per launch sequence (0: library default 16384)
   bool check_primes = false;  // planner verifies primality (composites -> invalid slot)
   int tiling = 0;         // 0 / 2: lane chains where supported, 1: warp tiles
-  // lane chains apply to the grouped formulations 48 (the default), 31, 39
-  // and the lane-only forms 40..47, with ILP 1 or 2, and not to the general
+  // lane chains apply to the grouped formulations 50 (the default), 31, 39
+  // and the lane-only forms 40..49, with ILP 1 or 2, and not to the general
   // index (its own single-term tiles)
   bool lane_chains() const {
     return tiling != 1 && (arith == 31 || arith >= 39) && (ilp == 1 || ilp == 2) && !gen_e_b &&
@@ -155,20 +155,22 @@ wv_status resolve_config(const wv_options *opt, bool want_b, bool want_e, Residu
 //   squares; 25..28 form 9 with other ALU/multiply-pipe splits of the table
 //   additions; 29, 30, 31 groups of 3 cubes, 4 squares, or both; 39 groups
 //   of 4 cubes / 5 squares; with lane chains also 40 (5 / 6), 41 (4 / 6) and
-//   44 (4 / 7), the u forms 45 (8 / 10), 46 (6 / 8), 47 (10 / 12), and 48
-//   (the default: per warp 45 on long pieces, 41 on short ones) (M31Form in
-//   wv_accum.cuh).
+//   44 (4 / 7), the u forms 45 (8 / 10), 46 (6 / 8), 47 (10 / 12), and 48,
+//   49, 50 (the default: per warp 45 on long pieces, 41 on short ones)
+//   (M31Form in wv_accum.cuh).
 //   64-bit path (2^31 <= p < 2^37): 1, 2, 4 single terms; every
 //   other value runs the grouped default (8 cubes / 12 squares) except 12..18
 //   and 21, other group sizes and register budgets, 32..36, the default
 //   with its table additions as PTX carry chains, 37, the default with the
 //   earlier, longer shrink of its tables, and 38, the default with its
-//   per-chain set-up unrolled as it was.  23: the paper's own
+//   per-chain set-up unrolled as it was; with lane chains 42, 43 (10 or 11
+//   squares), 49 (the u form, 12 cubes / 16 squares) and 50 (the default:
+//   per warp 49 on long pieces, the grouped form below).  23: the paper's own
 //   arithmetic on both paths.
-constexpr const char *kArithList = "1, 2, 4, 9, 12..18, 21, 23, 25..48";
+constexpr const char *kArithList = "1, 2, 4, 9, 12..18, 21, 23, 25..50";
 inline bool arith_selectable(int a) {
   return a == 1 || a == 2 || a == 4 || a == 9 || (a >= 12 && a <= 18) || a == 21 || a == 23 ||
-         (a >= 25 && a <= 48);
+         (a >= 25 && a <= 50);
 }
 
 // Residues for n primes (device array), asynchronous on s.

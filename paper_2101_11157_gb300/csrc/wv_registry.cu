@@ -129,8 +129,10 @@ int cong_default(int kind) { return kind == 0 ? kWvDefaultB : kWvDefaultE; }
 // with the size of p, Sec. 3 "Method for primes p < 6e10").  Measured on
 // GB300 with lane chains, for each kind alone, over windows of primes from
 // 1e5 to 1e11: with lane chains every congruence runs at the kernel's own
-// rate once its sums are a few thousand terms long, so the cheapest one
-// (most sums) wins from p ~ 1e8 on; below, the smaller ones.
+// rate once its sums are a few thousand terms long, so the cheaper ones
+// (more sums) win as p grows: BB2244 + EE2004 from 1.5e8, BB3802 + EE4122
+// (about twice the sums, which the planner and finaliser pay per prime)
+// from 1.2e9.
 void cong_for_range(uint64_t hi, int *cb, int *ce) {
   struct Band {
     uint64_t hi;
@@ -138,10 +140,10 @@ void cong_for_range(uint64_t hi, int *cb, int *ce) {
   };
   static const Band bands_b[] = {{5000000ull, "BB30"},      {20000000ull, "BB249"},
                                  {50000000ull, "BB476"},    {150000000ull, "BB1115"},
-                                 {~0ull, "BB2244"}};
+                                 {1200000000ull, "BB2244"}, {~0ull, "BB3802"}};
   static const Band bands_e[] = {{3000000ull, "EE33"},      {20000000ull, "EE200"},
-                                 {50000000ull, "EE404"},    {100000000ull, "EE967"},
-                                 {~0ull, "EE2004"}};
+                                 {50000000ull, "EE404"},    {150000000ull, "EE967"},
+                                 {1200000000ull, "EE2004"}, {~0ull, "EE4122"}};
   for (const Band &bd : bands_b)
     if (hi <= bd.hi) {
       *cb = id_of(bd.name, kWvDefaultB);
@@ -164,7 +166,7 @@ const uint64_t *cong_dist() { return registry().dist.data(); }
 wv_status cong_upload(DeviceState *d) {
   const Registry &R = registry();
   for (const CongView &v : R.views)
-    if (v.ndist > 256) return set_error(WV_EINVAL, "congruence %s: %u bases (max 256)", v.name, v.ndist);
+    if (v.ndist > 512) return set_error(WV_EINVAL, "congruence %s: %u bases (max 512)", v.name, v.ndist);
   WV_CUDA(cudaMalloc(&d->cg_rows, R.rows.size() * sizeof(uint32_t)));
   WV_CUDA(cudaMalloc(&d->cg_tc, R.tc.size() * sizeof(int64_t)));
   WV_CUDA(cudaMalloc(&d->cg_td, R.td.size() * sizeof(uint16_t)));

@@ -57,7 +57,7 @@ def test_host_validation_without_gpu():
     # n == 0 is a no-op that touches nothing
     assert lib.wv_residues_pm3(None, 0, None, None, None) == wv.WV_OK
     # the formulation and launch options are checked before any device work
-    for bad in ({"arith": 24}, {"arith": 49}, {"arith": 3}, {"arith": 10}, {"arith": 19},
+    for bad in ({"arith": 24}, {"arith": 51}, {"arith": 3}, {"arith": 10}, {"arith": 19},
                 {"arith": 25, "ilp": 4}, {"arith": 31, "ilp": 4}, {"arith": 2, "ilp": 4},
                 {"ilp": 4}, {"ilp": 3}, {"block": 48}, {"tiling": 3}, {"tiling": -1}):
         assert lib.wv_residues_ex(None, 0, None, None, wv._options(bad), None) == wv.WV_EINVAL, bad

@@ -39,4 +39,4 @@ def test_bench_window_line():
 def test_bench_top_line():
     d = _bench("--workload", "top", "--steps", "1", "--warmup", "1", "--width", "400", "--no-extras")
     assert d["roofline"]["kernel"] == "accumulate_m64" and d["value"] > 0
-    assert d["config"]["congruences"] == "BB2244+EE2004" and d["hits"] == 0
+    assert d["config"]["congruences"] == "BB3802+EE4122" and d["hits"] == 0

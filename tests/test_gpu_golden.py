@@ -5,8 +5,9 @@ the Stafford-Vandiver congruence, eqn 2.4; E_{p-3} by Glaisher's congruence,
 eqn 4.1), the residues of every prime of the 1e5-wide window at 1.06e9 and of
 the 8 seeded primes of [1e11 - 1e4, 1e11).  Here the CUDA path, through the C
 ABI, must give exactly those values: the search as the benchmark runs it (the
-congruences it picks by range: BB2244 + EE2004 at 1.06e9 and near 1e11), the default of a device prime list (BB30 + EE33), and each hot-loop
-formulation of both arithmetic paths."""
+congruences it picks by range: BB2244 + EE2004 at 1.06e9, BB3802 + EE4122
+near 1e11), the default of a device prime list (BB30 + EE33), and each
+hot-loop formulation of both arithmetic paths."""
 import numpy as np
 import pytest
 
@@ -82,7 +83,7 @@ def test_top_window_bench_step_equals_oracle():
     gp, gb, ge = _gold("top_window_subset_residues.txt")
     assert gp.size == 8 and np.array_equal(gp, W.top_window_subset(seed=5, k=8))
     cb, ce = wv.wv_congruence_for_range(*W.TOP_WINDOW)
-    assert [wv.wv_congruence_info(c)[0] for c in (cb, ce)] == ["BB2244", "EE2004"]
+    assert [wv.wv_congruence_info(c)[0] for c in (cb, ce)] == ["BB3802", "EE4122"]
     nh, pr, rb, re = _bench_step(*W.TOP_WINDOW)
     assert pr.size == 391 and nh == 0  # no Wolstenholme or Vandiver prime there (Theorem 1.1)
     idx = np.searchsorted(pr, gp)
@@ -92,7 +93,7 @@ def test_top_window_bench_step_equals_oracle():
 
 
 @pytest.mark.parametrize("opt", [None, {"arith": 1}, {"arith": 21}, {"arith": 32}, {"arith": 33},
-                                 {"arith": 37}, {"arith": 38}])
+                                 {"arith": 37}, {"arith": 38}, {"arith": 49}, {"arith": 50}])
 def test_top_window_formulations_equal_oracle(opt):
     """The 8 stored primes below 1e11 on the 64-bit path: the device-list
     default (BB30 + EE33) and the range's congruences, under the default, the
@@ -120,7 +121,8 @@ def test_p1e9_window_work_units_equal_oracle(opt):
     assert np.array_equal(rb, gb) and np.array_equal(re, ge)
 
 
-@pytest.mark.parametrize("opt", [None, {"arith": 42}, {"arith": 43}, {"tiling": 1}])
+@pytest.mark.parametrize("opt", [None, {"arith": 42}, {"arith": 43}, {"arith": 49}, {"arith": 50},
+                                 {"tiling": 1}])
 def test_lane_chains_few_primes_equal_oracle(opt):
     """Lists of 1 to 8 stored primes below 1e11 and the first 33 of the window at
     1.06e9: most lanes of the last warp of a class are padding, the sums split

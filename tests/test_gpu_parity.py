@@ -108,12 +108,12 @@ def test_p1e9_window_cross_congruences():
     """Every congruence, printed or generated, gives the identical residue (Sec. 3, 5)."""
     ps = u64(api.sieve(*W.P1E9_WINDOW))
     ref_b, ref_e = gpu_residues(ps)
-    # the paper's 13 congruences and the 8 generated ones, each against the
+    # the paper's 13 congruences and the 10 generated ones, each against the
     # default of a device prime list (BB30 + EE33); BB2244 + EE2004 is what the
     # search picks for this window
     for nb, ne in (("BB1", "EE3"), ("BB2", "EE5"), ("BB6", "EE9"), ("BB9", "EE16"),
                    ("BB16", "EE24"), ("BB22", "EE33"), ("BB249", "EE200"), ("BB476", "EE967"),
-                   ("BB1115", "EE404"), ("BB2244", "EE2004")):
+                   ("BB1115", "EE404"), ("BB2244", "EE2004"), ("BB3802", "EE4122")):
         gb, ge = gpu_residues(ps, {"cong_b": cong_id(nb), "cong_e": cong_id(ne)})
         assert np.array_equal(gb, ref_b), nb
         assert np.array_equal(ge, ref_e), ne
@@ -186,7 +186,7 @@ def test_launch_shapes_agree():
                 {"block": 32}, {"block": 96, "ilp": 1}, {"block": 128},
                 {"tiling": 1}, {"tiling": 1, "ilp": 1}, {"tiling": 2, "ilp": 1},
                 *({"arith": a} for a in (*range(12, 19), 21, 23, *range(32, 39))),
-                *({"arith": a, "ilp": i} for a in (*range(25, 32), *range(39, 49)) for i in (1, 2))):
+                *({"arith": a, "ilp": i} for a in (*range(25, 32), *range(39, 51)) for i in (1, 2))):
         gb, ge = gpu_residues(ps, opt)
         assert np.array_equal(gb, ref_b), opt
         assert np.array_equal(ge, ref_e), opt
