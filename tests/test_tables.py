@@ -31,10 +31,6 @@ PAPER = {
 # generated congruences (greedy search over Prop. 2.1 from BB30 / EE33)
 GENERATED = {"BB249": 0, "BB476": 0, "BB1115": 0, "BB2244": 0, "BB3802": 0,
              "EE200": 1, "EE404": 1, "EE967": 1, "EE2004": 1, "EE4122": 1}
-# the longest runs' narrowest rows need primes far above what the exact check
-# below can sweep on the CPU; they are checked there on their non-empty rows,
-# and every row at 1.06e9 against the stored oracle residues on the GPU
-NARROW = {"BB3802", "EE4122"}
 
 
 def _interval(cid, j):
@@ -175,8 +171,8 @@ def _inverse_power_prefix(p, e):
     return pre % np.uint64(p)
 
 
-# every row of every generated congruence outside NARROW holds at least one term at the
-# last of these
+# every row of every generated congruence holds at least one term at the last of these
+# (the narrowest rows, of EE2004 and EE4122, need p > 5.88e7)
 PRIMES_ALL_ROWS = [12_000_017, 31_000_003, 70_000_027]
 
 
@@ -204,5 +200,5 @@ def test_generated_congruences_at_large_primes(T, orc, p):
             S = (int(pre[e][hi]) - int(pre[e][lo - 1])) % p
             rhs += _coef(terms, p, e) * S
         assert rhs * pow(lhs, -1, p) % p == want[kind], (name, p)
-        if p == PRIMES_ALL_ROWS[-1] and name not in NARROW:
+        if p == PRIMES_ALL_ROWS[-1]:
             assert empty == 0, (name, p, empty)
