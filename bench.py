@@ -50,8 +50,21 @@ IMAD_SLOTS_PER_MODMUL64 = 17
 # run is that busy share scaled by the run's own terms per SM per clock.  Set an entry to None
 # whenever its kernel changes, until it is captured again.
 PIPE_PROFILE = {
-    "accumulate_m31": None,  # form 48 (the u form on long pieces): not yet captured
-    "accumulate_m64": None,  # form 50 (the u form on long pieces): not yet captured
+    # k_accumulate<0,1,48,1> (form 48: the u form on pieces of 6144+ terms, lane chains): 492
+    # primes of [1062200000, 1062210000), BB2244 + EE2004, 2.3139e10 terms, 8.544 ms at 2.069 GHz;
+    # IMAD pipe 79.71 %, ALU 72.78 % of elapsed.  Traffic: one launch of the full window
+    # (--metrics dram__bytes_read.sum,dram__bytes_write.sum, the second launch): 1.043 GB read +
+    # 0.637 GB written
+    "accumulate_m31": {"imad_pct": 0.7971, "alu_pct": 0.7278, "terms_per_clk_sm": 8.610,
+                       "traffic_bytes": 1043415552 + 637145600,
+                       "profile": "profiles/accumulate_m31_p1e9_small.md"},
+    # k_accumulate_m64cap<50,128,1> (form 50: the u form on pieces of 65536+ terms): 17 primes of
+    # [1e11 - 1e4, 1e11 - 9500), BB3802 + EE4122, 6.8787e10 terms, 47.171 ms at 2.057 GHz; IMAD
+    # pipe 88.10 %, ALU 57.64 %.  Traffic: one launch of the full 391-prime window: 112.3 MB read +
+    # 63.0 MB written
+    "accumulate_m64": {"imad_pct": 0.8810, "alu_pct": 0.5764, "terms_per_clk_sm": 4.665,
+                       "traffic_bytes": 112334592 + 62980096,
+                       "profile": "profiles/accumulate_m64_top_window.md"},
 }
 
 
