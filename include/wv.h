@@ -201,8 +201,10 @@ typedef struct {
                        tiles): 40, 41, 44 groups of 5 cubes / 6 squares, 4 / 6, 4 / 7;
                        45, 46, 47 the u form (G0 = u^e from a table of u = prod (s+i),
                        K + e(K-1) table additions per group instead of 2eK - e) with
-                       groups of 8 / 10, 6 / 8, 10 / 12; 48, 49, 50 (default) per warp
-                       45 on pieces of at least 6144 terms and 41 on shorter ones.  64-bit
+                       groups of 8 / 10, 6 / 8, 10 / 12; 51, 52 form 45 with 12 / 10 and
+                       4 / 4 of its table additions ALU-only; 48, 49, 50 (default) per
+                       warp 45 on pieces of at least uform_min31 terms and 41 on shorter
+                       ones.  64-bit
                        path (2^31 <= p < 2^37): 1, 2, 4 the single-term 64-bit kernel;
                        12..18 and 21 other group sizes, shrink intervals and register
                        budgets; 32..36 the default with a quarter to all of its 64-bit
@@ -212,7 +214,7 @@ typedef struct {
                        per-chain set-up unrolled; 42, 43 (lane chains only) the default
                        with Euler groups of 10 or 11 squares; 49 (lane chains only) the u
                        form, groups of 12 cubes / 16 squares; 50 (default; lane chains only)
-                       per warp 49 on pieces of at least 65536 terms and the grouped form
+                       per warp 49 on pieces of at least uform_min64 terms and the grouped form
                        below; every other value the grouped form (8 cubes / 12 squares).  23: the paper's own arithmetic on both
                        paths (plain residues, eqn 3.15 split products, remainders from
                        a double-precision quotient, single terms).  Other values:
@@ -226,10 +228,13 @@ typedef struct {
                        every lane of a warp sums its own piece of one (prime, sum), the
                        pieces sorted by length so that a warp's lanes finish together;
                        used with the grouped formulations 50 (default), 31 and 39..49
-                       and ILP 1 or 2, warp tiles otherwise.  1: warp tiles -- the 32 lanes of a warp split one piece
-                       and merge by shuffles (the earlier work unit, kept for ablation).
-                       Other values: WV_EINVAL */
-  int reserved[6];
+                       and ILP 1 or 2, warp tiles otherwise.  1: warp tiles -- the 32
+                       lanes of a warp split one piece and merge by shuffles (the earlier
+                       work unit, kept for ablation).  Other values: WV_EINVAL */
+  int uform_min31;  /* forms 48..50, lane chains: shortest piece (terms) that the 32-bit
+                       kernel sums in the u form (default 3072) */
+  int uform_min64;  /* form 50, lane chains: the same for the 64-bit kernel (default 32768) */
+  int reserved[4];
 } wv_options;
 
 /* wv_residues_pm3 with explicit congruence choice and launch shape.

@@ -65,6 +65,7 @@ struct Plan {
   uint64_t *lane_sum;
   uint64_t lane_target[2], lane_min[2];  // chains wanted per path, shortest chain length
   uint64_t lane_fix[2];  // nonzero: the chain length per path, fixed by the host
+  uint32_t uform_min[2];  // forms 48..50: pieces of at least this many terms take the u form
 };
 constexpr uint32_t kNoChain = 0xffffffffu;
 // One lane chain as the planner lists it, in sorted order, so that a warp's
@@ -1183,19 +1184,25 @@ template <int AR> struct M31UF { static constexpr bool on = false; };
 template <> struct M31UF<45> { static constexpr bool on = true; };
 template <> struct M31UF<46> { static constexpr bool on = true; };
 template <> struct M31UF<47> { static constexpr bool on = true; };
+template <> struct M31UF<51> { static constexpr bool on = true; };
+template <> struct M31UF<52> { static constexpr bool on = true; };
 template <> struct M31Form<45> { static constexpr int KC = 8, KS = 10, NFC = 8, NFS = 8; };
 template <> struct M31Form<46> { static constexpr int KC = 6, KS = 8, NFC = 6, NFS = 6; };
 template <> struct M31Form<47> { static constexpr int KC = 10, KS = 12, NFC = 10, NFS = 10; };
+// 51, 52: form 45 with more (12 / 10) and fewer (4 / 4) of a group's table
+// additions as ALU-only three-input adds
+template <> struct M31Form<51> { static constexpr int KC = 8, KS = 10, NFC = 12, NFS = 10; };
+template <> struct M31Form<52> { static constexpr int KC = 8, KS = 10, NFC = 4, NFS = 4; };
 // 48 (lane chains): per warp, the u form of 45 for pieces of at least
-// kUFormMinChain terms (its set-up visits e(K-1) + 1 points of K terms, about
-// three times form 41's, and pays on long pieces only) and form 41 below
+// Plan::uform_min[0] terms (3072 by default: its set-up visits e(K-1) + 1
+// points of K terms, about three times form 41's, and pays on long pieces
+// only) and form 41 below
 template <> struct M31Form<48> : M31Form<41> {};
 template <> struct M31Form<49> : M31Form<41> {};  // 49, 50: 48 on the 32-bit kernel
 template <> struct M31Form<50> : M31Form<41> {};
-constexpr uint64_t kUFormMinChain = 6144;
 // 64-bit path, form 50: per warp the u form of 49 on pieces of at least
-// kUFormMinChain64 terms (its set-up visits 34 points of 12 terms), form 9 below
-constexpr uint64_t kUFormMinChain64 = 65536;
+// Plan::uform_min[1] terms (32768 by default: its set-up visits 34 points of
+// 12 terms), form 9 below
 
 template <bool WIDE, int ILP, int AR, bool LANE = false>
 __device__ __forceinline__ void process_tile(const Plan &P, uint32_t g) {
@@ -1241,8 +1248,8 @@ __device__ __forceinline__ void process_tile(const Plan &P, uint32_t g) {
   // forms 48..50: the warp's pieces are sorted by length, so lane 0's decides
   constexpr bool ADAPT = AR >= 48 && AR <= 50;
   bool ufw = false;
-  if constexpr (ADAPT && !WIDE) ufw = __shfl_sync(0xffffffffu, n, 0) >= kUFormMinChain;
-  if constexpr (AR == 50 && WIDE) ufw = __shfl_sync(0xffffffffu, n, 0) >= kUFormMinChain64;
+  if constexpr (ADAPT && !WIDE) ufw = __shfl_sync(0xffffffffu, n, 0) >= P.uform_min[0];
+  if constexpr (AR == 50 && WIDE) ufw = __shfl_sync(0xffffffffu, n, 0) >= P.uform_min[1];
   using F45 = M31Form<45>;
   if (AR == 24) {
     tile_general(ctx, start, n, j < P.rows_b ? P.gen_e_b : P.gen_e_e, r0, r1);

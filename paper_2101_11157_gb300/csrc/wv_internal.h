@@ -140,6 +140,7 @@ struct ResidueConfig {
   size_t chunk = 0;       // primes per launch sequence (0: library default 16384)
   bool check_primes = false;  // planner verifies primality (composites -> invalid slot)
   int tiling = 0;         // 0 / 2: lane chains where supported, 1: warp tiles
+  uint32_t uform_min31 = 3072, uform_min64 = 32768;  // u form from pieces this long (48..50)
   // lane chains apply to the grouped formulations 50 (the default), 31, 39
   // and the lane-only forms 40..49, with ILP 1 or 2, and not to the general
   // index (its own single-term tiles)
@@ -167,10 +168,10 @@ wv_status resolve_config(const wv_options *opt, bool want_b, bool want_e, Residu
 //   squares), 49 (the u form, 12 cubes / 16 squares) and 50 (the default:
 //   per warp 49 on long pieces, the grouped form below).  23: the paper's own
 //   arithmetic on both paths.
-constexpr const char *kArithList = "1, 2, 4, 9, 12..18, 21, 23, 25..50";
+constexpr const char *kArithList = "1, 2, 4, 9, 12..18, 21, 23, 25..52";
 inline bool arith_selectable(int a) {
   return a == 1 || a == 2 || a == 4 || a == 9 || (a >= 12 && a <= 18) || a == 21 || a == 23 ||
-         (a >= 25 && a <= 50);
+         (a >= 25 && a <= 52);
 }
 
 // Residues for n primes (device array), asynchronous on s.

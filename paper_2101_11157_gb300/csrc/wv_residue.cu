@@ -391,7 +391,10 @@ static wv_status plan_launches(Plan &P, uint32_t *u32tmp, int sms, cudaStream_t 
     WV_LAUNCH("plan_tilemap", k_plan_tilemap, (unsigned)((ns + 255) / 256), 256, 0, s, P);
   WV_LAUNCH("plan_split", k_plan_split, 1, 1, 0, s, P);
   if (P.lane) {
-    const unsigned gs = (unsigned)(sms * 8);
+    // one segment per thread (grid-stride beyond 2^20 blocks): many warps in
+    // flight hide the atomics' and gathers' latency
+    const size_t gsz = (ns + 255) / 256;
+    const unsigned gs = (unsigned)(gsz < (1u << 20) ? (gsz ? gsz : 1) : (1u << 20));
     WV_CUDA(cudaMemsetAsync(P.chain_hist, 0, (size_t)kChainClasses * kChainBins * 4, s));
     WV_LAUNCH("chain_hist", k_chain_hist, gs, 256, 0, s, P);
     WV_LAUNCH("chain_offsets", k_chain_offsets, 1, kOffThreads, 0, s, P);
@@ -654,6 +657,8 @@ wv_status residues_device(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,
 // tile ranges) -> plan_finalize -> plan_free.
 
 static void fill_rows(Plan &P, const ResidueConfig &cfg, const DeviceState *dev) {
+  P.uform_min[0] = cfg.uform_min31;
+  P.uform_min[1] = cfg.uform_min64;
   P.cg_rows = dev->cg_rows;
   P.cg_tc = dev->cg_tc;
   P.cg_td = dev->cg_td;

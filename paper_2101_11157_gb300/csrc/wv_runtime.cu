@@ -293,6 +293,8 @@ wv_status resolve_config(const wv_options *opt, bool want_b, bool want_e, Residu
     if (opt->arith > 0) c.arith = opt->arith;
     c.check_primes = opt->check_primes != 0;
     c.tiling = opt->tiling;
+    if (opt->uform_min31 > 0) c.uform_min31 = (uint32_t)opt->uform_min31;
+    if (opt->uform_min64 > 0) c.uform_min64 = (uint32_t)opt->uform_min64;
   }
   if (c.tiling < 0 || c.tiling > 2)
     return set_error(WV_EINVAL, "tiling=%d must be 0, 1 or 2", c.tiling);

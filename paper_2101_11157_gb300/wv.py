@@ -59,7 +59,8 @@ class wv_options(ctypes.Structure):
                 ("ilp", ctypes.c_int), ("tile_terms", ctypes.c_int), ("max_tiles", ctypes.c_int),
                 ("blocks_per_sm", ctypes.c_int), ("arith", ctypes.c_int),
                 ("check_primes", ctypes.c_int), ("tiling", ctypes.c_int),
-                ("reserved", ctypes.c_int * 6)]
+                ("uform_min31", ctypes.c_int), ("uform_min64", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
 
 
 _lock = threading.Lock()

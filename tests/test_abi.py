@@ -57,13 +57,14 @@ def test_host_validation_without_gpu():
     # n == 0 is a no-op that touches nothing
     assert lib.wv_residues_pm3(None, 0, None, None, None) == wv.WV_OK
     # the formulation and launch options are checked before any device work
-    for bad in ({"arith": 24}, {"arith": 51}, {"arith": 3}, {"arith": 10}, {"arith": 19},
+    for bad in ({"arith": 24}, {"arith": 53}, {"arith": 3}, {"arith": 10}, {"arith": 19},
                 {"arith": 25, "ilp": 4}, {"arith": 31, "ilp": 4}, {"arith": 2, "ilp": 4},
                 {"ilp": 4}, {"ilp": 3}, {"block": 48}, {"tiling": 3}, {"tiling": -1}):
         assert lib.wv_residues_ex(None, 0, None, None, wv._options(bad), None) == wv.WV_EINVAL, bad
     for good in ({"arith": 23}, {"arith": 25}, {"arith": 28, "ilp": 1}, {"arith": 9, "ilp": 4},
                  {"arith": 32}, {"arith": 37}, {"arith": 38}, {"arith": 39, "ilp": 1}, {"arith": 21, "ilp": 4},
-                 {"check_primes": 1}, {"tiling": 1}, {"tiling": 2, "ilp": 1}):
+                 {"check_primes": 1}, {"tiling": 1}, {"tiling": 2, "ilp": 1},
+                 {"uform_min31": 1, "uform_min64": 1 << 30}):
         assert lib.wv_residues_ex(None, 0, None, None, wv._options(good), None) == wv.WV_OK, good
 
 

@@ -186,7 +186,7 @@ def test_launch_shapes_agree():
                 {"block": 32}, {"block": 96, "ilp": 1}, {"block": 128},
                 {"tiling": 1}, {"tiling": 1, "ilp": 1}, {"tiling": 2, "ilp": 1},
                 *({"arith": a} for a in (*range(12, 19), 21, 23, *range(32, 39))),
-                *({"arith": a, "ilp": i} for a in (*range(25, 32), *range(39, 51)) for i in (1, 2))):
+                *({"arith": a, "ilp": i} for a in (*range(25, 32), *range(39, 53)) for i in (1, 2))):
         gb, ge = gpu_residues(ps, opt)
         assert np.array_equal(gb, ref_b), opt
         assert np.array_equal(ge, ref_e), opt
