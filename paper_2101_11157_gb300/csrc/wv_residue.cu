@@ -417,44 +417,47 @@ __device__ __forceinline__ uint64_t special_value(uint64_t p, bool isB) {
   return WV_RESIDUE_INVALID;
 }
 
+// One block per (prime, kind): its threads compute the powers d^-e of the
+// congruence's bases and fold the sums' partials into fractions side by side,
+// and the block merges the fractions (a prime's thousands of sums would make
+// one warp's serial chain the launch's critical path).
 constexpr int kFinThreads = 256;
 __global__ void __launch_bounds__(kFinThreads) k_finalize(Plan P) {
   const int lane = threadIdx.x & 31;
-  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t item = blockIdx.x;  // (slot, kind), uniform over the block
   const uint32_t nk = (P.rows_b ? 1u : 0u) + (P.rows_e ? 1u : 0u);
-  if (gw >= P.n * nk) return;
-  const uint32_t slot = gw / nk, kk = gw - slot * nk;
+  if (item >= P.n * nk) return;
+  const uint32_t slot = item / nk, kk = item - slot * nk;
   const bool isB = (P.rows_b != 0) && kk == 0;
   uint64_t *out = isB ? P.out_b : P.out_e;
   if (!out) return;
   const PrimeCtx ctx = P.ctx[slot];
   const uint32_t ge = isB ? P.gen_e_b : P.gen_e_e;  // general index: exponent e, else 0
   if (ctx.flags & 2u) {
-    if (lane == 0) out[ctx.orig] = ge ? WV_RESIDUE_INVALID : special_value(ctx.p, isB);
+    if (threadIdx.x == 0) out[ctx.orig] = ge ? WV_RESIDUE_INVALID : special_value(ctx.p, isB);
     return;
   }
   const Mont M(ctx);
   const int64_t p = (int64_t)ctx.p;
   if (ge && ctx.p < (uint64_t)ge + 3) {  // the general forms need 2 <= 2k <= p - 3
-    if (lane == 0) out[ctx.orig] = WV_RESIDUE_INVALID;
+    if (threadIdx.x == 0) out[ctx.orig] = WV_RESIDUE_INVALID;
     return;
   }
   const uint32_t nrows = isB ? P.rows_b : P.rows_e;
   const uint32_t r0 = isB ? 0u : P.rows_b;
   const uint32_t seg0 = slot * P.rows_pp + r0;
-  // d^-ex for the congruence's distinct bases d, once per prime, per warp
-  __shared__ int64_t s_pow[kFinThreads / 32][kMaxDist];
-  int64_t *dpow = s_pow[threadIdx.x >> 5];
+  // d^-ex for the congruence's distinct bases d, once per prime and kind
+  __shared__ int64_t dpow[kMaxDist];
   {
     const uint32_t d0 = isB ? P.db0 : P.de0, nd = isB ? P.dbn : P.den;
     const uint64_t ex = isB ? P.ex_b : P.ex_e;
-    for (uint32_t i = lane; i < nd; i += 32)
+    for (uint32_t i = threadIdx.x; i < nd; i += kFinThreads)
       dpow[i] = M.pow(M.to_mont((int64_t)(P.cg_dist[d0 + i] % ctx.p)), ctx.p - 1 - ex);
-    __syncwarp();
+    __syncthreads();
   }
   const uint32_t reg0 = isB ? P.rb0 : P.re0;
   int64_t N = 0, D = M.one;  // running fraction N / D = sum coef_j c1_j / c0_j
-  for (uint32_t j = lane; j < nrows; j += 32) {
+  for (uint32_t j = threadIdx.x; j < nrows; j += kFinThreads) {
     const uint32_t s = seg0 + j;
     int64_t C0 = M.one, C1 = 0;
     const uint32_t f = P.seg_first[s], T = P.seg_tiles[s];
@@ -489,7 +492,17 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(Plan P) {
     N = M.add(M.mul(N, D2), M.mul(N2, D));
     D = M.mul(D, D2);
   }
+  __shared__ int64_t sN[kFinThreads / 32], sD[kFinThreads / 32];
   if (lane == 0) {
+    sN[threadIdx.x >> 5] = N;
+    sD[threadIdx.x >> 5] = D;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < kFinThreads / 32; ++w) {
+      N = M.add(M.mul(N, sD[w]), M.mul(sN[w], D));
+      D = M.mul(D, sD[w]);
+    }
     int64_t L;  // the constant on the left, plain
     if (ge && isB) {
       // C_k(a,b,c) = (a^e + b^e - c^e - 1) / (4k) with 4k = 2(p - e) = -2e (mod p):
@@ -644,8 +657,8 @@ wv_status residues_device(const uint64_t *d_primes, size_t n, uint64_t *d_out_b,
     WV_CHECK(launch_accumulate<false>(P, cfg, dev->sms, s));
     WV_CHECK(launch_accumulate<true>(P, cfg, dev->sms, s));
     const uint32_t nk = (do_b ? 1 : 0) + (do_e ? 1 : 0);
-    const size_t warps = (size_t)P.n * nk;
-    WV_LAUNCH("finalize", k_finalize, (unsigned)((warps * 32 + 255) / 256), 256, 0, s, P);
+    const size_t items = (size_t)P.n * nk;  // one block per (prime, kind)
+    WV_LAUNCH("finalize", k_finalize, (unsigned)items, kFinThreads, 0, s, P);
   }
   return WV_OK;
 }
@@ -851,8 +864,8 @@ wv_status plan_finalize(PlanState *ps, uint64_t *d_out_b, uint64_t *d_out_e, cud
   P.out_b = P.rows_b ? d_out_b : nullptr;
   P.out_e = P.rows_e ? d_out_e : nullptr;
   const uint32_t nk = (P.rows_b ? 1u : 0u) + (P.rows_e ? 1u : 0u);
-  const size_t warps = (size_t)P.n * nk;
-  WV_LAUNCH("finalize", k_finalize, (unsigned)((warps * 32 + 255) / 256), 256, 0, s, P);
+  const size_t items = (size_t)P.n * nk;
+  WV_LAUNCH("finalize", k_finalize, (unsigned)items, kFinThreads, 0, s, P);
   return WV_OK;
 }
 
@@ -1055,8 +1068,8 @@ wv_status residues_noalloc(const uint64_t *d_primes, size_t n, uint64_t *d_out_b
   WV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ64, k64, kAccThreads, 0));
   k31<<<(unsigned)(sms * (occ31 > 0 ? occ31 : 1)), kAccThreads, 0, s>>>(P);
   k64<<<(unsigned)(sms * (occ64 > 0 ? occ64 : 1)), kAccThreads, 0, s>>>(P);
-  const size_t warps = (size_t)P.n * ((do_b ? 1 : 0) + (do_e ? 1 : 0));
-  k_finalize<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(P);
+  const size_t items = (size_t)P.n * ((do_b ? 1 : 0) + (do_e ? 1 : 0));
+  k_finalize<<<(unsigned)items, kFinThreads, 0, s>>>(P);
   WV_CUDA(cudaGetLastError());
   return WV_OK;
 }
