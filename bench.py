@@ -58,12 +58,12 @@ PIPE_PROFILE = {
     "accumulate_m31": {"imad_pct": 0.7971, "alu_pct": 0.7278, "terms_per_clk_sm": 8.610,
                        "traffic_bytes": 1043415552 + 637145600,
                        "profile": "profiles/accumulate_m31_p1e9_small.md"},
-    # k_accumulate_m64cap<50,128,1> (form 50: the u form on pieces of 65536+ terms): 17 primes of
-    # [1e11 - 1e4, 1e11 - 9500), BB3802 + EE4122, 6.8787e10 terms, 47.171 ms at 2.057 GHz; IMAD
-    # pipe 88.10 %, ALU 57.64 %.  Traffic: one launch of the full 391-prime window: 112.3 MB read +
-    # 63.0 MB written
-    "accumulate_m64": {"imad_pct": 0.8810, "alu_pct": 0.5764, "terms_per_clk_sm": 4.665,
-                       "traffic_bytes": 112334592 + 62980096,
+    # k_accumulate_m64cap<50,128,1> (form 50: the u form with one-round products on pieces of
+    # 65536+ terms): 17 primes of [1e11 - 1e4, 1e11 - 9500), BB3802 + EE4122, 6.8787e10 terms,
+    # 44.022 ms at 2.057 GHz; IMAD pipe 85.51 %, ALU 53.12 %.  Traffic: not yet captured for
+    # this kernel
+    "accumulate_m64": {"imad_pct": 0.8551, "alu_pct": 0.5312, "terms_per_clk_sm": 4.9986,
+                       "traffic_bytes": None,
                        "profile": "profiles/accumulate_m64_top_window.md"},
 }
 

@@ -645,6 +645,12 @@ __device__ __forceinline__ uint64_t m64_redc2(uint32_t T0, uint64_t TY, const M6
   const uint64_t B = umad_wide(m1, K.p0, (uint64_t)ulo(U));   // low word is 0
   return umad_wide(m1, K.p1, (uint64_t)uhi(U)) + uhi(B);      // (U + m1 p) / 2^32
 }
+// (T0 + TY 2^32) 2^-32 mod p for T < 2^96: one round, result below T / 2^32 + p
+__device__ __forceinline__ uint64_t m64_redc1(uint32_t T0, uint64_t TY, const M64K &K) {
+  const uint32_t m0 = T0 * K.q;
+  const uint64_t A = umad_wide(m0, K.p0, (uint64_t)T0);  // low word is 0
+  return umad_wide(m0, K.p1, TY) + uhi(A);               // (T + m0 p) / 2^32
+}
 // T = c g as (T0, TY); c < p + 2^31, g < 2^57
 __device__ __forceinline__ void m64_prod(uint64_t c, uint64_t g, uint32_t &T0, uint64_t &TY) {
   const uint32_t c0 = ulo(c), c1 = uhi(c), g0 = ulo(g), g1 = uhi(g);
@@ -758,8 +764,11 @@ template <> struct M64Form<42> { static constexpr int KB = 8, KE = 10, BLK = 16,
 template <> struct M64Form<43> { static constexpr int KB = 8, KE = 11, BLK = 16, V = 16 | 32; };
 // 49: the u form (flag 64): G0 = u^e from a table of u = prod (s+i) of degree
 // K, groups of 12 cubes / 16 squares (tables of 13 + 34 and 17 + 31 entries,
-// the default's register budget)
-template <> struct M64Form<49> { static constexpr int KB = 12, KE = 16, BLK = 16, V = 16 | 32 | 64; };
+// the default's register budget), with one REDC round per product of u^e
+// (flag 128)
+template <> struct M64Form<49> {
+  static constexpr int KB = 12, KE = 16, BLK = 16, V = 16 | 32 | 64 | 128;
+};
 
 // a b 2^-64 mod p, below p + 2^12 for a, b < 2^38
 __device__ __forceinline__ uint64_t m64_mm(uint64_t a, uint64_t b, const M64K &K) {
@@ -791,6 +800,12 @@ __device__ __forceinline__ void tile_m64_grouped(const PrimeCtx &ctx, uint64_t s
   // degree K (the rolled set-up only)
   constexpr bool UF = (V & 64) != 0;
   static_assert(!UF || ((V & 32) && !(V & 12)), "the u form needs the rolled set-up, plain adds");
+  // flag 128: one 32-bit REDC round (a factor 2^-32) per product of u^EX
+  // instead of two: u's value below 6p < 2^39.6 gives u u 2^-32 < 2^47.2 and
+  // u^3 2^-64 < 2^55, still below 2^57, and every product of the pair
+  // update stays below 2^96 (c0, c1 < p + 2^32 from the full rounds there)
+  constexpr bool UH = (V & 128) != 0;
+  static_assert(!UH || UF, "one-round products belong to the u form");
   constexpr int DT = UF ? K : DA;          // degree of the first table
   constexpr int DTOP = DT > DB ? DT : DB;  // set-up points 0 .. DTOP
   const int lane = threadIdx.x & 31;
@@ -946,10 +961,10 @@ __device__ __forceinline__ void tile_m64_grouped(const PrimeCtx &ctx, uint64_t s
           // product below 2^40 keep it under 2^80), then EX - 1 products
           const uint64_t Us = m64_shrink_q(A, KK, np0, np1);
           m64_prod(Us, Us, T0, TY);
-          A = m64_redc2(T0, TY, KK);  // < p + 2^16
+          A = UH ? m64_redc1(T0, TY, KK) : m64_redc2(T0, TY, KK);  // < 2^47.2 or p + 2^16
           if (EX == 3) {
             m64_prod(A, Us, T0, TY);
-            A = m64_redc2(T0, TY, KK);
+            A = UH ? m64_redc1(T0, TY, KK) : m64_redc2(T0, TY, KK);  // < 2^55 or p + 2^16
           }
         }
         m64_prod(c0[k], A, T0, TY);
@@ -989,11 +1004,17 @@ __device__ __forceinline__ void tile_m64_grouped(const PrimeCtx &ctx, uint64_t s
     g += nb;
   }
   if constexpr (UF) {
-    // u^EX carries R^-(EX-1)K more than the pair tables' G0: scale c1 back
-    // once by R^(1-(EX-1)K) before the single-term tail
+    // u^EX carries R^-(EX-1)K more than the pair tables' G0 (with one-round
+    // products R^-(EX-1)(K-1/2), R = 2^64): scale c1 back once by that
+    // factor, as f = R^(1-(EX-1)K) (or the like) times R^-1 in the product
     uint64_t f = ctx.one;
+    if constexpr (UH) {
 #pragma unroll 1
-    for (int i = 0; i < (EX - 1) * K; ++i) f = m64_mm(f, 1, KK);
+      for (int i = 0; i < (EX - 1) * (2 * K - 1); ++i) f = m64_redc1(ulo(f), uhi(f), KK);
+    } else {
+#pragma unroll 1
+      for (int i = 0; i < (EX - 1) * K; ++i) f = m64_mm(f, 1, KK);
+    }
 #pragma unroll
     for (int k = 0; k < ILP; ++k) c1[k] = m64_mm(c1[k], f, KK);
   }
