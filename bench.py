@@ -60,10 +60,10 @@ PIPE_PROFILE = {
                        "profile": "profiles/accumulate_m31_p1e9_small.md"},
     # k_accumulate_m64cap<50,128,1> (form 50: the u form with one-round products on pieces of
     # 65536+ terms): 17 primes of [1e11 - 1e4, 1e11 - 9500), BB3802 + EE4122, 6.8787e10 terms,
-    # 44.022 ms at 2.057 GHz; IMAD pipe 85.51 %, ALU 53.12 %.  Traffic: not yet captured for
-    # this kernel
+    # 44.022 ms at 2.057 GHz; IMAD pipe 85.51 %, ALU 53.12 %.  Traffic: one launch of the full
+    # 391-prime window (the second launch): 112.9 MB read + 62.8 MB written
     "accumulate_m64": {"imad_pct": 0.8551, "alu_pct": 0.5312, "terms_per_clk_sm": 4.9986,
-                       "traffic_bytes": None,
+                       "traffic_bytes": 112914176 + 62783232,
                        "profile": "profiles/accumulate_m64_top_window.md"},
 }
 
