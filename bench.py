@@ -56,6 +56,7 @@ PIPE_PROFILE = {
     # (--metrics dram__bytes_read.sum,dram__bytes_write.sum, the second launch): 1.043 GB read +
     # 0.637 GB written
     "accumulate_m31": {"imad_pct": 0.7971, "alu_pct": 0.7278, "terms_per_clk_sm": 8.610,
+                       "inst_per_term": 7.572e9 * 32 / 2.3139e10,
                        "traffic_bytes": 1043415552 + 637145600,
                        "profile": "profiles/accumulate_m31_p1e9_small.md"},
     # k_accumulate_m64cap<50,128,1> (form 50: the u form with one-round products on pieces of
@@ -63,6 +64,7 @@ PIPE_PROFILE = {
     # 44.022 ms at 2.057 GHz; IMAD pipe 85.51 %, ALU 53.12 %.  Traffic: one launch of the full
     # 391-prime window (the second launch): 112.9 MB read + 62.8 MB written
     "accumulate_m64": {"imad_pct": 0.8551, "alu_pct": 0.5312, "terms_per_clk_sm": 4.9986,
+                       "inst_per_term": 3.3522e10 * 32 / 6.8787e10,
                        "traffic_bytes": 112914176 + 62783232,
                        "profile": "profiles/accumulate_m64_top_window.md"},
 }
@@ -340,7 +342,12 @@ def gpu_arm(args):
                 "frac_basis": f"IMAD-pipe busy {prof_k['imad_pct']:.3f} at {prof_k['terms_per_clk_sm']:.3f} "
                               f"terms/clk/SM ({prof_k['profile']}); this run {tpcs:.3f} terms/clk/SM at "
                               f"{clk_mhz:.0f} MHz",
-                "alu_pipe_busy_in_capture": prof_k.get("alu_pct")}
+                "alu_pipe_busy_in_capture": prof_k.get("alu_pct"),
+                # multiply-pipe lane-cycles and instructions (all pipes) per algorithmic
+                # Montgomery product (two per summed term, eqn 3.12), from the capture
+                "imad_slots_per_modmul": prof_k["imad_pct"] * IMAD_PER_SM_CLK
+                                         / prof_k["terms_per_clk_sm"] / 2.0,
+                "inst_per_modmul": prof_k["inst_per_term"] / 2.0}
     else:
         roof = {"bound": "alu", "achieved": None, "peak": pipe_peak, "unit": "IMAD-pipe cycles/s",
                 "frac": None, "traffic": None,
