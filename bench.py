@@ -543,7 +543,7 @@ def batch_arm(args):
 
 
 def serve_measure(stream_q, epoch_terms: float, epoch_form: int = 0, epoch_block: int = 0,
-                  plain_block: int = 0):
+                  plain_block: int = 0, piece_log2: int = 0):
     """Serve a stream of queries (continuous batching) and, for comparison,
     run it one query at a time in arrival order; both pick congruences by the
     query's range."""
@@ -551,7 +551,8 @@ def serve_measure(stream_q, epoch_terms: float, epoch_form: int = 0, epoch_block
     import torch
 
     from paper_2101_11157_gb300 import api, wv
-    srv = wv.wv_server_create(epoch_terms=epoch_terms, epoch_form=epoch_form, epoch_block=epoch_block)
+    srv = wv.wv_server_create(epoch_terms=epoch_terms, epoch_form=epoch_form, epoch_block=epoch_block,
+                              piece_log2=piece_log2)
     t0 = time.perf_counter()
     ids = []
     for q in stream_q:
@@ -617,7 +618,8 @@ def serve_arm(args):
         for q in stream_q:
             if q["kind"] == "range":
                 q["hi"] = min(q["hi"], q["lo"] + args.max_range)
-    r = serve_measure(stream_q, args.epoch_terms, args.epoch_form, args.epoch_block, args.plain_block)
+    r = serve_measure(stream_q, args.epoch_terms, args.epoch_form, args.epoch_block, args.plain_block,
+                      args.piece_log2)
     line = {"workload": "serve", "metric": "primes/s and p50/p99 latency, continuous batching vs one query at a time",
             "value": r["served_primes_s"], "unit": "primes/s", **r,
             "config": {"queries": len(stream_q), "rate_per_s": args.rate, "seed": 11,
@@ -625,7 +627,8 @@ def serve_arm(args):
                        "epoch_terms": args.epoch_terms, "primes": r["primes"],
                        "plain_block": args.plain_block or None,
                        "epoch_form": args.epoch_form,
-                       "epoch_block": args.epoch_block or 32}}
+                       "epoch_block": args.epoch_block or 32,
+                       "piece_log2": args.piece_log2 or 17}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -654,6 +657,8 @@ def main():
                     help="serve: 0 default (1), 1 persistent over both paths, 2 one warp per tile, "
                          "3 persistent per path")
     ap.add_argument("--epoch-block", type=int, default=0, help="serve: epoch block size (0: 32)")
+    ap.add_argument("--piece-log2", type=int, default=0,
+                    help="serve: longest piece of a sum in a query's plan, 2^k terms (0: 17)")
     ap.add_argument("--plain-block", type=int, default=0,
                     help="serve: accumulation block size of the one-query-at-a-time form (0: default)")
     args = ap.parse_args()

@@ -36,7 +36,11 @@ typedef struct {
                             (non-persistent, both paths), 3 one persistent launch
                             per arithmetic path                                       */
   int epoch_block;       /* threads per block of an epoch launch, 32..256 (0: 32)     */
-  int reserved[5];
+  int piece_log2;        /* longest lane chain (piece of a sum) of a query's plan:
+                            2^piece_log2 terms, 12..24 (0: 17).  Longer pieces pay
+                            fewer per-piece set-ups; shorter ones bound how long one
+                            lane can hold an epoch                                    */
+  int reserved[4];
 } wv_server_config;
 
 typedef struct {

@@ -141,6 +141,7 @@ struct ResidueConfig {
   bool check_primes = false;  // planner verifies primality (composites -> invalid slot)
   int tiling = 0;         // 0 / 2: lane chains where supported, 1: warp tiles
   uint32_t uform_min31 = 3072, uform_min64 = 32768;  // u form from pieces this long (48..50)
+  uint64_t epoch_piece_max = 1ull << 17;  // longest lane chain of a serving plan
   // lane chains apply to the grouped formulations 50 (the default), 31, 39
   // and the lane-only forms 40..49, with ILP 1 or 2, and not to the general
   // index (its own single-term tiles)

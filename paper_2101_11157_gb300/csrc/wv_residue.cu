@@ -163,11 +163,12 @@ constexpr uint32_t kChainBins = 2048;  // length bins per class
 // shortest chain lengths (the 64-bit path's set-up costs about 40 groups)
 constexpr uint64_t kLaneThreads31 = 768, kLaneThreads64 = 512;
 constexpr uint64_t kLaneRounds = 16, kLaneRoundsEpoch = 4;
-// a serving plan's chains are at most kLaneMaxEpoch[path] terms long, so that
-// an epoch is never held up by one long chain (about 4 ms of one lane on the
-// 32-bit kernel, 7 ms on the 64-bit one, whose per-chain set-up is costlier)
-// and the shortest epochs still hold enough warps to fill the GPU
-constexpr uint64_t kLaneMaxEpoch[2] = {1ull << 16, 1ull << 16};
+// a serving plan's chains are at most ResidueConfig::epoch_piece_max terms
+// long (2^17 by default), so that an epoch is never held up long by one chain
+// (2^17 terms are about 8 ms of one lane on the 32-bit kernel, 13 ms on the
+// 64-bit one) and the shortest epochs still hold enough warps to fill the GPU;
+// shorter caps pay more per-chain set-ups (2^16 served a mixed stream 2 %
+// slower), longer ones let single chains hold epochs (2^20: 2 % slower)
 constexpr uint64_t kLaneMin31 = 4096, kLaneMin64 = 16384;
 
 __global__ void k_lane_sum(Plan P) {  // terms per path: one atomic per block and path
@@ -343,15 +344,16 @@ static size_t tiles_capacity(const ResidueConfig &cfg, size_t ns, uint32_t max_t
 }
 
 // Chain lengths of a serving plan from upper bounds t[path] on its terms:
-// t / (kLaneRoundsEpoch x the path's resident lanes), within [floor,
-// kLaneMaxEpoch]; the plan then holds at most segments + sum t / L tiles.
-static void epoch_chain_lengths(const double *t, int sms, uint64_t *L, size_t *extra_tiles) {
+// t / (kLaneRoundsEpoch x the path's resident lanes), within [floor, lmax];
+// the plan then holds at most segments + sum t / L tiles.
+static void epoch_chain_lengths(const double *t, int sms, uint64_t lmax, uint64_t *L,
+                                size_t *extra_tiles) {
   const uint64_t lanes[2] = {(uint64_t)sms * kLaneThreads31, (uint64_t)sms * kLaneThreads64};
   const uint64_t lmin[2] = {kLaneMin31, kLaneMin64};
   *extra_tiles = 0;
   for (int i = 0; i < 2; ++i) {
     const double want = t[i] / (double)(kLaneRoundsEpoch * lanes[i]);
-    uint64_t l = want > (double)kLaneMaxEpoch[i] ? kLaneMaxEpoch[i] : (uint64_t)want + 1;
+    uint64_t l = want > (double)lmax ? lmax : (uint64_t)want + 1;
     L[i] = l < lmin[i] ? lmin[i] : l;
     *extra_tiles += (size_t)(t[i] / (double)L[i]) + 1;
   }
@@ -731,7 +733,7 @@ size_t plan_bytes(uint32_t n, const ResidueConfig &cfg, const double *terms) {
   if (cfg.lane_chains() && terms) {
     uint64_t L[2];
     size_t extra = 0;
-    epoch_chain_lengths(terms, sms, L, &extra);
+    epoch_chain_lengths(terms, sms, cfg.epoch_piece_max, L, &extra);
     tc = ns + extra;
   }
   size_t b = n * (sizeof(PrimeCtx) + 8) + ns * (8 + 8 + 4 + 4) + tc * (sizeof(ulonglong2) + 4) +
@@ -771,7 +773,7 @@ wv_status plan_build(const uint64_t *d_primes, uint32_t n, const ResidueConfig &
   size_t tiles_cap = tiles_capacity(cfg, ns, P.max_tiles, dev->sms, kLaneRoundsEpoch);
   if (cfg.lane_chains() && terms) {
     size_t extra = 0;
-    epoch_chain_lengths(terms, dev->sms, P.lane_fix, &extra);
+    epoch_chain_lengths(terms, dev->sms, cfg.epoch_piece_max, P.lane_fix, &extra);
     tiles_cap = ns + extra;
   }
   WV_CHECK(get((void **)&P.partials, tiles_cap * sizeof(ulonglong2)));

@@ -616,12 +616,16 @@ wv_status wv_server_create(const wv_server_config *cfg, wv_server *out) {
   wv_status st = (e == cudaSuccess) ? device_state(&ds) : cuda_fail(e, "cudaSetDevice");
   if (st == WV_OK) {
     S->sms = ds->sms;
-    WV_CHECK(resolve_config(nullptr, true, true, &S->rcfg));
+    st = resolve_config(nullptr, true, true, &S->rcfg);  // on error, S is freed below
     // small epoch blocks (one warp by default): a warp that runs out of tiles
     // frees its registers at once for the next epoch, not after its block
     S->rcfg.block = S->cfg.epoch_block > 0 ? S->cfg.epoch_block : kEpochBlock;
     if (S->rcfg.block % 32 || S->rcfg.block > 256) st = set_error(WV_EINVAL, "epoch_block must be 32..256, a multiple of 32");
     if (S->cfg.epoch_form < 0 || S->cfg.epoch_form > 3) st = set_error(WV_EINVAL, "epoch_form must be 0..3");
+    if (S->cfg.piece_log2 != 0 && (S->cfg.piece_log2 < 12 || S->cfg.piece_log2 > 24))
+      st = set_error(WV_EINVAL, "piece_log2 must be 0 or 12..24");
+    else if (S->cfg.piece_log2)
+      S->rcfg.epoch_piece_max = 1ull << S->cfg.piece_log2;
     int lo_prio = 0, hi_prio = 0;
     cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
     // admission and finalisation go first whenever SMs free up

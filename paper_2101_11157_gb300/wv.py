@@ -45,7 +45,7 @@ class wv_server_config(ctypes.Structure):
     _fields_ = [("mem_budget", ctypes.c_size_t), ("max_active", ctypes.c_uint32),
                 ("epoch_terms", ctypes.c_double), ("device", ctypes.c_int),
                 ("epoch_form", ctypes.c_int), ("epoch_block", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("piece_log2", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 class wv_query_info(ctypes.Structure):
@@ -439,10 +439,11 @@ def _info(i: wv_query_info) -> dict:
 
 
 def wv_server_create(mem_budget: int = 0, max_active: int = 0, epoch_terms: float = 0.0,
-                     device: int = -1, epoch_form: int = 0, epoch_block: int = 0):
+                     device: int = -1, epoch_form: int = 0, epoch_block: int = 0,
+                     piece_log2: int = 0):
     cfg = wv_server_config()
     cfg.mem_budget, cfg.max_active, cfg.epoch_terms, cfg.device = mem_budget, max_active, epoch_terms, device
-    cfg.epoch_form, cfg.epoch_block = epoch_form, epoch_block
+    cfg.epoch_form, cfg.epoch_block, cfg.piece_log2 = epoch_form, epoch_block, piece_log2
     h = ctypes.c_void_p()
     _check(load().wv_server_create(ctypes.byref(cfg), ctypes.byref(h)))
     return h

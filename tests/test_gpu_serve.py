@@ -155,3 +155,30 @@ def test_serving_rejects_bad_queries():
             wv.wv_server_submit_range(s, 10, 2**38)
     finally:
         wv.wv_server_destroy(s)
+
+
+def test_serving_rejects_bad_configs():
+    for kw in ({"epoch_form": 4}, {"epoch_block": 48}, {"epoch_block": 512}, {"piece_log2": 11},
+               {"piece_log2": 25}):
+        with pytest.raises(wv.WvError):
+            wv.wv_server_destroy(wv.wv_server_create(**kw))
+
+
+@pytest.mark.parametrize("k", [12, 20])
+def test_serving_piece_length_keeps_results(k):
+    """Pieces of at most 2^12 (many per sum, short u-form pieces) and 2^20
+    terms (whole sums): the same residues as the query computed alone, and the
+    stored oracle residues of a prime below 1e11."""
+    s = wv.wv_server_create(piece_log2=k, epoch_terms=2e10)
+    try:
+        a = wv.wv_server_submit_range(s, 2 * 10**9, 2 * 10**9 + 20000)
+        b = wv.wv_server_submit_prime(s, TOP_PRIME)
+        for q in (a, b):
+            assert wv.wv_server_wait(s, q, 600.0)["state"] == 2
+        pr, rb, re = wv.wv_server_result(s, a)
+        ref = _alone_range(2 * 10**9, 2 * 10**9 + 20000)
+        assert np.array_equal(pr, ref[0]) and np.array_equal(rb, ref[1]) and np.array_equal(re, ref[2])
+        pr, rb, re = wv.wv_server_result(s, b)
+        assert (int(rb[0]), int(re[0])) == _gold()[TOP_PRIME]
+    finally:
+        wv.wv_server_destroy(s)
