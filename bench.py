@@ -50,14 +50,14 @@ IMAD_SLOTS_PER_MODMUL64 = 17
 # run is that busy share scaled by the run's own terms per SM per clock.  Set an entry to None
 # whenever its kernel changes, until it is captured again.
 PIPE_PROFILE = {
-    # k_accumulate<0,1,48,1> (form 48: the u form on pieces of 6144+ terms, lane chains): 492
-    # primes of [1062200000, 1062210000), BB2244 + EE2004, 2.3139e10 terms, 8.544 ms at 2.069 GHz;
-    # IMAD pipe 79.71 %, ALU 72.78 % of elapsed.  Traffic: one launch of the full window
-    # (--metrics dram__bytes_read.sum,dram__bytes_write.sum, the second launch): 1.043 GB read +
-    # 0.637 GB written
-    "accumulate_m31": {"imad_pct": 0.7971, "alu_pct": 0.7278, "terms_per_clk_sm": 8.610,
-                       "inst_per_term": 7.572e9 * 32 / 2.3139e10,
-                       "traffic_bytes": 1043415552 + 637145600,
+    # k_accumulate<0,1,48,1> (form 48: the u form on pieces of 3072+ terms, lane chains; chain
+    # set-up with folded REDC products): 492 primes of [1062200000, 1062210000), BB2244 +
+    # EE2004, 2.3139e10 terms, 8.031 ms at 2.068 GHz; IMAD pipe 79.86 %, ALU 70.04 % of elapsed.
+    # Traffic: one launch of the full window (--metrics dram__bytes_read.sum,dram__bytes_write.sum,
+    # the second launch): 1.041 GB read + 0.637 GB written
+    "accumulate_m31": {"imad_pct": 0.7986, "alu_pct": 0.7004, "terms_per_clk_sm": 9.164,
+                       "inst_per_term": 6.9373e9 * 32 / 2.3139e10,
+                       "traffic_bytes": 1040936960 + 636912384,
                        "profile": "profiles/accumulate_m31_p1e9_small.md"},
     # k_accumulate_m64cap<50,128,1> (form 50: the u form with one-round products on pieces of
     # 65536+ terms): 17 primes of [1e11 - 1e4, 1e11 - 9500), BB3802 + EE4122, 6.8787e10 terms,

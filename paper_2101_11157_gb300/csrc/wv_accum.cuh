@@ -347,45 +347,76 @@ __device__ __forceinline__ void tile_m31_grouped(const PrimeCtx &ctx, uint64_t s
       // the point loop stays rolled (it runs once per chain; unrolled it is
       // kilobytes of code that short tiles fetch again and again); the table
       // indices stay compile-time, the diagonal lengths are predicated
+      // (signed words, p < 2^30) the point's products as the main loop's
+      // REDC folded into a wide multiply-add, not canonicalised: from t in
+      // [0, p), P and Pu stay in (-p, p) and Q in (-2p, 2p); u's factor x
+      // steps as a plain integer (it falls by at most K (DTOP + 1) < 2^10
+      // below 0); one canonicalisation per point before the fold
+      const int32_t sp = (int32_t)ctx.p;
+      auto sredc = [&](int32_t a, int32_t b) {
+        const int64_t w = mul_wide(a, b);
+        return hi32(mad_wide((int32_t)((uint32_t)lo32(w) * q), np, w));
+      };
+      int32_t xs = (int32_t)xc;
 #pragma unroll 1
       for (int m = DTOP; m >= 0; --m) {
         uint32_t P = 0, Q = S.one, Pu = 0;
+        if constexpr (!U) {
+          int32_t Ps = 0, Qs = (int32_t)S.one, Pus = 0;
 #pragma unroll
-        for (int i = 0; i < K; ++i) {
-          if (i == 0) {
-            P = t;
-            if (UF) Pu = xc;
-          } else {
-            Q = S.add(S.mul(Q, t), P);
-            P = S.mul(P, t);
-            if (UF) Pu = S.mul(Pu, xc);
+          for (int i = 0; i < K; ++i) {
+            if (i == 0) {
+              Ps = (int32_t)t;
+              if (UF) Pus = xs;
+            } else {
+              Qs = sredc(Qs, (int32_t)t) + Ps;
+              Ps = sredc(Ps, (int32_t)t);
+              if (UF) Pus = sredc(Pus, xs);
+            }
+            t = S.sub(t, d1);
+            d1 = S.sub(d1, d2);
+            if (EX == 3) d2 = S.sub(d2, S.c6);
+            if (UF) xs -= 1;
           }
-          t = S.sub(t, d1);
-          d1 = S.sub(d1, d2);
-          if (EX == 3) d2 = S.sub(d2, S.c6);
-          if (UF) xc = S.sub(xc, S.c1);
+          P = (uint32_t)m31_canon(Ps, sp);
+          Q = (uint32_t)m31_canon(Qs, sp);
+          if (UF) Pu = (uint32_t)m31_canon(Pus, sp);
+        } else {
+#pragma unroll
+          for (int i = 0; i < K; ++i) {
+            if (i == 0) {
+              P = t;
+              if (UF) Pu = xc;
+            } else {
+              Q = S.add(S.mul(Q, t), P);
+              P = S.mul(P, t);
+              if (UF) Pu = S.mul(Pu, xc);
+            }
+            t = S.sub(t, d1);
+            d1 = S.sub(d1, d2);
+            if (EX == 3) d2 = S.sub(d2, S.c6);
+            if (UF) xc = S.sub(xc, S.c1);
+          }
         }
+        // fold the point into the diagonals over their whole length: with
+        // zeros before the first point, a difference of order j <= D at the
+        // last point still involves only its last j + 1 (real) points
         if (m <= DT) {
           uint32_t nv = UF ? Pu : P;
 #pragma unroll
           for (int j = 0; j <= DT; ++j) {
-            if (j <= DT - m) {
-              const uint32_t old = va[j];
-              va[j] = nv;
-              nv = S.sub(nv, old);
-            }
+            const uint32_t old = va[j];
+            va[j] = nv;
+            if (j < DT) nv = S.sub(nv, old);
           }
         }
-        uint32_t nv;
         if (m <= DB) {
-          nv = Q;
+          uint32_t nv = Q;
 #pragma unroll
           for (int j = 0; j <= DB; ++j) {
-            if (j <= DB - m) {
-              const uint32_t old = vb[j];
-              vb[j] = nv;
-              nv = S.sub(nv, old);
-            }
+            const uint32_t old = vb[j];
+            vb[j] = nv;
+            if (j < DB) nv = S.sub(nv, old);
           }
         }
       }
