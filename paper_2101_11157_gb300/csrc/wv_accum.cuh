@@ -448,7 +448,10 @@ __device__ __forceinline__ void tile_m31_grouped(const PrimeCtx &ctx, uint64_t s
     a = (int32_t)r;
   };
   const uint32_t G32 = (uint32_t)G;  // chains hold fewer than 2^32 groups (tiles < 2^32 terms)
-#pragma unroll 1
+  // two groups per loop trip: the trip's counter, compare and branch are
+  // about 3 % of a group's instructions (unrolling the 64-bit kernel's loop
+  // the same way measured 0.6 % slower)
+#pragma unroll 2
   for (uint32_t g = 0; g < G32; ++g) {
 #pragma unroll
     for (int k = 0; k < ILP; ++k) {
