@@ -880,7 +880,9 @@ __device__ __forceinline__ void tile_m64_grouped(const PrimeCtx &ctx, uint64_t s
     {
       uint64_t xr = s + (uint64_t)(K * (DTOP + 1) - 1);
       xr = xr >= p ? xr % p : xr;
-      uint64_t xc = xr;  // the plain x of the current term (u form)
+      // the plain x of the current term (u form), kept as x + p: it falls by
+      // at most K (DTOP + 1) < 2^10 during the set-up and stays positive
+      uint64_t xc = xr + p;
       const uint64_t sq = (uint64_t)M.mulmod((int64_t)xr, (int64_t)xr);
       uint64_t t, d1, d2;
       if (EX == 3) {  // x^3, 3x^2 - 3x + 1, 6x - 6, 6
@@ -892,7 +894,10 @@ __device__ __forceinline__ void tile_m64_grouped(const PrimeCtx &ctx, uint64_t s
         d1 = (2 * xr + p - 1) % p;
         d2 = 2;
       }
-      // one point: the pair (P, Q) of the K consecutive x from the current x down
+      // one point: the pair (P, Q) of the K consecutive x from the current x
+      // down, products not canonicalised (P, Pu < p + 2^12, Q < 2p + 2^13:
+      // inputs below about 2^38 keep each product below p + 2^12); the
+      // caller reduces them
       auto point = [&](uint64_t &P, uint64_t &Q, uint64_t &Pu) {
         P = 0;
         Q = ctx.one;
@@ -903,20 +908,23 @@ __device__ __forceinline__ void tile_m64_grouped(const PrimeCtx &ctx, uint64_t s
             P = t;
             if (UF) Pu = xc;
           } else {
-            Q = m64_once(m64_mm(Q, t, KK) + P, p);
+            Q = m64_mm(Q, t, KK) + P;
             P = m64_mm(P, t, KK);
-            if (UF) Pu = m64_once(m64_mm(Pu, xc, KK), p);
+            if (UF) Pu = m64_mm(Pu, xc, KK);
           }
           t = m64_subm(t, d1, p);
           d1 = m64_subm(d1, d2, p);
           if (EX == 3) d2 = m64_subm(d2, 6, p);
-          if (UF) xc = m64_subm(xc, 1, p);
+          if (UF) xc -= 1;
         }
+        Q = m64_once(m64_once(Q, p), p);
       };
       if constexpr ((V & 32) != 0) {
         // the point loop rolled (flag 32): a few hundred instructions of code
         // instead of DA + 1 unrolled copies; the table indices stay
-        // compile-time and the diagonal lengths are predicated
+        // compile-time, and each point folds into the diagonals over their
+        // whole length (with zeros before the first point, a difference of
+        // order j <= D at the last point involves only its last j + 1 points)
 #pragma unroll
         for (int j = 0; j <= DT; ++j) ga[k][j] = 0;
 #pragma unroll
@@ -930,22 +938,18 @@ __device__ __forceinline__ void tile_m64_grouped(const PrimeCtx &ctx, uint64_t s
             nv = m64_once(UF ? Pu : P, p);
 #pragma unroll
             for (int j = 0; j <= DT; ++j) {
-              if (j <= DT - m) {
-                const uint64_t old = ga[k][j];
-                ga[k][j] = nv;
-                if (j < DT - m) nv = m64_subm(nv, old, p);
-              }
+              const uint64_t old = ga[k][j];
+              ga[k][j] = nv;
+              if (j < DT) nv = m64_subm(nv, old, p);
             }
           }
           if (m <= DB) {
-            nv = m64_once(Q, p);
+            nv = Q;
 #pragma unroll
             for (int j = 0; j <= DB; ++j) {
-              if (j <= DB - m) {
-                const uint64_t old = gb[k][j];
-                gb[k][j] = nv;
-                if (j < DB - m) nv = m64_subm(nv, old, p);
-              }
+              const uint64_t old = gb[k][j];
+              gb[k][j] = nv;
+              if (j < DB) nv = m64_subm(nv, old, p);
             }
           }
         }
@@ -963,7 +967,7 @@ __device__ __forceinline__ void tile_m64_grouped(const PrimeCtx &ctx, uint64_t s
             if (j < DA - m) nv = m64_subm(nv, old, p);
           }
           if (m <= DB) {
-            nv = m64_once(Q, p);
+            nv = Q;
 #pragma unroll
             for (int j = 0; j <= DB - m; ++j) {
               const uint64_t old = gb[k][j];
