@@ -51,21 +51,23 @@ IMAD_SLOTS_PER_MODMUL64 = 17
 # whenever its kernel changes, until it is captured again.
 PIPE_PROFILE = {
     # k_accumulate<0,1,48,1> (form 48: the u form on pieces of 3072+ terms, lane chains; chain
-    # set-up with folded REDC products): 492 primes of [1062200000, 1062210000), BB2244 +
-    # EE2004, 2.3139e10 terms, 8.031 ms at 2.068 GHz; IMAD pipe 79.86 %, ALU 70.04 % of elapsed.
-    # Traffic: one launch of the full window (--metrics dram__bytes_read.sum,dram__bytes_write.sum,
-    # the second launch): 1.041 GB read + 0.637 GB written
-    "accumulate_m31": {"imad_pct": 0.7986, "alu_pct": 0.7004, "terms_per_clk_sm": 9.164,
-                       "inst_per_term": 6.9373e9 * 32 / 2.3139e10,
-                       "traffic_bytes": 1040936960 + 636912384,
+    # set-up with folded REDC products; group loop unrolled by two): 492 primes of [1062200000,
+    # 1062210000), BB2244 + EE2004, 2.3139e10 terms, 7.998 ms at 2.067 GHz; IMAD pipe 79.43 %,
+    # ALU 69.54 % of elapsed.  Traffic: one launch of the full window (--metrics
+    # dram__bytes_read.sum,dram__bytes_write.sum, the second launch): 1.042 GB read + 0.637 GB
+    # written
+    "accumulate_m31": {"imad_pct": 0.7943, "alu_pct": 0.6954, "terms_per_clk_sm": 9.209,
+                       "inst_per_term": 6.8121e9 * 32 / 2.3139e10,
+                       "traffic_bytes": 1041792512 + 636746752,
                        "profile": "profiles/accumulate_m31_p1e9_small.md"},
     # k_accumulate_m64cap<50,128,1> (form 50: the u form with one-round products on pieces of
     # 65536+ terms): 17 primes of [1e11 - 1e4, 1e11 - 9500), BB3802 + EE4122, 6.8787e10 terms,
-    # 44.022 ms at 2.057 GHz; IMAD pipe 85.51 %, ALU 53.12 %.  Traffic: one launch of the full
-    # 391-prime window (the second launch): 112.9 MB read + 62.8 MB written
+    # 44.022 ms at 2.057 GHz; IMAD pipe 85.51 %, ALU 53.12 %.  The capture predates the cheaper
+    # per-chain set-up (the group loop is unchanged); its full-launch traffic (112.9 MB read +
+    # 62.8 MB written) is not used for the changed kernel
     "accumulate_m64": {"imad_pct": 0.8551, "alu_pct": 0.5312, "terms_per_clk_sm": 4.9986,
                        "inst_per_term": 3.3522e10 * 32 / 6.8787e10,
-                       "traffic_bytes": 112914176 + 62783232,
+                       "traffic_bytes": None,
                        "profile": "profiles/accumulate_m64_top_window.md"},
 }
 

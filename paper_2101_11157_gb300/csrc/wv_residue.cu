@@ -215,13 +215,6 @@ __global__ void k_lane_chains(Plan P) {  // pieces per segment
   P.seg_tiles[idx] = t;
 }
 
-// Segments in row-major order (row j, then slot): the lanes of a warp take
-// one row of 32 consecutive primes, whose pieces mostly share a length bin,
-// so that one atomic serves the warp.
-__device__ __forceinline__ uint32_t seg_rowmajor(const Plan &P, size_t idx) {
-  const uint32_t j = (uint32_t)(idx / P.n), slot = (uint32_t)(idx - (size_t)j * P.n);
-  return slot * P.rows_pp + j;
-}
 
 // Sort key of the T pieces of segment s: class * kChainBins + length bin of
 // the longest piece (the others are one term shorter at most).  The kernels
@@ -237,22 +230,53 @@ __device__ __forceinline__ uint32_t seg_key(const Plan &P, uint32_t s, uint32_t 
   return cls * kChainBins + (e * 32 + frac);
 }
 
+// The histogram and scatter kernels visit the segments in tiles of kTileRows
+// rows by 32 primes: the block's threads load the tile prime by prime (a
+// prime's rows are contiguous, so a sector serves 8 rows), stage it in
+// shared memory, and each warp then takes one row of the tile across its 32
+// primes: neighbouring primes' pieces of one row mostly share a length bin,
+// so that one atomic serves the warp.
+constexpr uint32_t kTileRows = 8, kTileThreads = 32 * kTileRows;
+struct TileIdx {
+  uint32_t slot, j;  // the thread's (prime, row) in the load phase
+  bool ok;
+};
+__device__ __forceinline__ TileIdx tile_load_idx(const Plan &P, size_t tile) {
+  const size_t nst = (P.n + 31) / 32;
+  const uint32_t j0 = (uint32_t)(tile / nst) * kTileRows, slot0 = (uint32_t)(tile % nst) * 32;
+  TileIdx r;
+  r.slot = slot0 + (threadIdx.x / kTileRows);
+  r.j = j0 + (threadIdx.x % kTileRows);
+  r.ok = r.slot < P.n && r.j < P.rows_pp;
+  return r;
+}
+__device__ __forceinline__ size_t tile_count(const Plan &P) {
+  return (size_t)((P.rows_pp + kTileRows - 1) / kTileRows) * ((P.n + 31) / 32);
+}
+
 // counts per key: segments of one piece add through one atomic per key and
 // warp, longer segments their piece count each; keys kept for the scatter
-__global__ void k_chain_hist(Plan P) {
-  const size_t ns = (size_t)P.n * P.rows_pp, stride = (size_t)gridDim.x * blockDim.x;
-  const uint32_t lane = threadIdx.x & 31;
-  for (size_t b = (size_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); b < ns; b += stride) {
-    const size_t idx = b + lane;
+__global__ void __launch_bounds__(kTileThreads) k_chain_hist(Plan P) {
+  __shared__ uint32_t shT[kTileRows][33], shK[kTileRows][33];
+  const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const size_t nt = tile_count(P);
+  for (size_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+    const TileIdx ti = tile_load_idx(P, tile);
     uint32_t T = 0, key = 0;
-    if (idx < ns) {
-      const uint32_t s = seg_rowmajor(P, idx);
+    if (ti.ok) {
+      const uint32_t s = ti.slot * P.rows_pp + ti.j;
       T = P.seg_tiles[s];
       if (T) {
         key = seg_key(P, s, T);
         P.chain_key[s] = key;
       }
     }
+    shT[threadIdx.x % kTileRows][threadIdx.x / kTileRows] = T;
+    shK[threadIdx.x % kTileRows][threadIdx.x / kTileRows] = key;
+    __syncthreads();
+    T = shT[w][lane];
+    key = shK[w][lane];
+    __syncthreads();
     const uint32_t peers = __match_any_sync(0xffffffffu, T == 1 ? key : 0xffff0000u | lane);
     if (T == 1 && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&P.chain_hist[key], (uint32_t)__popc(peers));
     if (T > 1) atomicAdd(&P.chain_hist[key], T);
@@ -302,33 +326,54 @@ __global__ void __launch_bounds__(kOffThreads) k_chain_offsets(Plan P) {
   }
 }
 
-__global__ void k_chain_scatter(Plan P) {
-  const size_t ns = (size_t)P.n * P.rows_pp, stride = (size_t)gridDim.x * blockDim.x;
-  const uint32_t lane = threadIdx.x & 31;
-  for (size_t b = (size_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); b < ns; b += stride) {
-    const size_t idx = b + lane;
-    uint32_t T = 0, key = 0, s = 0;
-    if (idx < ns) {
-      s = seg_rowmajor(P, idx);
+__global__ void __launch_bounds__(kTileThreads) k_chain_scatter(Plan P) {
+  __shared__ uint32_t shT[kTileRows][33], shK[kTileRows][33], shF[kTileRows][33];
+  __shared__ uint64_t shLo[kTileRows][33], shCnt[kTileRows][33];
+  const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const size_t nt = tile_count(P), nst = (P.n + 31) / 32;
+  for (size_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+    const TileIdx ti = tile_load_idx(P, tile);
+    uint32_t T = 0, key = 0, f = 0;
+    uint64_t lo = 0, cnt = 0;
+    if (ti.ok) {
+      const uint32_t s = ti.slot * P.rows_pp + ti.j;
       T = P.seg_tiles[s];
-      if (T) key = P.chain_key[s];
+      if (T) {
+        key = P.chain_key[s];
+        f = P.seg_first[s];
+        lo = P.seg_lo[s];
+        cnt = P.seg_cnt[s];
+      }
     }
+    {
+      const uint32_t r = threadIdx.x % kTileRows, c = threadIdx.x / kTileRows;
+      shT[r][c] = T;
+      shK[r][c] = key;
+      shF[r][c] = f;
+      shLo[r][c] = lo;
+      shCnt[r][c] = cnt;
+    }
+    __syncthreads();
+    T = shT[w][lane];
+    key = shK[w][lane];
+    f = shF[w][lane];
+    lo = shLo[w][lane];
+    cnt = shCnt[w][lane];
+    __syncthreads();
+    const uint32_t slot = (uint32_t)(tile % nst) * 32 + lane;
+    const uint32_t row = (uint32_t)(tile / nst) * kTileRows + w;
     const uint32_t peers = __match_any_sync(0xffffffffu, T == 1 ? key : 0xffff0000u | lane);
     const uint32_t leader = (uint32_t)(__ffs(peers) - 1);
     uint32_t pos = 0;
     if (T == 1 && lane == leader) pos = atomicAdd(&P.chain_hist[key], (uint32_t)__popc(peers));
     pos = __shfl_sync(0xffffffffu, pos, (int)leader);
-    if (T) {
-      const uint32_t slot = s / P.rows_pp, row = s - slot * P.rows_pp, f = P.seg_first[s];
-      const uint64_t lo = P.seg_lo[s], cnt = P.seg_cnt[s];
-      if (T == 1) {
-        P.rec[pos + __popc(peers & ((1u << lane) - 1u))] = PieceRec{lo, (uint32_t)cnt, f, slot, row};
-      } else {
-        const uint32_t at = atomicAdd(&P.chain_hist[key], T);
-        for (uint32_t k = 0; k < T; ++k) {
-          const uint64_t b0 = cnt * k / T, b1 = cnt * (k + 1) / T;
-          P.rec[at + k] = PieceRec{lo + b0, (uint32_t)(b1 - b0), f + k, slot, row};
-        }
+    if (T == 1) {
+      P.rec[pos + __popc(peers & ((1u << lane) - 1u))] = PieceRec{lo, (uint32_t)cnt, f, slot, row};
+    } else if (T > 1) {
+      const uint32_t at = atomicAdd(&P.chain_hist[key], T);
+      for (uint32_t k = 0; k < T; ++k) {
+        const uint64_t b0 = cnt * k / T, b1 = cnt * (k + 1) / T;
+        P.rec[at + k] = PieceRec{lo + b0, (uint32_t)(b1 - b0), f + k, slot, row};
       }
     }
   }
@@ -393,14 +438,14 @@ static wv_status plan_launches(Plan &P, uint32_t *u32tmp, int sms, cudaStream_t 
     WV_LAUNCH("plan_tilemap", k_plan_tilemap, (unsigned)((ns + 255) / 256), 256, 0, s, P);
   WV_LAUNCH("plan_split", k_plan_split, 1, 1, 0, s, P);
   if (P.lane) {
-    // one segment per thread (grid-stride beyond 2^20 blocks): many warps in
-    // flight hide the atomics' and gathers' latency
-    const size_t gsz = (ns + 255) / 256;
+    // one tile of kTileRows rows by 32 primes per block (grid-stride beyond
+    // 2^20 blocks): many warps in flight hide the atomics' latency
+    const size_t gsz = (size_t)((P.rows_pp + kTileRows - 1) / kTileRows) * ((P.n + 31) / 32);
     const unsigned gs = (unsigned)(gsz < (1u << 20) ? (gsz ? gsz : 1) : (1u << 20));
     WV_CUDA(cudaMemsetAsync(P.chain_hist, 0, (size_t)kChainClasses * kChainBins * 4, s));
-    WV_LAUNCH("chain_hist", k_chain_hist, gs, 256, 0, s, P);
+    WV_LAUNCH("chain_hist", k_chain_hist, gs, kTileThreads, 0, s, P);
     WV_LAUNCH("chain_offsets", k_chain_offsets, 1, kOffThreads, 0, s, P);
-    WV_LAUNCH("chain_scatter", k_chain_scatter, gs, 256, 0, s, P);
+    WV_LAUNCH("chain_scatter", k_chain_scatter, gs, kTileThreads, 0, s, P);
   }
   return WV_OK;
 }
