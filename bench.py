@@ -61,13 +61,12 @@ PIPE_PROFILE = {
                        "traffic_bytes": 1041792512 + 636746752,
                        "profile": "profiles/accumulate_m31_p1e9_small.md"},
     # k_accumulate_m64cap<50,128,1> (form 50: the u form with one-round products on pieces of
-    # 65536+ terms): 17 primes of [1e11 - 1e4, 1e11 - 9500), BB3802 + EE4122, 6.8787e10 terms,
-    # 44.022 ms at 2.057 GHz; IMAD pipe 85.51 %, ALU 53.12 %.  The capture predates the cheaper
-    # per-chain set-up (the group loop is unchanged); its full-launch traffic (112.9 MB read +
-    # 62.8 MB written) is not used for the changed kernel
-    "accumulate_m64": {"imad_pct": 0.8551, "alu_pct": 0.5312, "terms_per_clk_sm": 4.9986,
-                       "inst_per_term": 3.3522e10 * 32 / 6.8787e10,
-                       "traffic_bytes": None,
+    # 32768+ terms, cheaper per-chain set-up): 17 primes of [1e11 - 1e4, 1e11 - 9500), BB3802 +
+    # EE4122, 6.8787e10 terms, 42.019 ms at 2.068 GHz; IMAD pipe 88.41 %, ALU 54.63 %.  Traffic:
+    # one launch of the full 391-prime window (the second launch): 111.6 MB read + 53.8 MB written
+    "accumulate_m64": {"imad_pct": 0.8841, "alu_pct": 0.5463, "terms_per_clk_sm": 5.2087,
+                       "inst_per_term": 3.2788e10 * 32 / 6.8787e10,
+                       "traffic_bytes": 111565056 + 53785600,
                        "profile": "profiles/accumulate_m64_top_window.md"},
 }
 
