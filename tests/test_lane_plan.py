@@ -20,7 +20,7 @@ from paper_2101_11157_gb300 import wv
 SMS = 152
 LANES = (768, 512)        # resident threads per SM: 32-bit kernel, 64-bit kernel
 LMIN = (4096, 16384)      # shortest chain per path
-ROUNDS, ROUNDS_EPOCH, LMAX_EPOCH = 16, 4, 1 << 16
+ROUNDS, ROUNDS_EPOCH, LMAX_EPOCH = 16, 4, 1 << 17  # serving cap: the piece_log2 default
 
 
 def _rows(cid):
@@ -120,3 +120,33 @@ def test_sort_keeps_warps_uniform():
         work += sum(ns)
         lost += 32 * max(ns) - sum(ns)
     assert work / (work + lost) > 0.9
+
+
+@pytest.mark.parametrize("n,rows", [(1, 30), (33, 63), (4907, 48), (100, 7), (64, 8)])
+def test_chain_kernel_tiles_cover_every_segment_once(n, rows):
+    """k_chain_hist / k_chain_scatter: tiles of 8 rows by 32 primes, loaded by
+    256 threads prime by prime (thread t: prime t / 8, row t % 8), staged in
+    shared memory and read back by warp w, lane l as (row w, prime l).  Every
+    segment s = prime * rows + row is loaded exactly once, by eight threads
+    reading eight consecutive segments, and each warp reads one row of 32
+    consecutive primes."""
+    tile_rows, nst = 8, (n + 31) // 32
+    nt = ((rows + tile_rows - 1) // tile_rows) * nst
+    seen = np.zeros(n * rows, dtype=np.int64)
+    for tile in range(nt):
+        j0, slot0 = (tile // nst) * tile_rows, (tile % nst) * 32
+        stage = {}
+        for t in range(256):
+            slot, j = slot0 + t // tile_rows, j0 + t % tile_rows
+            if slot < n and j < rows:
+                seen[slot * rows + j] += 1
+                stage[(t % tile_rows, t // tile_rows)] = (slot, j)
+        for t in range(0, 256, 8):  # eight threads, one prime, consecutive rows
+            segs = [stage[(r, t // 8)] for r in range(8) if (r, t // 8) in stage]
+            assert [j for _, j in segs] == list(range(segs[0][1], segs[0][1] + len(segs))) if segs else True
+        for w in range(tile_rows):
+            for lane in range(32):
+                if (w, lane) in stage:
+                    assert stage[(w, lane)] == (slot0 + lane, j0 + w)
+    assert (seen == 1).all()
+
