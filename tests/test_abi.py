@@ -79,3 +79,40 @@ def test_every_tuning_grid_passes_option_validation():
         for opt in grid:
             st = lib.wv_residues_ex(None, 0, None, None, wv._options(opt), None)
             assert st == wv.WV_OK, (name, opt, wv.wv_last_error())
+
+
+def test_binding_structs_match_the_headers(tmp_path):
+    """Every struct the binding passes across the boundary has the size and
+    field offsets the C headers give it (a C program built with the host
+    compiler prints them)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    structs = [s for s in ("wv_options", "wv_hit", "wv_request", "wv_server_config", "wv_query_info")
+               if hasattr(wv, s)]
+    headers = sorted(os.path.basename(h) for h in glob.glob(os.path.join(ROOT, "include", "*.h")))
+    lines = ['#include <stdio.h>', '#include <stddef.h>'] + [f'#include "{h}"' for h in headers]
+    lines.append("int main(void) {")
+    for s in structs:
+        lines.append(f'  printf("{s} size %zu\\n", sizeof({s}));')
+        for f, _ in getattr(wv, s)._fields_:
+            lines.append(f'  printf("{s} {f} %zu\\n", offsetof({s}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n"):
+        if line:
+            s, f, v = line.split()
+            got[(s, f)] = int(v)
+    for s in structs:
+        cls = getattr(wv, s)
+        assert got[(s, "size")] == ctypes.sizeof(cls), s
+        for f, _ in cls._fields_:
+            assert got[(s, f)] == getattr(cls, f).offset, (s, f)
