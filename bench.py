@@ -190,6 +190,7 @@ def reference_arm(args):
                                "Glaisher eqn 4.1 for E), one seeded prime per host core per step",
                    "l2": "n/a (CPU)"},
         "cpu_baseline": {"value": val, "unit": "primes/s", "cores": cores, "kind": "oracle",
+                         "value_per_core": val / cores,
                          "sample": f"{len(sample)} seeded primes of the window per step (one per host "
                                    f"core), B then E on each of {cores} threads"},
         "e2e": {"value": val, "unit": "primes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -312,7 +313,9 @@ def gpu_arm(args):
         cpu = {"value": len(sample) / dt, "unit": "primes/s", "cores": cores, "kind": "oracle",
                "sample": f"{len(sample)} seeded primes of the window (one per host core, both residues): "
                          "B by Stafford-Vandiver (eqn 2.4), E by Glaisher (eqn 4.1), 128-bit remainders",
-               "seconds": dt}
+               "seconds": dt,
+               # one prime per core, all cores at once: the rate of one core
+               "value_per_core": len(sample) / dt / cores}
         # the oracle and the GPU agree on the sample
         idx = np.searchsorted(primes, sample)
         gb, ge = api.to_u64(d_rb)[idx], api.to_u64(d_re)[idx]
