@@ -265,3 +265,98 @@ def test_m64_setup_products_without_canonicalisation(K):
             qc = Q - p if Q >= p else Q
             qc = qc - p if qc >= p else qc
             assert 0 <= qc < p and qc == Q % p
+
+
+# ------------------------------------------------------ one chain, mod p
+def chain_model(s, n, K, ex, p, R, uf, half=False):
+    """The grouped chain of tile_m31_grouped / tile_m64_grouped modelled mod p,
+    each REDC as a factor R^-1 (or h^-1 = 2^-32 for the 64-bit u form's
+    one-round products, `half`): tables from the set-up points (top down,
+    folded into the diagonals over their whole length, odd orders negated),
+    stepped by additions; each group's tabled values are checked against the
+    group's own products; returns c1 / c0 after the groups, the scale and
+    the single-term tail."""
+    Ri = pow(R, -1, p)
+    hi_ = pow(1 << 32, -1, p)
+    DA, DB = K * ex, (K - 1) * ex
+    DT = K if uf else DA
+    DTOP = max(DT, DB)
+    one = R % p
+
+    def point(m):  # the K consecutive x of point m, from the top down
+        xs = [s + m * K + K - 1 - i for i in range(K)]
+        ts = [pow(x, ex, p) for x in xs]
+        P, Q, Pu = ts[0], one, xs[0] % p
+        for i in range(1, K):
+            Q = (Q * ts[i] * Ri + P) % p
+            P = P * ts[i] * Ri % p
+            Pu = Pu * xs[i] * Ri % p
+        return P, Q, Pu
+
+    va, vb = [0] * (DT + 1), [0] * (DB + 1)
+    for m in range(DTOP, -1, -1):
+        P, Q, Pu = point(m)
+        for vals, nv, D in ((va, Pu if uf else P, DT), (vb, Q, DB)):
+            if m > D:
+                continue
+            for j in range(D + 1):
+                old = vals[j]
+                vals[j] = nv
+                if j < D:
+                    nv = (nv - old) % p
+    ga = [(-v) % p if j & 1 else v for j, v in enumerate(va)]
+    gb = [(-v) % p if j & 1 else v for j, v in enumerate(vb)]
+    G = n // K
+    c0, c1 = one, 0
+    for g in range(G):
+        P, Q, Pu = point(g)
+        assert ga[0] == (Pu if uf else P) and gb[0] == Q, g  # the tables reproduce the group
+        A = ga[0]
+        if uf:
+            u = A
+            if half:  # one-round products: u u 2^-32 (u^3 2^-64)
+                A = u * u * hi_ % p
+                if ex == 3:
+                    A = A * u * hi_ % p
+            else:
+                A = u * u * Ri % p
+                if ex == 3:
+                    A = A * u * Ri % p
+        c0, c1 = c0 * A * Ri % p, (c1 * A + c0 * gb[0]) * Ri % p
+        for tab in (ga, gb):
+            for j in range(len(tab) - 1):
+                tab[j] = (tab[j] + tab[j + 1]) % p
+    if uf:
+        if half:  # (ex - 1)(2K - 1) one-round steps of f = R, then c1 f R^-1
+            f = one
+            for _ in range((ex - 1) * (2 * K - 1)):
+                f = f * hi_ % p
+        else:  # (ex - 1) K steps f <- f 1 R^-1
+            f = one
+            for _ in range((ex - 1) * K):
+                f = f * Ri % p
+        c1 = c1 * f * Ri % p
+    for x in range(s + G * K, s + n):  # the tail, one term at a time (eqn 3.12)
+        t = pow(x, ex, p)
+        c0, c1 = c0 * t * Ri % p, (c1 * t * Ri + c0) % p
+    return c1 * pow(c0, -1, p) % p
+
+
+@pytest.mark.parametrize("K,ex,uf,half", [(2, 3, False, False), (3, 2, False, False),
+                                          (4, 3, False, False), (8, 3, True, False),
+                                          (10, 2, True, False), (12, 3, True, True),
+                                          (16, 2, True, True), (8, 3, True, True)])
+def test_chain_model_equals_single_terms(K, ex, uf, half):
+    """Groups of K terms through the difference tables give c1 / c0 = R sum
+    s^-e, as single-term steps do (eqn 3.12 against eqn 3.14), for the pair
+    tables, the u form and the 64-bit u form's one-round products."""
+    rng = random.Random(K * 7 + ex)
+    R = 1 << (64 if half else 32)
+    for p in (1000003, 1062232319, 2147483647, 99999998237):
+        if not half and p >= 1 << 31:
+            continue
+        for _ in range(3):
+            n = rng.randrange(K * (K * ex + 2), K * (K * ex + 2) + 3 * K)
+            s = rng.randrange(1, p - n - 1)
+            want = R * sum(pow(pow(x, ex, p), -1, p) for x in range(s, s + n)) % p
+            assert chain_model(s, n, K, ex, p, R, uf, half) == want
