@@ -47,6 +47,16 @@ def sredc(a, b, p):
     return s32(d >> 32)
 
 
+def sredc_sum(w, p):
+    """hi32(mad.wide(lo32(w) * q, -p, w)) for a 64-bit sum w of products."""
+    q = pow(p, -1, M32)
+    assert s64(w) == w
+    m = s32((w % M32) * q)
+    d = s64(w + m * s32(-p))
+    assert d == w - m * p and d % M32 == 0
+    return s32(d >> 32)
+
+
 @pytest.mark.parametrize("seed", [1, 2])
 def test_signed_redc_value_and_bound(seed):
     """REDC of w = a b is a b 2^-32 mod p and lies within |w| / 2^32 + p / 2."""
@@ -360,3 +370,49 @@ def test_chain_model_equals_single_terms(K, ex, uf, half):
             s = rng.randrange(1, p - n - 1)
             want = R * sum(pow(pow(x, ex, p), -1, p) for x in range(s, s + n)) % p
             assert chain_model(s, n, K, ex, p, R, uf, half) == want
+
+
+def test_pair_update_signed_keeps_accumulators_in_range():
+    """The signed path's group step c0 <- REDC(c0 G0), c1 <- REDC(c1 G0 + c0 G1)
+    (p < 2^30): with G0 in (-p, p) (a u-form power, or a canonical table
+    value) and G1 in [0, p), c0 and c1 stay in (-p, p) group after group,
+    every wide product exact, and the pair stays correct mod p."""
+    rng = random.Random(11)
+    for p in odd_moduli(rng, 3, 1 << 30, 12) + [(1 << 30) - 35, 1062232319 % (1 << 30) | 1]:
+        Ri = pow(M32, -1, p)
+        c0, c1 = M32 % p, 0
+        e0, e1 = c0, c1
+        for _ in range(300):
+            A = rng.choice([rng.randrange(-p + 1, p), p - 1, -p + 1, 0])
+            B = rng.choice([rng.randrange(p), p - 1])
+            w1 = c1 * A + c0 * B  # mad.wide(c0, B, mul.wide(c1, A))
+            assert abs(w1) < 1 << 63
+            c0, c1 = sredc(c0, A, p), sredc_sum(w1, p)
+            e0, e1 = e0 * A * Ri % p, (e1 * A + e0 * B) * Ri % p
+            assert abs(c0) < p and abs(c1) < p
+            assert (c0 - e0) % p == 0 and (c1 - e1) % p == 0
+
+
+def test_pair_update_unsigned_canonical():
+    """2^30 <= p < 2^31 (unsigned words): c0 G0 and c1 G0 + c0 G1 stay below
+    2 p^2 < 2^63, the REDC's high word below 2p, and one conditional
+    subtraction makes each result canonical."""
+    rng = random.Random(12)
+    for p in odd_moduli(rng, 1 << 30, 1 << 31, 12) + [2147483647]:
+        qn = (-pow(p, -1, M32)) % M32
+        Ri = pow(M32, -1, p)
+
+        def redc(w):
+            assert 0 <= w < 1 << 63
+            m = lo(w) * qn % M32
+            t = hi(umad(m, p, w))
+            return min(t, (t - p) % M32)
+
+        c0, c1 = M32 % p, 0
+        for _ in range(300):
+            A, B = rng.randrange(p), rng.randrange(p)
+            w0, w1 = c0 * A, c1 * A + c0 * B
+            assert w1 < 2 * p * p < 1 << 63
+            n0, n1 = redc(w0), redc(w1)
+            assert n0 == w0 * Ri % p and n1 == w1 * Ri % p
+            c0, c1 = n0, n1
